@@ -1,0 +1,429 @@
+#!/usr/bin/env python3
+"""Benchmark of the aggregated hydro RHS on one GB300 (or N replicas).
+
+Workload (default): 32768 sub-grids of 8^3 (256^3 cells, 11 fields: rho,
+momentum, E, tau and 5 species) holding two n = 1.5 polytropes on a 1e-10
+atmosphere; inputs ~7.9 GB on the device, far larger than L2.
+
+Metric: cell-updates/s of one RHS evaluation (interior cells x evaluations /
+s).  `value` is the binary64 aggregated form (one tuned, graph-replayed launch
+per step); the JSON line also carries the mixed binary32/binary64 form, the
+per-sub-grid launch form, the end-to-end number through the C ABI with host
+buffers, the roofline of the dominant kernel and the oracle timed on the host
+cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+GAMMA = 5.0 / 3.0
+WORKLOAD = "polytropes: 32768 sub-grids of 8^3 + 3 ghost layers (256^3 cells), 11 FP64 fields"
+
+
+# ------------------------------------------------------------ workloads --
+class Batch:
+    pass
+
+
+def polytrope_batch(n=256, nf=11, N=8, device="cuda", chunk=2048):
+    """Ghosted sub-grids of the polytrope domain, resident on the device.
+
+    The global periodic array is drawn on the host (synth.polytropes), copied
+    once, and cut into ghosted blocks on the device with index gathers."""
+    import torch
+
+    import paper_2210_06438_gb300 as hydro
+
+    glob = synth.polytropes(n=n, nf=nf)
+    gd = torch.from_numpy(glob).to(device)
+    del glob
+    nb = n // N
+    S = nb ** 3
+    G = N + 6
+    blocks = torch.empty((S, nf, G, G, G), dtype=torch.float64, device=device)
+    r = torch.arange(-3, N + 3, device=device)
+    ids = torch.arange(S, device=device)
+    bx, by, bz = ids % nb, (ids // nb) % nb, ids // (nb * nb)
+    for s0 in range(0, S, chunk):
+        sl = slice(s0, min(S, s0 + chunk))
+        ix = (bx[sl, None] * N + r[None, :]) % n
+        iy = (by[sl, None] * N + r[None, :]) % n
+        iz = (bz[sl, None] * N + r[None, :]) % n
+        g = gd[:, iz[:, :, None, None], iy[:, None, :, None], ix[:, None, None, :]]
+        blocks[sl] = g.permute(1, 0, 2, 3, 4)
+    del gd
+    torch.cuda.synchronize()
+    b = Batch()
+    b.n, b.N, b.nf, b.dx = S, N, nf, 2.0 / n
+    b.blocks = blocks
+    b.desc = hydro.descriptors([(int(blocks[s].data_ptr()), b.dx, N, nf) for s in range(S)])
+    b.out_doubles = S * nf * N ** 3
+    b.cells = S * N ** 3
+    b.alg_bytes = S * synth.algorithmic_bytes(N, nf)
+    return b
+
+
+# -------------------------------------------------- algorithmic counts --
+def fp64_ops_per_cell(N=8, F=11):
+    """Floating-point operations (add, sub, mul, div, sqrt; comparisons and
+    selections not counted) of the reference definition per interior cell:
+      primitives  (F + 9) per read cell,  (N^3 + 18 N^2) read cells
+      PPM         per line and field: (N+4) slopes x 6 + (N+3) faces x 5
+                  + (N+2) limited cells x 10;  3 N^2 lines
+      flux        10 F + 26 per face;  3 N^2 (N+1) faces
+      divergence  6 F per cell"""
+    n3 = N ** 3
+    prim = (F + 9) * (n3 + 18 * N * N)
+    ppm = 3 * N * N * F * ((N + 4) * 6 + (N + 3) * 5 + (N + 2) * 10)
+    flux = 3 * N * N * (N + 1) * (10 * F + 26)
+    div = 6 * F * n3
+    return (prim + ppm + flux + div) / n3
+
+
+def fp64_peak_gflops(sm_mhz, n_sm=152):
+    """binary64 FMA pipe: 2 DFMA per SM per clock (measured on this GPU:
+    1.6-2.0 per clock), i.e. 4 flop per SM per clock."""
+    return n_sm * 4 * sm_mhz * 1e-3
+
+
+# ---------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- timing --
+def time_steps(fn, steps, warmup, stream):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------- cpu baseline --
+def oracle_sample_rate(blocks_host, dx, seconds=10.0, threads=None, mode=0):
+    """The oracle (as it stands) over a sample of sub-grids, repeated until
+    `seconds` of wall time; returns (cells/s, threads, repetitions)."""
+    import oracle
+
+    threads = threads or os.cpu_count() or 1
+    cells = sum(b.shape[1] - 6 for b in blocks_host[:1]) ** 3 * len(blocks_host)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.rhs_batch(blocks_host, GAMMA, dx, mode, threads=threads)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return cells * reps / el, threads, reps
+
+
+# ------------------------------------------------------------ reference --
+def run_reference(args, rank, world):
+    """The oracle timed on the host cores: the reference arm of this build."""
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    n_sample = 2048
+    glob = synth.polytropes(n=128, nf=11)  # same recipe, smaller domain for the sample
+    blocks = list(synth.gather_blocks(glob, 8)[:n_sample])
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.rhs_batch(blocks, GAMMA, 2.0 / 128, 0, threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.rhs_batch(blocks, GAMMA, 2.0 / 128, 0, threads=threads)
+    el = time.perf_counter() - t0
+    cells = n_sample * 512
+    value = cells * args.steps / el
+    line = {
+        "impl": "reference", "metric": "cell-updates/s (FP64 hydro RHS)", "value": value,
+        "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "%d sub-grids of the polytrope recipe per step"
+                   % n_sample},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads,
+                         "kind": "oracle",
+                         "sample": "%d sub-grids of 8^3, 11 fields, per step" % n_sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours --
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2210_06438_gb300 as hydro
+
+    hydro.load(build_if_missing=True)
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    batch = polytrope_batch(n=args.domain)
+    cells = batch.cells
+    out = torch.empty(batch.out_doubles, dtype=torch.float64, device=dev)
+    amax = torch.empty(batch.n, dtype=torch.float64, device=dev)
+
+    plan64 = hydro.Plan(batch.desc, ghost=3, gamma=GAMMA, prec=hydro.FP64, autotune=True,
+                        stream=stream, n=batch.n)
+    planmx = hydro.Plan(batch.desc, ghost=3, gamma=GAMMA, prec=hydro.FP32_FLUX_FP64_ACC,
+                        autotune=True, stream=stream, n=batch.n)
+    info64, infomx = plan64.info(), planmx.info()
+    hydro.status(stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- headline: binary64 aggregated form
+    for _ in range(args.warmup):
+        plan64.execute(out, amax, stream)
+    barrier()
+    clk = ClockSampler(dev.index)
+    clk.start()
+    ms64 = time_steps(lambda: plan64.execute(out, amax, stream), args.steps, 0, stream)
+    clocks = clk.stop()
+    barrier()
+    rc, bad = hydro.status(stream)
+    if rc != hydro.HYDRO_OK:
+        raise RuntimeError("nonphysical input flagged in sub-grid %d" % bad)
+    out64 = out.clone()
+    msmx = time_steps(lambda: planmx.execute(out, amax, stream), args.steps, args.warmup, stream)
+    diff = (out - out64).view(batch.n, batch.nf, -1)
+    scale = out64.view(batch.n, batch.nf, -1).abs().amax(dim=2).clamp_min(1e-300)
+    mixed_err = float((diff.abs().amax(dim=2) / scale).max())
+    drift = out.view(batch.n, batch.nf, -1).sum(dim=(0, 2)) / \
+        out.view(batch.n, batch.nf, -1).abs().sum(dim=(0, 2)).clamp_min(1e-300)
+    drift = float(drift.abs().max())
+    del diff, scale, out64
+
+    # ---- per-sub-grid launch form (strategy-2 analogue), 128-stream pool
+    pool = [torch.cuda.Stream(device=dev) for _ in range(args.streams)]
+
+    def per_sub(prec):
+        hydro.rhs_per_subgrid(batch.desc, out, amax, pool, ghost=3, gamma=GAMMA, prec=prec,
+                              n=batch.n)
+
+    def timed_pool(prec, steps):
+        for _ in range(1):
+            per_sub(prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            per_sub(prec)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / steps * 1e3
+
+    ps_steps = max(1, min(args.steps, 3))
+    ms_ps64 = timed_pool(hydro.FP64, ps_steps)
+    ms_psmx = timed_pool(hydro.FP32_FLUX_FP64_ACC, ps_steps)
+
+    # ---- end to end through the C ABI with host buffers
+    host_in = torch.empty(batch.blocks.shape, dtype=torch.float64, pin_memory=True)
+    host_in.copy_(batch.blocks)
+    host_out = torch.empty(batch.out_doubles, dtype=torch.float64, pin_memory=True)
+    host_amax = torch.empty(batch.n, dtype=torch.float64, pin_memory=True)
+
+    def e2e_step():
+        batch.blocks.copy_(host_in, non_blocking=True)
+        plan64.execute(out, amax, stream)
+        host_out.copy_(out, non_blocking=True)
+        host_amax.copy_(amax, non_blocking=True)
+
+    e2e_steps = max(1, min(args.steps, 5))
+    ms_e2e = time_steps(e2e_step, e2e_steps, 1, stream)
+    h2d = batch.blocks.numel() * 8
+    d2h = (batch.out_doubles + batch.n) * 8
+    del host_in, host_out
+
+    # ---- max over ranks
+    t = torch.tensor([ms64, msmx, ms_ps64, ms_psmx, ms_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms64, msmx, ms_ps64, ms_psmx, ms_e2e = [float(x) for x in t.cpu()]
+    if rank != 0:
+        return
+
+    # ---- roofline of the dominant kernel (the binary64 tile kernel)
+    peaks = measured_peaks()
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    flops = fp64_ops_per_cell(8, 11) * cells
+    peak_fp64 = fp64_peak_gflops(peaks.get("sm_max_mhz", 2070.0))
+    ach = flops / (ms64 * 1e-3) * 1e-9
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roof = {"bound": "alu", "achieved": ach, "peak": peak_fp64, "unit": "GFLOP/s (fp64)",
+            "frac": ach / peak_fp64, "traffic": None,
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz" %
+            peaks.get("sm_max_mhz", 2070.0),
+            "hbm": {"achieved_gbs": batch.alg_bytes / (ms64 * 1e-3) * 1e-9, "peak_gbs": hbm_peak,
+                    "frac": batch.alg_bytes / (ms64 * 1e-3) * 1e-9 / hbm_peak,
+                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}}
+    mixed_roof = {"bound": "hbm", "achieved": batch.alg_bytes / (msmx * 1e-3) * 1e-9,
+                  "peak": hbm_peak, "unit": "GB/s",
+                  "frac": batch.alg_bytes / (msmx * 1e-3) * 1e-9 / hbm_peak,
+                  "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+
+    # ---- oracle on the host cores (bounded sample of the same workload)
+    cpu = None
+    if not args.no_cpu_baseline:
+        idx = np.linspace(0, batch.n - 1, args.cpu_sample).astype(int)
+        host_blocks = [batch.blocks[int(i)].cpu().numpy() for i in idx]
+        rate, thr, reps = oracle_sample_rate(host_blocks, batch.dx, seconds=args.cpu_seconds)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": thr, "kind": "oracle",
+               "sample": "%d evenly spaced sub-grids of the workload, %d passes, FP64, OpenMP over "
+                         "sub-grids" % (len(idx), reps)}
+
+    value = cells * world / (ms64 * 1e-3)
+    line = {
+        "metric": "cell-updates/s (aggregated FP64 hydro RHS: PPM + Kurganov-Tadmor)",
+        "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "subgrids": batch.n, "cells": cells,
+                   "inputs_bytes": batch.blocks.numel() * 8, "l2": "inputs (7.9 GB) > L2",
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "plan_fp64": info64, "plan_mixed": infomx},
+        "e2e": {"value": cells * world / (ms_e2e * 1e-3), "unit": "cell-updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+        "gpu_launches": args.steps,
+        "roofline": roof,
+        "forms": {
+            "fp64_aggregated": {"value": value, "ms": ms64},
+            "mixed_aggregated": {"value": cells * world / (msmx * 1e-3), "ms": msmx,
+                                 "roofline": mixed_roof, "max_rel_err_vs_fp64": mixed_err,
+                                 "conservation_drift": drift},
+            "fp64_per_subgrid": {"value": cells * world / (ms_ps64 * 1e-3), "ms": ms_ps64,
+                                 "streams": args.streams, "launches": batch.n},
+            "mixed_per_subgrid": {"value": cells * world / (ms_psmx * 1e-3), "ms": ms_psmx,
+                                  "streams": args.streams, "launches": batch.n},
+        },
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--domain", type=int, default=256, help="cells per edge of the domain")
+    ap.add_argument("--streams", type=int, default=128)
+    ap.add_argument("--cpu-sample", type=int, default=2048)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch
+
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * hydro.h -- C ABI of libhydro: the aggregated per-sub-grid hydro
+ * right-hand-side (RHS) evaluation on one NVIDIA GB300 (sm_103a).
+ *
+ * The operation (Sec. IV-B of "From Task-Based GPU Work Aggregation to
+ * Stellar Mergers", Daiss et al.): for each sub-grid of an octree AMR mesh
+ * (N^3 interior cells plus a ghost layer of thickness 3, Sec. V-A), convert
+ * the conserved fields to primitives, reconstruct them on every cell face with
+ * the piecewise-parabolic method (Colella & Woodward 1984), evaluate the
+ * central(-upwind) flux of Kurganov & Tadmor with the largest local signal
+ * speed, and return the flux divergence dU/dt together with the largest
+ * signal speed (the input of the Courant condition, Sec. IV-B).  Many
+ * sub-grids are evaluated in one launch: the explicit work aggregation of
+ * Sec. V-D (strategy 3), with mixed sub-grid sizes (strategy 1, Sec. V-B).
+ *
+ * Conventions common to every entry point
+ *   - Fields, in order: 0 rho, 1-3 momentum (x, y, z), 4 total energy E,
+ *     5 entropy tracer tau = (rho e)^(1/gamma), 6.. species densities rho_k.
+ *     n_fields = 6 + species, 6 <= n_fields <= HYDRO_MAX_FIELDS.
+ *   - Input U of a sub-grid: DEVICE memory, binary64, [n_fields][G][G][G]
+ *     with G = N + 2*ghost and x fastest; 8-byte aligned.  Only the 3
+ *     innermost ghost layers are read, and of those only the cells with at
+ *     most one coordinate outside the interior.  U is never written.
+ *   - Output dU/dt: DEVICE memory, binary64, packed in descriptor order:
+ *     sub-grid s occupies n_fields_s * N_s^3 doubles ([f][z][y][x]) starting at
+ *     sum_{t<s} n_fields_t * N_t^3.  Output amax: DEVICE, one double per
+ *     sub-grid.  Both are owned by the caller and fully overwritten.
+ *   - Streams are cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Every launch entry point is asynchronous with respect to the
+ *     host.  Pointers are plain device pointers (e.g. from torch tensors).
+ *   - Return value: HYDRO_OK (0) or a negative status below.  No entry point
+ *     aborts the process or traps the GPU; device-side problems are recorded
+ *     in a per-device status word read back by hydro_status().
+ *   - Thread safety: calls from several host threads are serialised by a
+ *     library lock; a plan or server handle may be used by one thread at a
+ *     time.
+ */
+#ifndef HYDRO_H_
+#define HYDRO_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HYDRO_MAX_FIELDS 11 /* 6 + up to 5 species */
+#define HYDRO_MAX_N 256     /* largest interior edge accepted */
+
+/* status codes */
+#define HYDRO_OK 0
+#define HYDRO_EINVAL (-1)    /* bad argument: NULL pointer, N < 2, ghost < 3, n_fields out of
+                                range, gamma <= 1, dx <= 0, uniform-batch mismatch, overflow */
+#define HYDRO_ENOMEM (-2)    /* a library workspace could not be allocated */
+#define HYDRO_ECUDA (-3)     /* a CUDA runtime call failed; see hydro_last_cuda_error() */
+#define HYDRO_ENONPHYS (-4)  /* device flag: rho <= 0, p <= 0 or non-finite value read */
+#define HYDRO_EBUDGET (-5)   /* serving: the task can never fit the memory budget */
+#define HYDRO_ETIMEDOUT (-6) /* serving: the wait ran past its deadline */
+#define HYDRO_EBUSY (-7)     /* serving: queue full, try again */
+
+/* One sub-grid task.  The aggregation allocator's per-task chunk of Sec. V-D:
+ * each task brings its own input block; the library packs the outputs. */
+typedef struct {
+  const double* U; /* device, [n_fields][N+2g]^3, x fastest */
+  double dx;       /* cell width > 0 (depends on the octree level) */
+  int32_t N;       /* interior cells per edge, 2..HYDRO_MAX_N (8 and 16 are the paper's) */
+  int32_t n_fields;
+} hydro_subgrid_t;
+
+/* Arithmetic of the reconstruction and flux steps.
+ *   HYDRO_FP64: every step in binary64 (Sec. VI-A: all floating point in
+ *     double precision).
+ *   HYDRO_FP32_FLUX_FP64_ACC: primitives and the dual-energy decision as in
+ *     HYDRO_FP64 within binary32 rounding, reconstruction and flux in
+ *     binary32, flux differences and their sum carried exactly/in binary64
+ *     so that the divergence telescopes (conservation). */
+typedef enum { HYDRO_FP64 = 0, HYDRO_FP32_FLUX_FP64_ACC = 1 } hydro_precision_t;
+
+/* ---------------------------------------------------------------------------
+ * hydro_rhs -- one aggregated RHS evaluation over n_subgrids sub-grids in one
+ * fused launch (Sec. V-D), binary64, on the legacy default stream.
+ *   subgrids   HOST array of n_subgrids descriptors; copied, reusable on return
+ *   n_subgrids >= 0 (0 is a no-op)
+ *   N, n_fields  if > 0, every descriptor must match (uniform batch), else
+ *              HYDRO_EINVAL; 0 means per-descriptor values
+ *   ghost      ghost layers stored in U, >= 3 (layers beyond 3 are ignored)
+ *   gamma      ratio of specific heats, > 1
+ *   out_dUdt, out_amax  DEVICE outputs as described above
+ * Allocation: the first call on a device (and a call with a larger batch than
+ * any before) allocates library workspace; later calls allocate nothing. */
+int hydro_rhs(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t N, int32_t ghost,
+              int32_t n_fields, double gamma, double* out_dUdt, double* out_amax);
+
+/* hydro_rhs with a precision, a stream (cudaStream_t as void*) and flags
+ * (HYDRO_F_* below, 0 for defaults). */
+#define HYDRO_F_NO_STATUS 1u /* skip the nonphysical-input checks' status writes */
+int hydro_rhs_ex(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t N, int32_t ghost,
+                 int32_t n_fields, double gamma, double* out_dUdt, double* out_amax,
+                 hydro_precision_t prec, void* stream, uint32_t flags);
+
+/* The plain per-sub-grid launch form (strategy 2 of Sec. V-C): the same
+ * arithmetic as hydro_rhs_ex, but one kernel launch per sub-grid, issued
+ * round-robin over `n_streams` caller-provided streams (streams[i] as void*;
+ * n_streams >= 1).  Kept as the comparison baseline of the aggregated form.
+ * Allocation as for hydro_rhs. */
+int hydro_rhs_per_subgrid(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t ghost,
+                          double gamma, double* out_dUdt, double* out_amax,
+                          hydro_precision_t prec, void* const* streams, int32_t n_streams);
+
+/* ---------------------------------------------------------------------------
+ * Plans: a fixed batch (the descriptors, hence the input pointers, are bound
+ * at creation) whose work list is built, sorted and uploaded once, whose
+ * launch configuration is chosen by the autotuner (HYDRO_PLAN_AUTOTUNE) and
+ * whose launch is captured once in a CUDA graph and replayed by
+ * hydro_plan_execute (the aggregation region of Sec. V-D, made static).
+ * hydro_plan_create allocates (work list, tuning scratch); execute allocates
+ * nothing.  The output pointers may change between executions. */
+typedef struct hydro_plan hydro_plan_t;
+#define HYDRO_PLAN_AUTOTUNE 1u /* time candidate launch shapes and keep the fastest */
+#define HYDRO_PLAN_NO_GRAPH 2u /* launch directly instead of replaying a graph */
+
+typedef struct {
+  int64_t n_subgrids;
+  int64_t n_tiles;         /* 8^3 work tiles (a 16^3 sub-grid is 8 tiles) */
+  int64_t interior_cells;  /* sum of N^3 */
+  int64_t out_doubles;     /* packed dU/dt length */
+  int64_t alg_bytes;       /* algorithmic bytes of one execution (read region + outputs) */
+  int32_t threads_per_cta; /* chosen launch shape */
+  int32_t ctas_per_sm;
+  int32_t grid;
+  int32_t smem_bytes;
+  float tuned_ms;          /* autotuner's best time, 0 if not tuned */
+  int32_t n_candidates;    /* configurations the autotuner timed */
+} hydro_plan_info_t;
+
+int hydro_plan_create(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t ghost,
+                      double gamma, hydro_precision_t prec, uint32_t flags, void* stream,
+                      hydro_plan_t** out_plan);
+int hydro_plan_execute(hydro_plan_t* plan, double* out_dUdt, double* out_amax, void* stream);
+int hydro_plan_info(const hydro_plan_t* plan, hydro_plan_info_t* info);
+int hydro_plan_destroy(hydro_plan_t* plan);
+
+/* ---------------------------------------------------------------------------
+ * hydro_status -- synchronise `stream`, then read and clear this device's
+ * sticky status word.  Returns HYDRO_OK, or HYDRO_ENONPHYS if any launch since
+ * the last call read a nonphysical value (rho <= 0, p <= 0 or non-finite) in a
+ * sub-grid's read region; then *first_bad_subgrid (may be NULL) receives the
+ * smallest offending sub-grid index of those launches (index within its own
+ * batch).  Outputs of a flagged sub-grid are written but meaningless. */
+int hydro_status(void* stream, int64_t* first_bad_subgrid);
+
+/* Text for a status code; never NULL. */
+const char* hydro_strerror(int status);
+/* Text of the last CUDA error seen by the library on this thread's calls. */
+const char* hydro_last_cuda_error(void);
+
+/* Packed output length (doubles) of a batch; -1 on bad arguments. */
+int64_t hydro_output_doubles(const hydro_subgrid_t* subgrids, int64_t n_subgrids);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int hydro_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYDRO_H_ */

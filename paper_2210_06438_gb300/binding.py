@@ -1,0 +1,222 @@
+"""ctypes binding of libhydro (``include/hydro.h``): argument marshalling only.
+
+Every computation runs in the CUDA kernels of ``csrc/``; this module turns
+Python objects (torch tensors, ints, streams) into the plain pointers and
+sizes of the C ABI and turns status codes into exceptions.  If the shared
+library is missing the import of the functions fails loudly: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, Sequence
+
+from . import _build
+
+HYDRO_OK = 0
+HYDRO_EINVAL = -1
+HYDRO_ENOMEM = -2
+HYDRO_ECUDA = -3
+HYDRO_ENONPHYS = -4
+HYDRO_EBUDGET = -5
+HYDRO_ETIMEDOUT = -6
+HYDRO_EBUSY = -7
+HYDRO_MAX_FIELDS = 11
+HYDRO_MAX_N = 256
+
+FP64 = 0
+FP32_FLUX_FP64_ACC = 1
+PLAN_AUTOTUNE = 1
+PLAN_NO_GRAPH = 2
+F_NO_STATUS = 1
+
+#: every symbol include/hydro.h declares
+EXPORTED = (
+    "hydro_rhs", "hydro_rhs_ex", "hydro_rhs_per_subgrid", "hydro_plan_create",
+    "hydro_plan_execute", "hydro_plan_info", "hydro_plan_destroy", "hydro_status",
+    "hydro_strerror", "hydro_last_cuda_error", "hydro_output_doubles", "hydro_version",
+    "hydro_server_create", "hydro_server_submit", "hydro_server_poll", "hydro_server_wait",
+    "hydro_server_stats", "hydro_server_destroy",
+)
+
+
+class HydroError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = "%s: %s (%d)" % (where, strerror(code), code)
+        if code == HYDRO_ECUDA:
+            msg += " [%s]" % last_cuda_error()
+        super().__init__(msg)
+
+
+class Subgrid(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_void_p), ("dx", ctypes.c_double), ("N", ctypes.c_int32),
+                ("n_fields", ctypes.c_int32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_subgrids", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
+                ("interior_cells", ctypes.c_int64), ("out_doubles", ctypes.c_int64),
+                ("alg_bytes", ctypes.c_int64), ("threads_per_cta", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32), ("tuned_ms", ctypes.c_float),
+                ("n_candidates", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libhydro.  Raises if it is not built (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError("libhydro is not built (%s); run __graft_entry__.build()"
+                               % _build.LIB)
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    P = ctypes.c_void_p
+    i32, i64, dbl, u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint32
+    SG = ctypes.POINTER(Subgrid)
+    sig = {
+        "hydro_rhs": (ctypes.c_int, [SG, i64, i32, i32, i32, dbl, P, P]),
+        "hydro_rhs_ex": (ctypes.c_int, [SG, i64, i32, i32, i32, dbl, P, P, ctypes.c_int, P, u32]),
+        "hydro_rhs_per_subgrid": (ctypes.c_int, [SG, i64, i32, dbl, P, P, ctypes.c_int,
+                                                 ctypes.POINTER(P), i32]),
+        "hydro_plan_create": (ctypes.c_int, [SG, i64, i32, dbl, ctypes.c_int, u32, P,
+                                             ctypes.POINTER(P)]),
+        "hydro_plan_execute": (ctypes.c_int, [P, P, P, P]),
+        "hydro_plan_info": (ctypes.c_int, [P, ctypes.POINTER(PlanInfo)]),
+        "hydro_plan_destroy": (ctypes.c_int, [P]),
+        "hydro_status": (ctypes.c_int, [P, ctypes.POINTER(i64)]),
+        "hydro_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "hydro_last_cuda_error": (ctypes.c_char_p, []),
+        "hydro_output_doubles": (i64, [SG, i64]),
+        "hydro_version": (ctypes.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().hydro_strerror(int(code)).decode()
+
+
+def last_cuda_error() -> str:
+    return load().hydro_last_cuda_error().decode()
+
+
+def _check(rc, where):
+    if rc != HYDRO_OK:
+        raise HydroError(rc, where)
+
+
+def _ptr(x) -> int:
+    """Device pointer of a torch tensor (or an int address)."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def descriptors(items: Sequence) -> ctypes.Array:
+    """Descriptor array from (U, dx, N, n_fields) tuples; U a device tensor or address."""
+    arr = (Subgrid * max(len(items), 1))()
+    for i, (U, dx, N, F) in enumerate(items):
+        arr[i].U = _ptr(U)
+        arr[i].dx = float(dx)
+        arr[i].N = int(N)
+        arr[i].n_fields = int(F)
+    return arr
+
+
+def output_doubles(desc, n=None) -> int:
+    n = len(desc) if n is None else n
+    r = load().hydro_output_doubles(desc, n)
+    if r < 0:
+        raise HydroError(HYDRO_EINVAL, "hydro_output_doubles")
+    return int(r)
+
+
+def rhs(desc, out, amax, ghost=3, gamma=5.0 / 3.0, N=0, n_fields=0, prec=FP64, stream=None,
+        flags=0, n=None):
+    """One aggregated RHS (hydro_rhs_ex): ``desc`` from ``descriptors``."""
+    n = len(desc) if n is None else n
+    _check(load().hydro_rhs_ex(desc, n, N, ghost, n_fields, float(gamma), _ptr(out), _ptr(amax),
+                               int(prec), _stream(stream), int(flags)), "hydro_rhs_ex")
+
+
+def rhs_per_subgrid(desc, out, amax, streams: Iterable, ghost=3, gamma=5.0 / 3.0, prec=FP64,
+                    n=None):
+    """The per-sub-grid launch form (hydro_rhs_per_subgrid) over a stream pool."""
+    n = len(desc) if n is None else n
+    st = [_stream(s) for s in streams]
+    arr = (ctypes.c_void_p * len(st))(*st)
+    _check(load().hydro_rhs_per_subgrid(desc, n, ghost, float(gamma), _ptr(out), _ptr(amax),
+                                        int(prec), arr, len(st)), "hydro_rhs_per_subgrid")
+
+
+def status(stream=None):
+    """(status code, first bad sub-grid or -1); synchronises the stream."""
+    fb = ctypes.c_int64(-1)
+    rc = load().hydro_status(_stream(stream), ctypes.byref(fb))
+    if rc not in (HYDRO_OK, HYDRO_ENONPHYS):
+        raise HydroError(rc, "hydro_status")
+    return rc, int(fb.value)
+
+
+class Plan:
+    """hydro_plan_*: fixed batch, tuned launch shape, CUDA-graph replay."""
+
+    def __init__(self, desc, ghost=3, gamma=5.0 / 3.0, prec=FP64, autotune=False, graph=True,
+                 stream=None, n=None):
+        n = len(desc) if n is None else n
+        self._desc = desc  # keep the pointers' owner alive
+        h = ctypes.c_void_p()
+        flags = (PLAN_AUTOTUNE if autotune else 0) | (0 if graph else PLAN_NO_GRAPH)
+        _check(load().hydro_plan_create(desc, n, ghost, float(gamma), int(prec), flags,
+                                        _stream(stream), ctypes.byref(h)), "hydro_plan_create")
+        self._h = h
+
+    def execute(self, out, amax, stream=None):
+        _check(load().hydro_plan_execute(self._h, _ptr(out), _ptr(amax), _stream(stream)),
+               "hydro_plan_execute")
+
+    def info(self) -> dict:
+        pi = PlanInfo()
+        _check(load().hydro_plan_info(self._h, ctypes.byref(pi)), "hydro_plan_info")
+        return pi.as_dict()
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().hydro_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,338 @@
+// hydro_api.cu -- host side of libhydro: argument validation, the tile work
+// list (the aggregation allocator's chunk table of Sec. V-D), launches, plans
+// with CUDA-graph replay and autotuning, and the sticky device status word.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hydro.h"
+#include "hydro_internal.h"
+#include "hydro_kernels.cuh"
+
+using hydro_dev::Tile;
+using hydro_dev::Status;
+
+namespace hydro_host {
+
+thread_local std::string g_last_cuda_error = "no CUDA error";
+std::mutex g_lock;
+
+int cuda_fail(cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  g_last_cuda_error = buf;
+  return HYDRO_ECUDA;
+}
+
+// ------------------------------------------------------------ device ctx --
+struct DeviceCtx {
+  bool ready = false;
+  int device = -1;
+  int n_sm = 0;
+  int smem_optin = 0;
+  Status* status = nullptr;  // sticky status word (device)
+  // ring of work-list slots for the non-plan entry points
+  static constexpr int RING = 4;
+  Tile* dev_tiles[RING] = {};
+  Tile* host_tiles[RING] = {};  // pinned staging
+  size_t cap[RING] = {};
+  cudaEvent_t done[RING] = {};
+  int next = 0;
+};
+
+static DeviceCtx g_ctx[64];
+
+static const Status kStatusClear = {0u, 0u, ~0ull};
+
+int ctx_get(DeviceCtx** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return HYDRO_EINVAL;
+  DeviceCtx& c = g_ctx[dev];
+  if (!c.ready) {
+    c.device = dev;
+    if ((e = cudaDeviceGetAttribute(&c.n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return cuda_fail(e, "cudaDeviceGetAttribute(SM count)");
+    if ((e = cudaDeviceGetAttribute(&c.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+        cudaSuccess)
+      return cuda_fail(e, "cudaDeviceGetAttribute(smem)");
+    c.smem_optin -= 1024;  // room for the kernels' static shared memory
+    if ((e = cudaMalloc(&c.status, sizeof(Status))) != cudaSuccess) return HYDRO_ENOMEM;
+    if ((e = cudaMemcpy(c.status, &kStatusClear, sizeof(Status), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return cuda_fail(e, "cudaMemcpy(status)");
+    for (int i = 0; i < DeviceCtx::RING; i++)
+      if ((e = cudaEventCreateWithFlags(&c.done[i], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventCreate");
+    if ((e = kernels_init(c.smem_optin)) != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    c.ready = true;
+  }
+  *out = &c;
+  return HYDRO_OK;
+}
+
+int ctx_status_ptr(Status** st, int* n_sm, int* smem_optin) {
+  DeviceCtx* c;
+  int rc = ctx_get(&c);
+  if (rc) return rc;
+  *st = c->status;
+  *n_sm = c->n_sm;
+  *smem_optin = c->smem_optin;
+  return HYDRO_OK;
+}
+
+// --------------------------------------------------------- validation --
+int validate(const hydro_subgrid_t* sg, int64_t n, int32_t N, int32_t ghost, int32_t F,
+             double gamma) {
+  if (n < 0) return HYDRO_EINVAL;
+  if (n > 0 && !sg) return HYDRO_EINVAL;
+  if (ghost < 3 || ghost > 64) return HYDRO_EINVAL;
+  if (!(gamma > 1.0) || !std::isfinite(gamma)) return HYDRO_EINVAL;
+  if (n > (int64_t)1 << 31) return HYDRO_EINVAL;
+  for (int64_t s = 0; s < n; s++) {
+    const hydro_subgrid_t& d = sg[s];
+    if (!d.U) return HYDRO_EINVAL;
+    if (d.N < 2 || d.N > HYDRO_MAX_N) return HYDRO_EINVAL;
+    if (d.n_fields < 6 || d.n_fields > HYDRO_MAX_FIELDS) return HYDRO_EINVAL;
+    if (!(d.dx > 0.0) || !std::isfinite(d.dx)) return HYDRO_EINVAL;
+    if (N > 0 && d.N != N) return HYDRO_EINVAL;
+    if (F > 0 && d.n_fields != F) return HYDRO_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d.U) % 8 != 0) return HYDRO_EINVAL;
+  }
+  return HYDRO_OK;
+}
+
+int64_t output_doubles(const hydro_subgrid_t* sg, int64_t n) {
+  int64_t tot = 0;
+  for (int64_t s = 0; s < n; s++) tot += (int64_t)sg[s].n_fields * sg[s].N * sg[s].N * sg[s].N;
+  return tot;
+}
+
+// Work list: one Tile per 8^3 tile.  `order` (optional) permutes sub-grids.
+void build_tiles(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, std::vector<Tile>& tiles,
+                 std::vector<int64_t>* first_tile, bool sort_by_cost, int* Fmax, bool* any_multi) {
+  std::vector<int64_t> off(n + 1, 0);
+  for (int64_t s = 0; s < n; s++)
+    off[s + 1] = off[s] + (int64_t)sg[s].n_fields * sg[s].N * sg[s].N * sg[s].N;
+  std::vector<int64_t> order(n);
+  for (int64_t s = 0; s < n; s++) order[s] = s;
+  if (sort_by_cost)  // largest field count first: the longest tiles start first
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t a, int64_t b) { return sg[a].n_fields > sg[b].n_fields; });
+  tiles.clear();
+  if (first_tile) first_tile->assign(n + 1, 0);
+  *Fmax = 6;
+  *any_multi = false;
+  for (int64_t k = 0; k < n; k++) {
+    int64_t s = order[k];
+    const hydro_subgrid_t& d = sg[s];
+    int nt = (d.N + hydro_dev::TE - 1) / hydro_dev::TE;
+    bool multi = nt > 1;
+    *any_multi |= multi;
+    *Fmax = std::max(*Fmax, (int)d.n_fields);
+    if (first_tile) (*first_tile)[s] = (int64_t)tiles.size();
+    for (int tz = 0; tz < nt; tz++)
+      for (int ty = 0; ty < nt; ty++)
+        for (int tx = 0; tx < nt; tx++) {
+          Tile t;
+          memset(&t, 0, sizeof t);
+          t.U = d.U;
+          t.out_off = off[s];
+          t.inv_dx = 1.0 / d.dx;
+          t.sub = (int)s;
+          t.N = d.N;
+          t.F = d.n_fields;
+          t.G = d.N + 2 * ghost;
+          t.ghost = ghost;
+          t.ox = (short)(tx * hydro_dev::TE);
+          t.oy = (short)(ty * hydro_dev::TE);
+          t.oz = (short)(tz * hydro_dev::TE);
+          t.multi = multi ? 1 : 0;
+          tiles.push_back(t);
+        }
+  }
+  if (first_tile) (*first_tile)[n] = (int64_t)tiles.size();
+}
+
+// Copy a work list into the next ring slot, ordered after the slot's last
+// use.  Returns the device pointer in *dev.
+int stage_tiles(DeviceCtx* c, const std::vector<Tile>& tiles, cudaStream_t st, Tile** dev,
+                int* slot_out) {
+  int slot = c->next;
+  c->next = (c->next + 1) % DeviceCtx::RING;
+  cudaError_t e;
+  // the previous launch that read this slot must be done before the host
+  // staging buffer and the device copy are overwritten
+  if ((e = cudaEventSynchronize(c->done[slot])) != cudaSuccess)
+    return cuda_fail(e, "cudaEventSynchronize(ring)");
+  size_t need = std::max<size_t>(tiles.size(), 1);
+  if (need > c->cap[slot]) {
+    size_t cap = std::max<size_t>(need, 1024);
+    if (c->dev_tiles[slot]) cudaFree(c->dev_tiles[slot]);
+    if (c->host_tiles[slot]) cudaFreeHost(c->host_tiles[slot]);
+    c->dev_tiles[slot] = nullptr;
+    c->host_tiles[slot] = nullptr;
+    c->cap[slot] = 0;
+    if (cudaMalloc(&c->dev_tiles[slot], cap * sizeof(Tile)) != cudaSuccess) return HYDRO_ENOMEM;
+    if (cudaMallocHost(&c->host_tiles[slot], cap * sizeof(Tile)) != cudaSuccess) return HYDRO_ENOMEM;
+    c->cap[slot] = cap;
+  }
+  if (!tiles.empty()) {
+    memcpy(c->host_tiles[slot], tiles.data(), tiles.size() * sizeof(Tile));
+    if ((e = cudaMemcpyAsync(c->dev_tiles[slot], c->host_tiles[slot], tiles.size() * sizeof(Tile),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync(work list)");
+  }
+  *dev = c->dev_tiles[slot];
+  *slot_out = slot;
+  return HYDRO_OK;
+}
+
+}  // namespace hydro_host
+
+using namespace hydro_host;
+
+// ================================================================ C ABI ==
+extern "C" {
+
+int hydro_version(void) { return 100; }
+
+const char* hydro_strerror(int s) {
+  switch (s) {
+    case HYDRO_OK: return "ok";
+    case HYDRO_EINVAL: return "invalid argument";
+    case HYDRO_ENOMEM: return "out of device or pinned memory";
+    case HYDRO_ECUDA: return "CUDA runtime error";
+    case HYDRO_ENONPHYS: return "nonphysical input (rho <= 0, p <= 0 or non-finite)";
+    case HYDRO_EBUDGET: return "task exceeds the serving memory budget";
+    case HYDRO_ETIMEDOUT: return "timed out";
+    case HYDRO_EBUSY: return "busy";
+    default: return "unknown status";
+  }
+}
+
+const char* hydro_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+int64_t hydro_output_doubles(const hydro_subgrid_t* sg, int64_t n) {
+  if (n < 0 || (n > 0 && !sg)) return -1;
+  for (int64_t s = 0; s < n; s++)
+    if (sg[s].N < 2 || sg[s].N > HYDRO_MAX_N || sg[s].n_fields < 6 ||
+        sg[s].n_fields > HYDRO_MAX_FIELDS)
+      return -1;
+  return output_doubles(sg, n);
+}
+
+int hydro_rhs_ex(const hydro_subgrid_t* sg, int64_t n, int32_t N, int32_t ghost, int32_t F,
+                 double gamma, double* out, double* amax, hydro_precision_t prec, void* stream,
+                 uint32_t flags) {
+  int rc = validate(sg, n, N, ghost, F, gamma);
+  if (rc) return rc;
+  if (prec != HYDRO_FP64 && prec != HYDRO_FP32_FLUX_FP64_ACC) return HYDRO_EINVAL;
+  if (n == 0) return HYDRO_OK;
+  if (!out || !amax) return HYDRO_EINVAL;
+  std::lock_guard<std::mutex> g(g_lock);
+  DeviceCtx* c;
+  if ((rc = ctx_get(&c))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<Tile> tiles;
+  int Fmax;
+  bool multi;
+  build_tiles(sg, n, ghost, tiles, nullptr, true, &Fmax, &multi);
+  Tile* dt;
+  int slot;
+  if ((rc = stage_tiles(c, tiles, st, &dt, &slot))) return rc;
+  cudaError_t e;
+  if (multi && (e = cudaMemsetAsync(amax, 0, n * sizeof(double), st)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemsetAsync(amax)");
+  LaunchCfg cfg = default_cfg(prec, Fmax, c->n_sm, c->smem_optin, (int64_t)tiles.size());
+  if ((e = launch_tiles(cfg, prec, dt, (int)tiles.size(), Fmax, out, amax, c->status, gamma,
+                        !(flags & HYDRO_F_NO_STATUS), st)) != cudaSuccess)
+    return cuda_fail(e, "launch");
+  if ((e = cudaEventRecord(c->done[slot], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  return HYDRO_OK;
+}
+
+int hydro_rhs(const hydro_subgrid_t* sg, int64_t n, int32_t N, int32_t ghost, int32_t F,
+              double gamma, double* out, double* amax) {
+  return hydro_rhs_ex(sg, n, N, ghost, F, gamma, out, amax, HYDRO_FP64, nullptr, 0u);
+}
+
+int hydro_rhs_per_subgrid(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, double gamma,
+                          double* out, double* amax, hydro_precision_t prec, void* const* streams,
+                          int32_t n_streams) {
+  int rc = validate(sg, n, 0, ghost, 0, gamma);
+  if (rc) return rc;
+  if (prec != HYDRO_FP64 && prec != HYDRO_FP32_FLUX_FP64_ACC) return HYDRO_EINVAL;
+  if (n_streams < 1 || !streams) return HYDRO_EINVAL;
+  if (n == 0) return HYDRO_OK;
+  if (!out || !amax) return HYDRO_EINVAL;
+  std::lock_guard<std::mutex> g(g_lock);
+  DeviceCtx* c;
+  if ((rc = ctx_get(&c))) return rc;
+  std::vector<Tile> tiles;
+  std::vector<int64_t> first;
+  int Fmax;
+  bool multi;
+  build_tiles(sg, n, ghost, tiles, &first, false, &Fmax, &multi);
+  cudaStream_t s0 = (cudaStream_t)streams[0];
+  Tile* dt;
+  int slot;
+  if ((rc = stage_tiles(c, tiles, s0, &dt, &slot))) return rc;
+  cudaError_t e;
+  // every stream starts after the work list is on the device
+  cudaEvent_t ready = c->done[slot];
+  if ((e = cudaEventRecord(ready, s0)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  for (int i = 1; i < n_streams; i++)
+    if ((e = cudaStreamWaitEvent((cudaStream_t)streams[i], ready, 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamWaitEvent");
+  for (int64_t s = 0; s < n; s++) {
+    cudaStream_t st = (cudaStream_t)streams[s % n_streams];
+    int nt = (int)(first[s + 1] - first[s]);
+    int F = sg[s].n_fields;
+    if (nt > 1 && (e = cudaMemsetAsync(amax + s, 0, sizeof(double), st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemsetAsync(amax)");
+    LaunchCfg cfg = default_cfg(prec, F, c->n_sm, c->smem_optin, nt);
+    cfg.grid = nt;
+    if ((e = launch_tiles(cfg, prec, dt + first[s], nt, F, out, amax, c->status, gamma, 1, st)) !=
+        cudaSuccess)
+      return cuda_fail(e, "launch");
+  }
+  // the ring slot is free once every stream has finished
+  for (int i = 1; i < n_streams; i++) {
+    if ((e = cudaEventRecord(ready, (cudaStream_t)streams[i])) != cudaSuccess)
+      return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(s0, ready, 0)) != cudaSuccess) return cuda_fail(e, "wait");
+  }
+  if ((e = cudaEventRecord(ready, s0)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  return HYDRO_OK;
+}
+
+int hydro_status(void* stream, int64_t* first_bad) {
+  std::lock_guard<std::mutex> g(g_lock);
+  DeviceCtx* c;
+  int rc;
+  if ((rc = ctx_get(&c))) return rc;
+  cudaError_t e;
+  if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamSynchronize");
+  Status h;
+  if ((e = cudaMemcpy(&h, c->status, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpy(status)");
+  if ((e = cudaMemcpy(c->status, &kStatusClear, sizeof h, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpy(status clear)");
+  if (h.flags & 1u) {
+    if (first_bad) *first_bad = (int64_t)h.first_bad;
+    return HYDRO_ENONPHYS;
+  }
+  if (first_bad) *first_bad = -1;
+  return HYDRO_OK;
+}
+
+}  // extern "C"

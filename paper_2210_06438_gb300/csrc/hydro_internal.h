@@ -1,0 +1,42 @@
+// hydro_internal.h -- declarations shared by libhydro's host translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+
+#include "hydro.h"
+
+namespace hydro_dev {
+struct Tile;
+struct Status;
+}  // namespace hydro_dev
+
+namespace hydro_host {
+
+// Launch shape of the tile kernel.
+struct LaunchCfg {
+  int threads = 256;   // threads per CTA (128, 256 or 512)
+  int lch = 32;        // lines per chunk of the reconstruct/flux phases (16, 32 or 64)
+  int grid = 0;        // CTAs (persistent: a multiple of the SM count)
+  int ctas_per_sm = 1;
+  int smem = 0;        // dynamic shared memory bytes
+};
+
+cudaError_t kernels_init(int smem_optin);
+int smem_bytes(hydro_precision_t prec, int Fmax, int lch);
+int occupancy(hydro_precision_t prec, int threads, int smem);
+LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin, int64_t n_tiles);
+cudaError_t launch_tiles(const LaunchCfg& cfg, hydro_precision_t prec, const hydro_dev::Tile* tiles,
+                         int n_tiles, int Fmax, double* out, double* amax, hydro_dev::Status* status,
+                         double gamma, int write_status, cudaStream_t st);
+// kernel entry and argument block, for graph nodes
+void kernel_node(const LaunchCfg& cfg, hydro_precision_t prec, void** func);
+
+extern thread_local std::string g_last_cuda_error;
+extern std::mutex g_lock;
+int cuda_fail(cudaError_t e, const char* what);
+
+}  // namespace hydro_host

@@ -1,0 +1,79 @@
+// hydro_launch.cu -- kernel instantiations and launch shapes of libhydro.
+#include "hydro_internal.h"
+#include "hydro_kernels.cuh"
+
+namespace hydro_host {
+
+using hydro_dev::rhs_tiles_kernel;
+
+template <int MODE, int NT>
+static void* kfunc() {
+  return (void*)&rhs_tiles_kernel<MODE, NT>;
+}
+
+static void* pick(hydro_precision_t prec, int threads) {
+  int m = prec == HYDRO_FP64 ? 0 : 1;
+  switch (threads) {
+    case 128: return m ? kfunc<1, 128>() : kfunc<0, 128>();
+    case 512: return m ? kfunc<1, 512>() : kfunc<0, 512>();
+    default: return m ? kfunc<1, 256>() : kfunc<0, 256>();
+  }
+}
+
+cudaError_t kernels_init(int smem_optin) {
+  const int th[3] = {128, 256, 512};
+  for (int m = 0; m < 2; m++)
+    for (int i = 0; i < 3; i++) {
+      cudaError_t e = cudaFuncSetAttribute(pick((hydro_precision_t)m, th[i]),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
+int smem_bytes(hydro_precision_t prec, int Fmax, int lch) {
+  int es = prec == HYDRO_FP64 ? 8 : 4;
+  return es * (Fmax * hydro_dev::STAR + 2 * Fmax * lch * hydro_dev::NFC);
+}
+
+int occupancy(hydro_precision_t prec, int threads, int smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick(prec, threads), threads, smem) !=
+      cudaSuccess)
+    return 0;
+  return nb;
+}
+
+LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin,
+                      int64_t n_tiles) {
+  LaunchCfg c;
+  c.threads = 256;
+  c.lch = prec == HYDRO_FP64 ? 32 : 64;
+  c.smem = smem_bytes(prec, Fmax, c.lch);
+  while (c.smem > smem_optin && c.lch > 16) {
+    c.lch /= 2;
+    c.smem = smem_bytes(prec, Fmax, c.lch);
+  }
+  c.ctas_per_sm = occupancy(prec, c.threads, c.smem);
+  if (c.ctas_per_sm < 1) c.ctas_per_sm = 1;
+  int64_t g = (int64_t)c.ctas_per_sm * n_sm;
+  c.grid = (int)(n_tiles < g ? n_tiles : g);
+  if (c.grid < 1) c.grid = 1;
+  return c;
+}
+
+cudaError_t launch_tiles(const LaunchCfg& cfg, hydro_precision_t prec, const hydro_dev::Tile* tiles,
+                         int n_tiles, int Fmax, double* out, double* amax, hydro_dev::Status* status,
+                         double gamma, int write_status, cudaStream_t st) {
+  int lch = cfg.lch;
+  void* args[] = {(void*)&tiles, (void*)&n_tiles, (void*)&Fmax, (void*)&lch, (void*)&out,
+                  (void*)&amax, (void*)&status, (void*)&gamma, (void*)&write_status};
+  return cudaLaunchKernel(pick(prec, cfg.threads), dim3(cfg.grid), dim3(cfg.threads), args,
+                          (size_t)cfg.smem, st);
+}
+
+void kernel_node(const LaunchCfg& cfg, hydro_precision_t prec, void** func) {
+  *func = pick(prec, cfg.threads);
+}
+
+}  // namespace hydro_host

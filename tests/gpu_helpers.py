@@ -1,0 +1,110 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI
+and compare with the oracle under the tolerances the tests declare.
+
+Binary64 form (the 1e-12 gate): per sub-grid and field,
+  max_i |gpu - oracle| <= 1e-12 * max(max_i |oracle|, S_f),
+  S_f = amax * max|U_f| / dx  (a flux-divergence scale, so that exact zeros of
+  a uniform region do not divide by zero); amax within 1e-14 relative.
+
+Mixed form against the oracle's mixed mode: both take binary32 face fluxes,
+so they may differ by a few binary32 roundings of the flux magnitude:
+  max_i |gpu - oracle| <= 64 * 2^-24 * S32_f / dx,
+  S32_f = 2 amax (max|U_f| + [f in 1..4] max E)  (bound of |Fhat_f|).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+import paper_2210_06438_gb300 as hydro
+
+G53 = 5.0 / 3.0
+EPS32 = 2.0 ** -24
+
+
+def to_dev(blocks):
+    return [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in blocks]
+
+
+def run_gpu(dev_blocks, dxs, prec=hydro.FP64, ghost=3, gamma=G53, form="rhs", streams=None,
+            plan_kw=None):
+    items = []
+    for U, dx in zip(dev_blocks, dxs):
+        F = U.shape[0]
+        N = U.shape[1] - 2 * ghost
+        items.append((U, dx, N, F))
+    desc = hydro.descriptors(items)
+    n = len(items)
+    tot = hydro.output_doubles(desc, n) if n else 0
+    out = torch.full((max(tot, 1),), float("nan"), dtype=torch.float64, device="cuda")
+    amax = torch.full((max(n, 1),), float("nan"), dtype=torch.float64, device="cuda")
+    if form == "rhs":
+        hydro.rhs(desc, out, amax, ghost=ghost, gamma=gamma, prec=prec, n=n)
+    elif form == "per_subgrid":
+        hydro.rhs_per_subgrid(desc, out, amax, streams or [None], ghost=ghost, gamma=gamma,
+                              prec=prec, n=n)
+    elif form == "plan":
+        p = hydro.Plan(desc, ghost=ghost, gamma=gamma, prec=prec, n=n, **(plan_kw or {}))
+        p.execute(out, amax)
+        torch.cuda.synchronize()
+        p.close()
+    torch.cuda.synchronize()
+    res = []
+    off = 0
+    o = out.cpu().numpy()
+    for U, dx, N, F in items:
+        m = F * N ** 3
+        res.append(o[off:off + m].reshape(F, N, N, N))
+        off += m
+    return res, amax.cpu().numpy()[:n]
+
+
+def oracle_ref(blocks, dxs, mode=0, ghost=3, gamma=G53, threads=8):
+    outs, amax, flags = oracle.rhs_batch(list(blocks), gamma, np.asarray(dxs, dtype=float), mode,
+                                         ghost=ghost, threads=threads)
+    return outs, amax, flags
+
+
+def _interior_read_max(U, ghost):
+    return np.abs(U).reshape(U.shape[0], -1).max(axis=1)
+
+
+def check_fp64(got, ref, got_amax, ref_amax, blocks, dxs, tol=1e-12):
+    worst = 0.0
+    for s in range(len(ref)):
+        Umax = _interior_read_max(blocks[s], 3)
+        for f in range(ref[s].shape[0]):
+            S = ref_amax[s] * Umax[f] / dxs[s]
+            scale = max(np.abs(ref[s][f]).max(), S, 1e-300)
+            err = np.abs(got[s][f] - ref[s][f]).max() / scale
+            worst = max(worst, err)
+            assert err <= tol, ("sub-grid", s, "field", f, err)
+    rel = np.abs(got_amax - ref_amax) / np.maximum(ref_amax, 1e-300)
+    assert rel.max() <= 1e-14, rel.max()
+    return worst
+
+
+def check_mixed(got, ref, got_amax, ref_amax, blocks, dxs, ulps=64):
+    worst = 0.0
+    for s in range(len(ref)):
+        Umax = _interior_read_max(blocks[s], 3)
+        Emax = Umax[4]
+        for f in range(ref[s].shape[0]):
+            S = 2.0 * ref_amax[s] * (Umax[f] + (Emax if 1 <= f <= 4 else 0.0))
+            bound = ulps * EPS32 * S / dxs[s]
+            err = np.abs(got[s][f] - ref[s][f]).max()
+            worst = max(worst, err / bound)
+            assert err <= bound, ("sub-grid", s, "field", f, err, bound)
+    rel = np.abs(got_amax - ref_amax) / np.maximum(ref_amax, 1e-300)
+    assert rel.max() <= 1e-6, rel.max()
+    return worst
+
+
+def normwise_vs(got, ref):
+    """max over (sub-grid, field) of max|got-ref| / max|ref|."""
+    w = 0.0
+    for s in range(len(ref)):
+        for f in range(ref[s].shape[0]):
+            w = max(w, np.abs(got[s][f] - ref[s][f]).max() / max(np.abs(ref[s][f]).max(), 1e-300))
+    return w

@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs, for every workload shape and the edge cases."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2210_06438_gb300 as hydro
+import synth
+from tests import gpu_helpers as gh
+
+pytestmark = pytest.mark.gpu
+G53 = 5.0 / 3.0
+
+
+def _both(blocks, dxs, prec=hydro.FP64, **kw):
+    dev = gh.to_dev(blocks)
+    got, gam = gh.run_gpu(dev, dxs, prec=prec, **kw)
+    return got, gam
+
+
+# ------------------------------------------------------- one sub-grid --
+@pytest.mark.parametrize("nf", [6, 11])
+def test_one_subgrid_fp64(nf):
+    U, dx = synth.one_subgrid(nf=nf)
+    got, gam = _both([U], [dx])
+    ref, ram, fl = gh.oracle_ref([U], [dx])
+    assert not fl.any()
+    gh.check_fp64(got, ref, gam, ram, [U], [dx])
+    rc, bad = hydro.status()
+    assert rc == hydro.HYDRO_OK
+
+
+@pytest.mark.parametrize("nf", [6, 11])
+def test_one_subgrid_mixed(nf):
+    U, dx = synth.one_subgrid(nf=nf)
+    got, gam = _both([U], [dx], prec=hydro.FP32_FLUX_FP64_ACC)
+    ref, ram, _ = gh.oracle_ref([U], [dx], mode=1)
+    gh.check_mixed(got, ref, gam, ram, [U], [dx])
+
+
+# ------------------------------------------------------ plain domain --
+@pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
+def test_plain_aggregation_512_subgrids(prec):
+    glob = synth.plain_domain(n=64, nf=11)
+    blocks = synth.gather_blocks(glob, 8)
+    dxs = [1.0 / 64] * len(blocks)
+    got, gam = _both(list(blocks), dxs, prec=prec)
+    mode = 0 if prec == hydro.FP64 else 1
+    ref, ram, fl = gh.oracle_ref(list(blocks), dxs, mode=mode)
+    assert not fl.any()
+    if mode == 0:
+        gh.check_fp64(got, ref, gam, ram, blocks, dxs)
+    else:
+        gh.check_mixed(got, ref, gam, ram, blocks, dxs)
+        # against the binary64 oracle: the same flux-scaled binary32 bound, and a
+        # normwise cap on smooth data (the error grows with the cancellation in
+        # the flux differences, i.e. with resolution)
+        ref64, ram64, _ = gh.oracle_ref(list(blocks), dxs, mode=0)
+        gh.check_mixed(got, ref64, gam, ram64, blocks, dxs)
+        assert gh.normwise_vs(got, ref64) <= 1e-4
+    # periodic domain: the GPU result conserves every field on its own
+    tot = np.sum([o.sum(axis=(1, 2, 3)) for o in got], axis=0)
+    mag = np.sum([np.abs(o).sum(axis=(1, 2, 3)) for o in got], axis=0)
+    assert np.all(np.abs(tot) <= 1e-13 * mag)
+
+
+# ------------------------------------------------------- uneven batch --
+@pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
+def test_uneven_octree_batch(prec):
+    leaves = synth.uneven_octree(n_subgrids=48)
+    assert {l[0] for l in leaves} == {8, 16} and {l[1] for l in leaves} == {6, 11}
+    blocks = [synth.leaf_block(synth.BASE_SEED, l) for l in leaves]
+    dxs = [l[2] for l in leaves]
+    got, gam = _both(blocks, dxs, prec=prec)
+    mode = 0 if prec == hydro.FP64 else 1
+    ref, ram, _ = gh.oracle_ref(blocks, dxs, mode=mode)
+    if mode == 0:
+        gh.check_fp64(got, ref, gam, ram, blocks, dxs)
+    else:
+        gh.check_mixed(got, ref, gam, ram, blocks, dxs)
+
+
+# --------------------------------------------------------- edge cases --
+@pytest.mark.parametrize("N", [2, 3, 5, 12, 16, 17])
+def test_ragged_sizes_and_partial_tiles(N):
+    blocks = [synth.iid_block(synth.rng_for(7, N), N, 8)]
+    dxs = [0.3]
+    got, gam = _both(blocks, dxs)
+    ref, ram, _ = gh.oracle_ref(blocks, dxs)
+    gh.check_fp64(got, ref, gam, ram, blocks, dxs)
+
+
+def test_wider_ghost_layer_is_ignored_beyond_three():
+    U4 = synth.iid_block(synth.rng_for(8, 0), 8, 7, ghost=4)
+    U4[:, 0, :, :] = np.nan  # the 4th layer is never read
+    dev = gh.to_dev([U4])
+    got, gam = gh.run_gpu(dev, [0.1], ghost=4)
+    ref, ram, _ = oracle.rhs_batch([U4[:, 1:-1, 1:-1, 1:-1].copy()], G53, 0.1, 0)
+    gh.check_fp64(got, ref, gam, ram, [U4[:, 1:-1, 1:-1, 1:-1]], [0.1])
+
+
+def test_every_field_count():
+    blocks = [synth.iid_block(synth.rng_for(9, f), 8, f) for f in range(6, 12)]
+    dxs = [0.125] * len(blocks)
+    got, gam = _both(blocks, dxs)
+    ref, ram, _ = gh.oracle_ref(blocks, dxs)
+    gh.check_fp64(got, ref, gam, ram, blocks, dxs)
+
+
+def test_empty_batch_is_a_noop():
+    desc = hydro.descriptors([])
+    hydro.rhs(desc, None, None, n=0)
+
+
+def test_invalid_arguments_are_rejected():
+    U = torch.zeros(6, 14, 14, 14, dtype=torch.float64, device="cuda")
+    out = torch.empty(6 * 512, dtype=torch.float64, device="cuda")
+    am = torch.empty(1, dtype=torch.float64, device="cuda")
+    bad = [
+        dict(items=[(U, 0.1, 1, 6)]),          # N < 2
+        dict(items=[(U, 0.1, 8, 5)]),          # too few fields
+        dict(items=[(U, 0.1, 8, 12)]),         # too many fields
+        dict(items=[(U, -0.1, 8, 6)]),         # dx <= 0
+        dict(items=[(U, 0.1, 8, 6)], ghost=2),
+        dict(items=[(U, 0.1, 8, 6)], gamma=1.0),
+        dict(items=[(U, 0.1, 8, 6)], N=16),    # uniform-batch mismatch
+        dict(items=[(0, 0.1, 8, 6)]),          # NULL input
+    ]
+    for b in bad:
+        desc = hydro.descriptors(b["items"])
+        with pytest.raises(hydro.HydroError) as ei:
+            hydro.rhs(desc, out, am, ghost=b.get("ghost", 3), gamma=b.get("gamma", G53),
+                      N=b.get("N", 0))
+        assert ei.value.code == hydro.HYDRO_EINVAL
+
+
+def test_nonphysical_input_is_flagged_not_fatal():
+    blocks = synth.iid_batch(4, 8, 6, seed=21)
+    blocks[2] = blocks[2].copy()
+    blocks[2][0, 1, 6, 6] = -1.0  # negative density in a z-ghost layer of sub-grid 2
+    blocks[3] = blocks[3].copy()
+    blocks[3][0, 0, 0, 0] = np.nan  # a corner cell: outside the read region
+    hydro.status()  # clear
+    got, gam = _both(blocks, [0.1] * 4)
+    rc, bad = hydro.status()
+    assert rc == hydro.HYDRO_ENONPHYS and bad == 2
+    ref, ram, fl = gh.oracle_ref(blocks, [0.1] * 4)
+    assert fl[2] and not fl[3]
+    gh.check_fp64([got[i] for i in (0, 1, 3)], [ref[i] for i in (0, 1, 3)], gam[[0, 1, 3]],
+                  ram[[0, 1, 3]], [blocks[i] for i in (0, 1, 3)], [0.1] * 3)
+    rc, bad = hydro.status()
+    assert rc == hydro.HYDRO_OK and bad == -1
+
+
+# -------------------------------------------- forms agree bitwise --
+def test_uniform_state_gives_exact_zero_on_gpu():
+    shp = (22, 22, 22)
+    U = synth.conserved_from_states(np.full(shp, 1.3), np.full(shp, 0.2), np.full(shp, -0.1),
+                                    np.full(shp, 0.05), np.full(shp, 0.9), None)
+    for prec in (hydro.FP64, hydro.FP32_FLUX_FP64_ACC):
+        got, gam = _both([U, U[:, 4:-4, 4:-4, 4:-4].copy()], [0.1, 0.1], prec=prec)
+        assert np.all(got[0] == 0) and np.all(got[1] == 0)
+
+
+@pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
+def test_alone_in_batch_per_subgrid_and_plan_are_bitwise_equal(prec):
+    leaves = synth.uneven_octree(n_subgrids=24)
+    blocks = [synth.leaf_block(synth.BASE_SEED, l) for l in leaves]
+    dxs = [l[2] for l in leaves]
+    dev = gh.to_dev(blocks)
+    batch, bam = gh.run_gpu(dev, dxs, prec=prec)
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    per, pam = gh.run_gpu(dev, dxs, prec=prec, form="per_subgrid", streams=streams)
+    plan, plam = gh.run_gpu(dev, dxs, prec=prec, form="plan")
+    tuned, tam = gh.run_gpu(dev, dxs, prec=prec, form="plan", plan_kw={"autotune": True})
+    for s in (0, 5, 17):
+        alone, aam = gh.run_gpu([dev[s]], [dxs[s]], prec=prec)
+        assert np.array_equal(alone[0], batch[s]) and aam[0] == bam[s]
+    for other, oam in ((per, pam), (plan, plam), (tuned, tam)):
+        for s in range(len(blocks)):
+            assert np.array_equal(other[s], batch[s]), s
+        assert np.array_equal(oam, bam)
+    again, agam = gh.run_gpu(dev, dxs, prec=prec)
+    for s in range(len(blocks)):
+        assert np.array_equal(again[s], batch[s])
+
+
+# ------------------------------------- polytropes at full size, sampled --
+@pytest.mark.slow
+def test_polytropes_full_size_sampled():
+    """The 32768-sub-grid polytrope workload at full size through a tuned
+    plan (the configuration the benchmark times): sampled sub-grids against
+    the oracle, all sub-grids for conservation and finiteness."""
+    from bench import polytrope_batch
+
+    batch = polytrope_batch(n=256)
+    dxs = [batch.dx] * batch.n
+    for prec in (hydro.FP64, hydro.FP32_FLUX_FP64_ACC):
+        p = hydro.Plan(batch.desc, ghost=3, gamma=G53, prec=prec, autotune=True, n=batch.n)
+        out = torch.empty(batch.out_doubles, dtype=torch.float64, device="cuda")
+        amax = torch.empty(batch.n, dtype=torch.float64, device="cuda")
+        p.execute(out, amax)
+        rc, bad = hydro.status()
+        assert rc == hydro.HYDRO_OK
+        o = out.view(batch.n, 11, 8, 8, 8)
+        assert torch.isfinite(o).all()
+        tot = o.sum(dim=(0, 2, 3, 4)).cpu().numpy()
+        mag = o.abs().sum(dim=(0, 2, 3, 4)).cpu().numpy()
+        assert np.all(np.abs(tot) <= 1e-12 * mag), (tot, mag)
+        rng = np.random.default_rng(5)
+        sample = np.sort(rng.choice(batch.n, 96, replace=False))
+        blocks = [batch.blocks[s].cpu().numpy() for s in sample]
+        got = [o[s].cpu().numpy() for s in sample]
+        gam = amax.cpu().numpy()[sample]
+        mode = 0 if prec == hydro.FP64 else 1
+        ref, ram, fl = gh.oracle_ref(blocks, [batch.dx] * len(sample), mode=mode)
+        if mode == 0:
+            gh.check_fp64(got, ref, gam, ram, blocks, [batch.dx] * len(sample))
+        else:
+            gh.check_mixed(got, ref, gam, ram, blocks, [batch.dx] * len(sample))
+        p.close()
+        del out, amax
