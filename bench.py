@@ -175,12 +175,121 @@ def time_steps(fn, steps, warmup, stream):
     return a.elapsed_time(b) / steps
 
 
+def normwise_error(got, ref, ref_amax, batch):
+    """max over (sub-grid, field) of max|got - ref| / max(max|ref|, S), with
+    the flux-divergence floor S = amax * max|U_f| / dx of the parity tests."""
+    g = got.view(batch.n, batch.nf, -1)
+    r = ref.view(batch.n, batch.nf, -1)
+    umax = batch.blocks.abs().amax(dim=(2, 3, 4))
+    floor = ref_amax[:, None] * umax / batch.dx
+    scale = torch_max(r.abs().amax(dim=2), floor).clamp_min(1e-300)
+    return float(((g - r).abs().amax(dim=2) / scale).max())
+
+
+def torch_max(a, b):
+    import torch
+
+    return torch.maximum(a, b)
+
+
+def conservation_drift(out, batch):
+    """|sum of dU/dt| / sum |dU/dt| over the periodic domain, worst field."""
+    o = out.view(batch.n, batch.nf, -1)
+    return float((o.sum(dim=(0, 2)) / o.abs().sum(dim=(0, 2)).clamp_min(1e-300)).abs().max())
+
+
+def max_over_ranks(values, world, device="cuda"):
+    """Element-wise maximum of per-rank timings (all ranks get the result)."""
+    import torch
+
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)
     except Exception:
         return {}
+
+
+# --------------------------------------------------------------- serving --
+def serving_run(rate, duration, per_task, budget=40 << 30, n_streams=4, max_batch=4096,
+                pool_per_f=96, ring_bytes=4 << 30, seed=synth.BASE_SEED, prec=0):
+    """Replay a Poisson task stream (synth.serving_trace) through the server.
+
+    Sub-grid states live in a device pool (pool_per_f sub-grids of 8^3 for each
+    field count 6..11); each task draws its sub-grids from the pool of its field
+    count and writes into its own slice of an output ring.  Tasks are submitted
+    at their arrival times from this thread.  Returns throughput and latency
+    percentiles (completion - arrival, host monotonic clock)."""
+    import torch
+
+    import paper_2210_06438_gb300 as hydro
+
+    t_arr, sizes, nfs = synth.serving_trace(seed, rate=rate, duration=duration)
+    rng = np.random.default_rng(seed)
+    pools = {}
+    for F in range(6, 12):
+        blk = torch.empty((pool_per_f, F, 14, 14, 14), dtype=torch.float64, device="cuda")
+        for i in range(pool_per_f):
+            blk[i] = torch.from_numpy(synth.iid_block(synth.rng_for(seed, 7000 + 100 * F + i), 8, F))
+        pools[F] = blk
+    ring = torch.empty(ring_bytes // 8, dtype=torch.float64, device="cuda")
+    ring_am = torch.empty(1 << 20, dtype=torch.float64, device="cuda")
+    descs = []
+    for k in range(t_arr.size):
+        F = int(nfs[k])
+        ids = rng.integers(0, pool_per_f, int(sizes[k]))
+        descs.append(hydro.descriptors([(int(pools[F][i].data_ptr()), 1.0 / 64, 8, F) for i in ids]))
+    srv = hydro.Server(budget_bytes=budget, max_batch=max_batch, n_streams=n_streams,
+                       per_task=per_task, prec=prec)
+    off = 0
+    aoff = 0
+    slot_owner = {}
+    tickets = []
+    t0 = time.perf_counter() + 0.05
+    for k in range(t_arr.size):
+        n = int(sizes[k])
+        need = n * int(nfs[k]) * 512
+        if off + need > ring.numel():
+            off = 0
+        if aoff + n > ring_am.numel():
+            aoff = 0
+        prev = slot_owner.get(off)
+        if prev is not None:
+            srv.wait(prev)
+        while time.perf_counter() < t0 + t_arr[k]:
+            pass
+        rc, t = srv.submit(descs[k], int(ring.data_ptr()) + 8 * off, int(ring_am.data_ptr()) + 8 * aoff, n=n)
+        if rc != hydro.HYDRO_OK:
+            raise RuntimeError("submit failed: %d" % rc)
+        tickets.append((t, n))
+        slot_owner[off] = t
+        off += need
+        aoff += n
+    for t, _ in tickets:
+        srv.wait(t)
+    torch.cuda.synchronize()
+    lat, first, last, cells = [], None, None, 0
+    for t, n in tickets:
+        ts, tl, td = srv.times(t)
+        lat.append((td - ts) * 1e-3)
+        first = ts if first is None else min(first, ts)
+        last = td if last is None else max(last, td)
+        cells += n * 512
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"tasks": len(tickets), "offered_tasks_per_s": rate, "duration_s": duration,
+            "cell_updates_per_s": cells / ((last - first) * 1e-9),
+            "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+            "mean_us": float(lat.mean()), "launches": st["launches"],
+            "max_subgrids_per_launch": st["max_subgrids_per_launch"],
+            "peak_bytes_in_flight": st["peak_bytes_in_flight"], "per_task": per_task}
 
 
 # ---------------------------------------------------------- cpu baseline --
@@ -209,9 +318,11 @@ def run_reference(args, rank, world):
     import oracle
 
     oracle.build()
-    n_sample = 2048
+    n_sample = args.ref_sample
     glob = synth.polytropes(n=128, nf=11)  # same recipe, smaller domain for the sample
-    blocks = list(synth.gather_blocks(glob, 8)[:n_sample])
+    idx = np.linspace(0, (128 // 8) ** 3 - 1, n_sample).astype(int)
+    nb = 128 // 8
+    blocks = list(synth.gather_blocks(glob, 8, blocks=[(i % nb, (i // nb) % nb, i // (nb * nb)) for i in idx]))
     threads = os.cpu_count() or 1
     for _ in range(args.warmup):
         oracle.rhs_batch(blocks, GAMMA, 2.0 / 128, 0, threads=threads)
@@ -277,14 +388,12 @@ def run_ours(args, rank, world):
     if rc != hydro.HYDRO_OK:
         raise RuntimeError("nonphysical input flagged in sub-grid %d" % bad)
     out64 = out.clone()
+    amax64 = amax.clone()
+    drift64 = conservation_drift(out64, batch)
     msmx = time_steps(lambda: planmx.execute(out, amax, stream), args.steps, args.warmup, stream)
-    diff = (out - out64).view(batch.n, batch.nf, -1)
-    scale = out64.view(batch.n, batch.nf, -1).abs().amax(dim=2).clamp_min(1e-300)
-    mixed_err = float((diff.abs().amax(dim=2) / scale).max())
-    drift = out.view(batch.n, batch.nf, -1).sum(dim=(0, 2)) / \
-        out.view(batch.n, batch.nf, -1).abs().sum(dim=(0, 2)).clamp_min(1e-300)
-    drift = float(drift.abs().max())
-    del diff, scale, out64
+    mixed_err = normwise_error(out, out64, amax64, batch)
+    drift = conservation_drift(out, batch)
+    del out64
 
     # ---- per-sub-grid launch form (strategy-2 analogue), 128-stream pool
     pool = [torch.cuda.Stream(device=dev) for _ in range(args.streams)]
@@ -325,11 +434,18 @@ def run_ours(args, rank, world):
     d2h = (batch.out_doubles + batch.n) * 8
     del host_in, host_out
 
+    # ---- serving: Poisson task stream, continuous batching vs one launch per task
+    serving = None
+    if not args.no_serving:
+        serving = {
+            "aggregated": serving_run(args.rate, args.serve_seconds, per_task=False),
+            "per_task": serving_run(args.rate, args.serve_seconds, per_task=True),
+            "stress_x4_aggregated": serving_run(4 * args.rate, args.serve_seconds / 2, per_task=False),
+        }
+
     # ---- max over ranks
-    t = torch.tensor([ms64, msmx, ms_ps64, ms_psmx, ms_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms64, msmx, ms_ps64, ms_psmx, ms_e2e = [float(x) for x in t.cpu()]
+    ms64, msmx, ms_ps64, ms_psmx, ms_e2e = max_over_ranks([ms64, msmx, ms_ps64, ms_psmx, ms_e2e],
+                                                          world, device=dev)
     if rank != 0:
         return
 
@@ -377,7 +493,7 @@ def run_ours(args, rank, world):
         "gpu_launches": args.steps,
         "roofline": roof,
         "forms": {
-            "fp64_aggregated": {"value": value, "ms": ms64},
+            "fp64_aggregated": {"value": value, "ms": ms64, "conservation_drift": drift64},
             "mixed_aggregated": {"value": cells * world / (msmx * 1e-3), "ms": msmx,
                                  "roofline": mixed_roof, "max_rel_err_vs_fp64": mixed_err,
                                  "conservation_drift": drift},
@@ -388,8 +504,36 @@ def run_ours(args, rank, world):
         },
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_profile(args):
+    """A short run of one form for ncu: the tuned plan, `warmup` untimed and
+    `steps` timed executions.  Prints how many launches of the tile kernel
+    precede the timed ones (autotuner candidates x 4 + warm-ups), the value to
+    give ncu's --launch-skip."""
+    import torch
+
+    import paper_2210_06438_gb300 as hydro
+
+    hydro.load(build_if_missing=True)
+    stream = torch.cuda.current_stream()
+    batch = polytrope_batch(n=args.domain)
+    prec = hydro.FP64 if args.profile == "fp64" else hydro.FP32_FLUX_FP64_ACC
+    plan = hydro.Plan(batch.desc, ghost=3, gamma=GAMMA, prec=prec, autotune=True, stream=stream,
+                      n=batch.n)
+    info = plan.info()
+    out = torch.empty(batch.out_doubles, dtype=torch.float64, device="cuda")
+    amax = torch.empty(batch.n, dtype=torch.float64, device="cuda")
+    ms = time_steps(lambda: plan.execute(out, amax, stream), args.steps, args.warmup, stream)
+    rc, bad = hydro.status(stream)
+    print(json.dumps({"profile": args.profile, "domain": args.domain, "subgrids": batch.n,
+                      "ms": ms, "alg_bytes": batch.alg_bytes,
+                      "gbs": batch.alg_bytes / (ms * 1e-3) * 1e-9, "status": rc,
+                      "launches_before_timed": 4 * info["n_candidates"] + args.warmup,
+                      "plan": info}), flush=True)
 
 
 def main():
@@ -401,9 +545,19 @@ def main():
     ap.add_argument("--domain", type=int, default=256, help="cells per edge of the domain")
     ap.add_argument("--streams", type=int, default=128)
     ap.add_argument("--cpu-sample", type=int, default=2048)
+    ap.add_argument("--ref-sample", type=int, default=2048,
+                    help="sub-grids per step of the reference (oracle) arm")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--rate", type=float, default=20000.0, help="serving arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--profile", choices=["fp64", "mixed"], default=None,
+                    help="short run of one form for ncu (no JSON bench line)")
     args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

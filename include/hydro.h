@@ -131,6 +131,9 @@ typedef struct {
   int32_t smem_bytes;
   float tuned_ms;          /* autotuner's best time, 0 if not tuned */
   int32_t n_candidates;    /* configurations the autotuner timed */
+  int32_t lines_per_chunk; /* lines reconstructed per shared-memory chunk */
+  int32_t prefetch;        /* L2 prefetch of the next tile: 0 none, 1 per row, 2 per plane */
+  int32_t regs_cap;        /* kernel variant: 65536 / (threads * min resident CTAs) */
 } hydro_plan_info_t;
 
 int hydro_plan_create(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t ghost,
@@ -153,6 +156,70 @@ int hydro_status(void* stream, int64_t* first_bad_subgrid);
 const char* hydro_strerror(int status);
 /* Text of the last CUDA error seen by the library on this thread's calls. */
 const char* hydro_last_cuda_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop over the aggregated kernel (strategy 3 of Sec. V-D
+ * with several parent executors, combined with strategy 2).  Tasks
+ * (one or more sub-grids whose state is already resident on the device) are
+ * submitted from any host thread; a scheduler thread admits queued tasks in
+ * arrival order while the memory budget allows and a launch stream is idle,
+ * packs every admitted task's sub-grids into one work list and launches one
+ * kernel for all of them on that stream (continuous batching: tasks that
+ * arrive while other launches run join the next launch on a free stream).
+ * Completion is observed with CUDA events; latency is measured on the host
+ * monotonic clock (CLOCK_MONOTONIC nanoseconds).
+ *
+ * hydro_server_create allocates the streams, events and per-stream work-list
+ * buffers; submit and the scheduler allocate nothing unless a launch needs a
+ * larger work list than any before.  The server launches on its own streams;
+ * a task's outputs are complete when poll/wait report HYDRO_OK (the host may
+ * then read them after a device-wide or stream synchronisation of its own). */
+typedef struct hydro_server hydro_server_t;
+
+typedef struct {
+  int64_t budget_bytes;   /* admitted-and-unfinished tasks' bytes (read blocks + outputs) stay
+                             below this; a task larger than the whole budget is rejected */
+  int32_t max_batch;      /* most sub-grids per launch (the "maximum aggregated kernels" of
+                             Sec. V-D); a single larger task is launched alone */
+  int32_t n_streams;      /* launch streams, >= 1 */
+  int32_t ghost;          /* ghost layers of every submitted U, >= 3 */
+  int32_t queue_capacity; /* queued tasks before submit answers HYDRO_EBUSY, >= 1 */
+  double gamma;           /* > 1 */
+  hydro_precision_t prec;
+  int32_t per_task;       /* 1: never aggregate; one launch per task (the comparison form) */
+  int64_t dry_run_ns;     /* > 0: no GPU work at all; a launch "completes" this many ns after
+                             it starts (host-only testing of admission, order and timeouts) */
+} hydro_server_cfg_t;
+
+typedef struct {
+  int64_t submitted, completed, rejected;
+  int64_t launches, subgrids_launched, max_subgrids_per_launch;
+  int64_t bytes_in_flight, peak_bytes_in_flight;
+  int64_t queued;
+} hydro_server_stats_t;
+
+int hydro_server_create(const hydro_server_cfg_t* cfg, hydro_server_t** out_server);
+/* subgrids: HOST array of n >= 1 descriptors (copied).  out_dUdt / out_amax:
+ * DEVICE outputs of this task (packed as for hydro_rhs).  *ticket receives the
+ * task's id.  HYDRO_EBUDGET: the task alone exceeds the budget; HYDRO_EBUSY:
+ * queue full. */
+int hydro_server_submit(hydro_server_t* srv, const hydro_subgrid_t* subgrids, int32_t n,
+                        double* out_dUdt, double* out_amax, int64_t* ticket);
+/* HYDRO_OK if the task has completed, HYDRO_EBUSY if not yet, HYDRO_EINVAL for
+ * an unknown ticket; HYDRO_ECUDA if its launch failed. */
+int hydro_server_poll(hydro_server_t* srv, int64_t ticket);
+/* Block until the task completes or timeout_ns (< 0: no limit) passes; the
+ * deadline is host-side, the task itself keeps running: HYDRO_ETIMEDOUT. */
+int hydro_server_wait(hydro_server_t* srv, int64_t ticket, int64_t timeout_ns);
+/* Host monotonic times of a task: submitted, launched, completion observed
+ * (0 where not reached yet). */
+int hydro_server_times(hydro_server_t* srv, int64_t ticket, int64_t* t_submit_ns,
+                       int64_t* t_launch_ns, int64_t* t_done_ns);
+int hydro_server_stats(hydro_server_t* srv, hydro_server_stats_t* stats);
+/* Drain (wait for every admitted launch), stop the scheduler, free. */
+int hydro_server_destroy(hydro_server_t* srv);
+/* Host monotonic clock in ns, the clock of hydro_server_times. */
+int64_t hydro_now_ns(void);
 
 /* Packed output length (doubles) of a batch; -1 on bad arguments. */
 int64_t hydro_output_doubles(const hydro_subgrid_t* subgrids, int64_t n_subgrids);

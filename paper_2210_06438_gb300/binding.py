@@ -31,14 +31,6 @@ PLAN_AUTOTUNE = 1
 PLAN_NO_GRAPH = 2
 F_NO_STATUS = 1
 
-#: every symbol include/hydro.h declares
-EXPORTED = (
-    "hydro_rhs", "hydro_rhs_ex", "hydro_rhs_per_subgrid", "hydro_plan_create",
-    "hydro_plan_execute", "hydro_plan_info", "hydro_plan_destroy", "hydro_status",
-    "hydro_strerror", "hydro_last_cuda_error", "hydro_output_doubles", "hydro_version",
-    "hydro_server_create", "hydro_server_submit", "hydro_server_poll", "hydro_server_wait",
-    "hydro_server_stats", "hydro_server_destroy",
-)
 
 
 class HydroError(RuntimeError):
@@ -55,13 +47,31 @@ class Subgrid(ctypes.Structure):
                 ("n_fields", ctypes.c_int32)]
 
 
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int32),
+                ("n_streams", ctypes.c_int32), ("ghost", ctypes.c_int32),
+                ("queue_capacity", ctypes.c_int32), ("gamma", ctypes.c_double),
+                ("prec", ctypes.c_int), ("per_task", ctypes.c_int32),
+                ("dry_run_ns", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "submitted", "completed", "rejected", "launches", "subgrids_launched",
+        "max_subgrids_per_launch", "bytes_in_flight", "peak_bytes_in_flight", "queued")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class PlanInfo(ctypes.Structure):
     _fields_ = [("n_subgrids", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
                 ("interior_cells", ctypes.c_int64), ("out_doubles", ctypes.c_int64),
                 ("alg_bytes", ctypes.c_int64), ("threads_per_cta", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32), ("tuned_ms", ctypes.c_float),
-                ("n_candidates", ctypes.c_int32)]
+                ("n_candidates", ctypes.c_int32), ("lines_per_chunk", ctypes.c_int32),
+                ("prefetch", ctypes.c_int32), ("regs_cap", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -103,6 +113,15 @@ def load(build_if_missing: bool = False):
         "hydro_last_cuda_error": (ctypes.c_char_p, []),
         "hydro_output_doubles": (i64, [SG, i64]),
         "hydro_version": (ctypes.c_int, []),
+        "hydro_server_create": (ctypes.c_int, [ctypes.POINTER(ServerCfg), ctypes.POINTER(P)]),
+        "hydro_server_submit": (ctypes.c_int, [P, SG, i32, P, P, ctypes.POINTER(i64)]),
+        "hydro_server_poll": (ctypes.c_int, [P, i64]),
+        "hydro_server_wait": (ctypes.c_int, [P, i64, i64]),
+        "hydro_server_times": (ctypes.c_int, [P, i64, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                              ctypes.POINTER(i64)]),
+        "hydro_server_stats": (ctypes.c_int, [P, ctypes.POINTER(ServerStats)]),
+        "hydro_server_destroy": (ctypes.c_int, [P]),
+        "hydro_now_ns": (i64, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -220,3 +239,58 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """hydro_server_*: continuous batching of sub-grid tasks (see include/hydro.h)."""
+
+    def __init__(self, budget_bytes=40 << 30, max_batch=4096, n_streams=4, ghost=3,
+                 queue_capacity=1 << 20, gamma=5.0 / 3.0, prec=FP64, per_task=False,
+                 dry_run_ns=0):
+        cfg = ServerCfg(int(budget_bytes), int(max_batch), int(n_streams), int(ghost),
+                        int(queue_capacity), float(gamma), int(prec), 1 if per_task else 0,
+                        int(dry_run_ns))
+        h = ctypes.c_void_p()
+        _check(load().hydro_server_create(ctypes.byref(cfg), ctypes.byref(h)), "hydro_server_create")
+        self._h = h
+
+    def submit(self, desc, out, amax, n=None):
+        """Returns (status, ticket); status is HYDRO_OK, HYDRO_EBUDGET or HYDRO_EBUSY."""
+        n = len(desc) if n is None else n
+        t = ctypes.c_int64(0)
+        rc = load().hydro_server_submit(self._h, desc, n, _ptr(out), _ptr(amax), ctypes.byref(t))
+        if rc not in (HYDRO_OK, HYDRO_EBUDGET, HYDRO_EBUSY):
+            raise HydroError(rc, "hydro_server_submit")
+        return rc, int(t.value)
+
+    def poll(self, ticket):
+        return load().hydro_server_poll(self._h, int(ticket))
+
+    def wait(self, ticket, timeout_ns=-1):
+        return load().hydro_server_wait(self._h, int(ticket), int(timeout_ns))
+
+    def times(self, ticket):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().hydro_server_times(self._h, int(ticket), ctypes.byref(a), ctypes.byref(b),
+                                         ctypes.byref(c)), "hydro_server_times")
+        return a.value, b.value, c.value
+
+    def stats(self):
+        st = ServerStats()
+        _check(load().hydro_server_stats(self._h, ctypes.byref(st)), "hydro_server_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().hydro_server_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def now_ns() -> int:
+    return int(load().hydro_now_ns())

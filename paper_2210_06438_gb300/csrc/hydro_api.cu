@@ -115,6 +115,25 @@ int64_t output_doubles(const hydro_subgrid_t* sg, int64_t n) {
   return tot;
 }
 
+void fill_tile(Tile& t, const hydro_subgrid_t& d, int ghost, int64_t out_off, int64_t amax_off,
+               int sub, int tx, int ty, int tz, bool multi) {
+  memset(&t, 0, sizeof t);
+  t.U = d.U;
+  t.out_off = out_off;
+  t.amax_off = amax_off;
+  t.inv_dx = 1.0 / d.dx;
+  t.sub = sub;
+  t.N = d.N;
+  t.F = d.n_fields;
+  t.G = d.N + 2 * ghost;
+  t.ox = (short)(tx * hydro_dev::TE);
+  t.oy = (short)(ty * hydro_dev::TE);
+  t.oz = (short)(tz * hydro_dev::TE);
+  int ex2;
+  bool pow2 = std::frexp(d.dx, &ex2) == 0.5 && ex2 > -120 && ex2 < 120;
+  t.flags = (short)((multi ? 1 : 0) | (pow2 ? 2 : 0));
+}
+
 // Work list: one Tile per 8^3 tile.  `order` (optional) permutes sub-grids.
 void build_tiles(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, std::vector<Tile>& tiles,
                  std::vector<int64_t>* first_tile, bool sort_by_cost, int* Fmax, bool* any_multi) {
@@ -143,18 +162,7 @@ void build_tiles(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, std::vecto
         for (int tx = 0; tx < nt; tx++) {
           Tile t;
           memset(&t, 0, sizeof t);
-          t.U = d.U;
-          t.out_off = off[s];
-          t.inv_dx = 1.0 / d.dx;
-          t.sub = (int)s;
-          t.N = d.N;
-          t.F = d.n_fields;
-          t.G = d.N + 2 * ghost;
-          t.ghost = ghost;
-          t.ox = (short)(tx * hydro_dev::TE);
-          t.oy = (short)(ty * hydro_dev::TE);
-          t.oz = (short)(tz * hydro_dev::TE);
-          t.multi = multi ? 1 : 0;
+          fill_tile(t, d, ghost, off[s], s, (int)s, tx, ty, tz, multi);
           tiles.push_back(t);
         }
   }

@@ -19,15 +19,19 @@ namespace hydro_host {
 // Launch shape of the tile kernel.
 struct LaunchCfg {
   int threads = 256;   // threads per CTA (128, 256 or 512)
+  int minb = 1;        // kernel variant: minimum resident CTAs per SM it was compiled for
   int lch = 32;        // lines per chunk of the reconstruct/flux phases (16, 32 or 64)
   int grid = 0;        // CTAs (persistent: a multiple of the SM count)
   int ctas_per_sm = 1;
   int smem = 0;        // dynamic shared memory bytes
+  int prefetch = 0;    // L2 prefetch of the next tile: 0 none, 1 per row, 2 per plane
 };
 
 cudaError_t kernels_init(int smem_optin);
 int smem_bytes(hydro_precision_t prec, int Fmax, int lch);
-int occupancy(hydro_precision_t prec, int threads, int smem);
+int occupancy(hydro_precision_t prec, int threads, int minb, int smem);
+int num_variants();
+void variant(int i, int* threads, int* minb);
 LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin, int64_t n_tiles);
 cudaError_t launch_tiles(const LaunchCfg& cfg, hydro_precision_t prec, const hydro_dev::Tile* tiles,
                          int n_tiles, int Fmax, double* out, double* amax, hydro_dev::Status* status,

@@ -6,25 +6,36 @@ namespace hydro_host {
 
 using hydro_dev::rhs_tiles_kernel;
 
-template <int MODE, int NT>
-static void* kfunc() {
-  return (void*)&rhs_tiles_kernel<MODE, NT>;
+// Kernel variants: (threads per CTA, minimum resident CTAs per SM).  The
+// second number caps registers per thread (65536 / (threads * minb)); the
+// autotuner picks among them per batch.
+struct Variant {
+  int threads, minb;
+};
+static const Variant kVariants[] = {{256, 1}, {128, 1}, {512, 1}, {256, 2}, {128, 2}};
+static constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+template <int MODE>
+static void* kfunc(int threads, int minb) {
+  if (threads == 128) return minb == 2 ? (void*)&rhs_tiles_kernel<MODE, 128, 2> : (void*)&rhs_tiles_kernel<MODE, 128, 1>;
+  if (threads == 512) return (void*)&rhs_tiles_kernel<MODE, 512, 1>;
+  return minb == 2 ? (void*)&rhs_tiles_kernel<MODE, 256, 2> : (void*)&rhs_tiles_kernel<MODE, 256, 1>;
 }
 
-static void* pick(hydro_precision_t prec, int threads) {
-  int m = prec == HYDRO_FP64 ? 0 : 1;
-  switch (threads) {
-    case 128: return m ? kfunc<1, 128>() : kfunc<0, 128>();
-    case 512: return m ? kfunc<1, 512>() : kfunc<0, 512>();
-    default: return m ? kfunc<1, 256>() : kfunc<0, 256>();
-  }
+static void* pick(hydro_precision_t prec, int threads, int minb) {
+  return prec == HYDRO_FP64 ? kfunc<0>(threads, minb) : kfunc<1>(threads, minb);
+}
+
+int num_variants() { return kNumVariants; }
+void variant(int i, int* threads, int* minb) {
+  *threads = kVariants[i].threads;
+  *minb = kVariants[i].minb;
 }
 
 cudaError_t kernels_init(int smem_optin) {
-  const int th[3] = {128, 256, 512};
   for (int m = 0; m < 2; m++)
-    for (int i = 0; i < 3; i++) {
-      cudaError_t e = cudaFuncSetAttribute(pick((hydro_precision_t)m, th[i]),
+    for (int i = 0; i < kNumVariants; i++) {
+      cudaError_t e = cudaFuncSetAttribute(pick((hydro_precision_t)m, kVariants[i].threads, kVariants[i].minb),
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
       if (e != cudaSuccess) return e;
     }
@@ -36,9 +47,9 @@ int smem_bytes(hydro_precision_t prec, int Fmax, int lch) {
   return es * (Fmax * hydro_dev::STAR + 2 * Fmax * lch * hydro_dev::NFC);
 }
 
-int occupancy(hydro_precision_t prec, int threads, int smem) {
+int occupancy(hydro_precision_t prec, int threads, int minb, int smem) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick(prec, threads), threads, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick(prec, threads, minb), threads, smem) !=
       cudaSuccess)
     return 0;
   return nb;
@@ -48,13 +59,14 @@ LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin
                       int64_t n_tiles) {
   LaunchCfg c;
   c.threads = 256;
+  c.minb = 1;
   c.lch = prec == HYDRO_FP64 ? 32 : 64;
   c.smem = smem_bytes(prec, Fmax, c.lch);
   while (c.smem > smem_optin && c.lch > 16) {
     c.lch /= 2;
     c.smem = smem_bytes(prec, Fmax, c.lch);
   }
-  c.ctas_per_sm = occupancy(prec, c.threads, c.smem);
+  c.ctas_per_sm = occupancy(prec, c.threads, c.minb, c.smem);
   if (c.ctas_per_sm < 1) c.ctas_per_sm = 1;
   int64_t g = (int64_t)c.ctas_per_sm * n_sm;
   c.grid = (int)(n_tiles < g ? n_tiles : g);
@@ -65,15 +77,15 @@ LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin
 cudaError_t launch_tiles(const LaunchCfg& cfg, hydro_precision_t prec, const hydro_dev::Tile* tiles,
                          int n_tiles, int Fmax, double* out, double* amax, hydro_dev::Status* status,
                          double gamma, int write_status, cudaStream_t st) {
-  int lch = cfg.lch;
+  int lch = cfg.lch, pf = cfg.prefetch;
   void* args[] = {(void*)&tiles, (void*)&n_tiles, (void*)&Fmax, (void*)&lch, (void*)&out,
-                  (void*)&amax, (void*)&status, (void*)&gamma, (void*)&write_status};
-  return cudaLaunchKernel(pick(prec, cfg.threads), dim3(cfg.grid), dim3(cfg.threads), args,
+                  (void*)&amax, (void*)&status, (void*)&gamma, (void*)&write_status, (void*)&pf};
+  return cudaLaunchKernel(pick(prec, cfg.threads, cfg.minb), dim3(cfg.grid), dim3(cfg.threads), args,
                           (size_t)cfg.smem, st);
 }
 
 void kernel_node(const LaunchCfg& cfg, hydro_precision_t prec, void** func) {
-  *func = pick(prec, cfg.threads);
+  *func = pick(prec, cfg.threads, cfg.minb);
 }
 
 }  // namespace hydro_host

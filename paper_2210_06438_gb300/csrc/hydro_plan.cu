@@ -44,7 +44,8 @@ struct hydro_plan {
   Status* a_status = nullptr;
   double a_gamma = 0;
   int a_ws = 1;
-  void* args[9];
+  int a_pf = 0;
+  void* args[10];
   void* func = nullptr;
   bool use_graph = true;
   cudaGraph_t graph = nullptr;
@@ -113,6 +114,7 @@ static float time_cfg(hydro_plan* p, const LaunchCfg& c, cudaStream_t st, int re
   LaunchCfg keep = p->cfg;
   p->cfg = c;
   p->a_lch = c.lch;
+  p->a_pf = c.prefetch;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -132,6 +134,7 @@ static float time_cfg(hydro_plan* p, const LaunchCfg& c, cudaStream_t st, int re
   cudaEventDestroy(b);
   p->cfg = keep;
   p->a_lch = keep.lch;
+  p->a_pf = keep.prefetch;
   return ms;
 }
 
@@ -184,8 +187,9 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
   p->a_status = status;
   p->a_gamma = gamma;
   p->a_ws = 1;
-  void* a[9] = {&p->a_tiles, &p->a_n, &p->a_F, &p->a_lch, &p->a_out,
-                &p->a_amax, &p->a_status, &p->a_gamma, &p->a_ws};
+  p->a_pf = p->cfg.prefetch;
+  void* a[10] = {&p->a_tiles, &p->a_n, &p->a_F, &p->a_lch, &p->a_out,
+                 &p->a_amax, &p->a_status, &p->a_gamma, &p->a_ws, &p->a_pf};
   memcpy(p->args, a, sizeof a);
 
   if (flags & HYDRO_PLAN_AUTOTUNE) {
@@ -201,17 +205,18 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
     p->a_amax = am;
     float best = 1e30f;
     LaunchCfg bestc = p->cfg;
-    const int th[3] = {128, 256, 512};
     const int lc[3] = {16, 32, 64};
     int cands = 0;
-    for (int ti = 0; ti < 3; ti++)
-      for (int li = 0; li < 3; li++) {
+    for (int vi = 0; vi < num_variants(); vi++)
+      for (int li = 0; li < 3; li++)
+      for (int pf = 0; pf < 3; pf += 2) {
         LaunchCfg c;
-        c.threads = th[ti];
+        variant(vi, &c.threads, &c.minb);
         c.lch = lc[li];
+        c.prefetch = pf;
         c.smem = smem_bytes(prec, p->Fmax, c.lch);
         if (c.smem > smem_optin) continue;
-        int occ = occupancy(prec, c.threads, c.smem);
+        int occ = occupancy(prec, c.threads, c.minb, c.smem);
         if (occ < 1) continue;
         for (int k = 1; k <= occ; k++) {
           c.ctas_per_sm = k;
@@ -229,6 +234,7 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
     cudaStreamSynchronize(st);
     p->cfg = bestc;
     p->a_lch = bestc.lch;
+    p->a_pf = bestc.prefetch;
     p->info.tuned_ms = best < 1e29f ? best : 0.f;
     p->info.n_candidates = cands;
     cudaFree(o);
@@ -240,6 +246,9 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
   p->info.ctas_per_sm = p->cfg.ctas_per_sm;
   p->info.grid = p->cfg.grid;
   p->info.smem_bytes = p->cfg.smem;
+  p->info.lines_per_chunk = p->cfg.lch;
+  p->info.prefetch = p->cfg.prefetch;
+  p->info.regs_cap = 65536 / (p->cfg.threads * p->cfg.minb);
   kernel_node(p->cfg, prec, &p->func);
   p->use_graph = !(flags & HYDRO_PLAN_NO_GRAPH);
   *out_plan = p;
