@@ -57,6 +57,7 @@ extern "C" {
 #define HYDRO_EBUDGET (-5)   /* serving: the task can never fit the memory budget */
 #define HYDRO_ETIMEDOUT (-6) /* serving: the wait ran past its deadline */
 #define HYDRO_EBUSY (-7)     /* serving: queue full, try again */
+#define HYDRO_ETOOBIG (-8)   /* hydro_rhs_noalloc: more sub-grids than its fixed scratch holds */
 
 /* One sub-grid task.  The aggregation allocator's per-task chunk of Sec. V-D:
  * each task brings its own input block; the library packs the outputs. */
@@ -220,6 +221,42 @@ int hydro_server_stats(hydro_server_t* srv, hydro_server_stats_t* stats);
 int hydro_server_destroy(hydro_server_t* srv);
 /* Host monotonic clock in ns, the clock of hydro_server_times. */
 int64_t hydro_now_ns(void);
+
+/* ---------------------------------------------------------------------------
+ * hydro_rhs_noalloc -- hydro_rhs_ex for callers that cannot allocate memory.
+ * The paper has no counterpart: this is a service of the library.
+ *
+ * Who needs it: code that must not call cudaMalloc or any allocating routine
+ * -- work recorded into a CUDA graph under a capture mode that forbids
+ * allocation, real-time loops where an allocation (which may synchronise the
+ * device) is not acceptable, or processes whose device memory belongs to
+ * another allocator (a framework's caching allocator) that must not be
+ * bypassed.  hydro_rhs_ex allocates a work list on its first calls; this
+ * entry point allocates nothing, on the device or the host heap.  The caller
+ * still provides the inputs and the outputs.
+ *
+ * How: the sub-grid descriptors are copied into a fixed device array that is
+ * part of the library image (HYDRO_NOALLOC_MAX_SUBGRIDS entries, 192 KiB; it
+ * occupies device memory on every GPU that loads the library until the
+ * process exits), and the same tile kernel as hydro_rhs_ex reads them there.
+ * Results are bitwise equal to hydro_rhs_ex's for the same batch.
+ *   - Uniform batches only: N and n_fields must be > 0 and every descriptor
+ *     must match them (HYDRO_EINVAL otherwise); dx may differ per sub-grid.
+ *   - n_subgrids > HYDRO_NOALLOC_MAX_SUBGRIDS: HYDRO_ETOOBIG, nothing runs.
+ *   - The first call on a device resolves the array's device address and
+ *     sets the kernels' attributes for that device; make that first call
+ *     before any stream capture.
+ *   - Every call reuses the same array: two calls whose work overlaps on the
+ *     GPU (different streams, not ordered) race on it.  Calls on one stream,
+ *     or otherwise ordered, are safe; the descriptor array passed in may be
+ *     reused as soon as the call returns.
+ *   - Nonphysical inputs are not recorded (hydro_status does not see this
+ *     entry point's launches).
+ * Other arguments and the output layout are those of hydro_rhs_ex. */
+#define HYDRO_NOALLOC_MAX_SUBGRIDS 8192
+int hydro_rhs_noalloc(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t N,
+                      int32_t ghost, int32_t n_fields, double gamma, double* out_dUdt,
+                      double* out_amax, hydro_precision_t prec, void* stream);
 
 /* Packed output length (doubles) of a batch; -1 on bad arguments. */
 int64_t hydro_output_doubles(const hydro_subgrid_t* subgrids, int64_t n_subgrids);

@@ -22,6 +22,8 @@ HYDRO_ENONPHYS = -4
 HYDRO_EBUDGET = -5
 HYDRO_ETIMEDOUT = -6
 HYDRO_EBUSY = -7
+HYDRO_ETOOBIG = -8
+NOALLOC_MAX_SUBGRIDS = 8192
 HYDRO_MAX_FIELDS = 11
 HYDRO_MAX_N = 256
 
@@ -122,6 +124,7 @@ def load(build_if_missing: bool = False):
         "hydro_server_stats": (ctypes.c_int, [P, ctypes.POINTER(ServerStats)]),
         "hydro_server_destroy": (ctypes.c_int, [P]),
         "hydro_now_ns": (i64, []),
+        "hydro_rhs_noalloc": (ctypes.c_int, [SG, i64, i32, i32, i32, dbl, P, P, ctypes.c_int, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -186,6 +189,15 @@ def rhs(desc, out, amax, ghost=3, gamma=5.0 / 3.0, N=0, n_fields=0, prec=FP64, s
     n = len(desc) if n is None else n
     _check(load().hydro_rhs_ex(desc, n, N, ghost, n_fields, float(gamma), _ptr(out), _ptr(amax),
                                int(prec), _stream(stream), int(flags)), "hydro_rhs_ex")
+
+
+def rhs_noalloc(desc, out, amax, N, n_fields, ghost=3, gamma=5.0 / 3.0, prec=FP64, stream=None,
+                n=None):
+    """hydro_rhs_noalloc: a uniform batch evaluated without any allocation (its
+    descriptors go to a fixed device array of the library)."""
+    n = len(desc) if n is None else n
+    _check(load().hydro_rhs_noalloc(desc, n, int(N), ghost, int(n_fields), float(gamma), _ptr(out),
+                                    _ptr(amax), int(prec), _stream(stream)), "hydro_rhs_noalloc")
 
 
 def rhs_per_subgrid(desc, out, amax, streams: Iterable, ghost=3, gamma=5.0 / 3.0, prec=FP64,

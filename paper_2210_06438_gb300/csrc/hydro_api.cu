@@ -222,6 +222,7 @@ const char* hydro_strerror(int s) {
     case HYDRO_EBUDGET: return "task exceeds the serving memory budget";
     case HYDRO_ETIMEDOUT: return "timed out";
     case HYDRO_EBUSY: return "busy";
+    case HYDRO_ETOOBIG: return "batch exceeds the fixed scratch of the no-allocation entry point";
     default: return "unknown status";
   }
 }

@@ -521,14 +521,21 @@ template <int MODE> struct Prec;
 template <> struct Prec<0> { typedef double R; typedef double Acc; };
 template <> struct Prec<1> { typedef float R; typedef F2 Acc; };
 
+// Source of the tile descriptors: a prepared work list in global memory.
+struct TileList {
+  const Tile* __restrict__ tiles;
+  __device__ __forceinline__ Tile operator()(int t) const { return tiles[t]; }
+};
+
 // Shared memory (R = element type of the mode):
 //   W  [Fmax][STAR]          primitives of the read region
 //   QS [2][Fmax][lch][NFC]   left/right face states, then fluxes in place
-template <int MODE, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB)
-rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
-                 double* __restrict__ out, double* __restrict__ amax_out,
-                 Status* __restrict__ status, double gamma_d, int write_status, int prefetch) {
+// The persistent tile loop; `fetch(t)` returns tile t's descriptor.
+template <int MODE, int NT, class Fetch>
+__device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int Fmax, int lch,
+                                          double* __restrict__ out, double* __restrict__ amax_out,
+                                          Status* __restrict__ status, double gamma_d,
+                                          int write_status, int prefetch) {
   typedef typename Prec<MODE>::R R;
   typedef typename Prec<MODE>::Acc Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -544,7 +551,7 @@ rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
   constexpr int SPT = (STAR + NT - 1) / NT;          // read-region slots per thread
 
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const Tile tile = tiles[t];
+    const Tile tile = fetch(t);
     const int F = tile.F, G = tile.G, N = tile.N, gh = (tile.G - tile.N) >> 1;
     const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
     const long long plane = (long long)G * G * G;
@@ -628,7 +635,7 @@ rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
       }
     }
     bad = __syncthreads_or(bad);
-    if (prefetch && t + (int)gridDim.x < n_tiles) prefetch_tile_l2(tiles[t + gridDim.x], tid, NT, prefetch);
+    if (prefetch && t + (int)gridDim.x < n_tiles) prefetch_tile_l2(fetch(t + gridDim.x), tid, NT, prefetch);
     if (bad && tid == 0 && write_status) {
       atomicOr(&status->flags, 1u);
       atomicMin(&status->first_bad, (unsigned long long)tile.sub);
@@ -754,6 +761,15 @@ rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
     }
     __syncthreads();
   }
+}
+
+template <int MODE, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
+                 double* __restrict__ out, double* __restrict__ amax_out,
+                 Status* __restrict__ status, double gamma_d, int write_status, int prefetch) {
+  tile_loop<MODE, NT>(TileList{tiles}, n_tiles, Fmax, lch, out, amax_out, status, gamma_d,
+                      write_status, prefetch);
 }
 
 }  // namespace hydro_dev
