@@ -25,7 +25,7 @@
 // about 2 operations per SM per clock (1/64 of binary32), so the binary64 form
 // is bound by that pipe: comparisons, absolute values, minima, sign tests and
 // scalings by powers of two run on the integer pipe on the bit patterns, and
-// the flux is written in an algebraically reduced form (see kt_face64).
+// the flux is written in an algebraically reduced form (see kt_hydro64).
 //
 // MODE 1 (mixed) converts the binary64 inputs to binary32 with integer
 // operations, forms primitives in binary32 (the dual-energy decision and the
@@ -224,12 +224,16 @@ __device__ __forceinline__ bool prim64(const double* u, double gamma, bool g53, 
 // PPM along one line of LL cells (Colella & Woodward 1984): monotonised
 // central slopes, 4th-order face values, parabola limiter.  Produces the
 // states on both sides of the NFC faces i-1/2, i = 0..TE:
-//   left[i] = q+ of cell i-1,  right[i] = q- of cell i.
-// The parabola tests D*m > D^2/6 and D*m < -D^2/6 (m = q - (q- + q+)/2,
-// D = q+ - q-) are evaluated as (D X) vs +-(D D/3) with X = 2m; the limiter is
-// continuous at both switching surfaces, so the different rounding of the
-// tests moves results by rounding errors only.
-__device__ __forceinline__ void ppm_line64(const double* q, double* left, double* right) {  // left/right: shared memory
+//   left[i] = q+ of cell i-1,  right[i] = q- of cell i   (shared memory).
+// With up = q+ - q and dn = q - q- (same sign s, else the cell is an
+// extremum and flattened), m = q - (q- + q+)/2 = (dn - up)/2 and D = up + dn,
+// the parabola tests become sign tests:
+//   D m >  D^2/6  <=>  s (dn - 2 up) > 0   ->  q- = q - 2 up  (= 3q - 2q+)
+//   D m < -D^2/6  <=>  s (2 dn - up) < 0   ->  q+ = q + 2 dn  (= 3q - 2q-)
+// The limiter is continuous at both switching surfaces, so evaluating the
+// tests with different rounding than the reference moves results by
+// rounding errors only.
+__device__ __forceinline__ void ppm_line64(const double* q, double* left, double* right) {
   double dq[LL - 1];
 #pragma unroll
   for (int c = 0; c < LL - 1; c++) dq[c] = q[c + 1] - q[c];
@@ -241,7 +245,7 @@ __device__ __forceinline__ void ppm_line64(const double* q, double* left, double
     double m = dminp(dabs(dbar), dtwice(dminp(dabs(dm), dabs(dp))));
     del[c] = dsame(dp, dm) ? dcopysign(m, dbar) : 0.0;
   }
-  const double sixth = 1.0 / 6.0, third = 1.0 / 3.0;
+  const double sixth = 1.0 / 6.0;
   double fc[LL];
 #pragma unroll
   for (int c = 1; c <= LL - 3; c++) fc[c] = fma(del[c] - del[c + 1], sixth, dhalf(q[c] + q[c + 1]));
@@ -250,12 +254,10 @@ __device__ __forceinline__ void ppm_line64(const double* q, double* left, double
     double qc = q[c], lo = fc[c - 1], hi = fc[c];
     double up = hi - qc, dn = qc - lo;
     bool ext = !dsame(up, dn);
-    double D = up + dn;
-    double X = dn - up;
-    double Y = D * X;
-    double Z = D * (D * third);
-    bool A = dgt(Y, Z);
-    bool B = !A && dgt(-Z, Y);
+    double t1 = fma(-2.0, up, dn);  // dn - 2 up
+    double t2 = fma(2.0, dn, -up);  // 2 dn - up
+    bool A = dsame(t1, up);
+    bool B = !A && dsame(-t2, up);
     double lo2 = fma(-2.0, up, qc);
     double hi2 = fma(2.0, dn, qc);
     lo = ext ? qc : (A ? lo2 : lo);
@@ -274,10 +276,11 @@ __device__ __forceinline__ void ppm_line64(const double* q, double* left, double
 //   Fhat_q = (q_l g_l + q_r g_r)/2,  g_l = rho_l (u_l + a),  g_r = rho_r (u_r - a),
 // plus the pressure terms for momentum and energy.  Mathematically identical
 // to the definition; rounding differs by a few ulps of the flux magnitude.
-// Writes Fhat_f to fout[f*fstride]; returns a.
-__device__ __forceinline__ double kt_face64(const double* wl, const double* wr, int F, int d,
-                                            double gamma, double inv_gm1, double* fout,
-                                            int fstride) {
+// w: (rho, vx, vy, vz, p) on each side.  Writes the five hydro fluxes to
+// fout[f*fstride], returns a and the two g factors the passive fields use.
+__device__ __forceinline__ double kt_hydro64(const double* wl, const double* wr, int d,
+                                             double gamma, double inv_gm1, double* fout,
+                                             int fstride, double& gl, double& gr) {
   double rl = wl[0], rr = wr[0], pl = wl[4], pr = wr[4];
   double ul = d == 0 ? wl[1] : (d == 1 ? wl[2] : wl[3]);
   double ur = d == 0 ? wr[1] : (d == 1 ? wr[2] : wr[3]);
@@ -290,7 +293,8 @@ __device__ __forceinline__ double kt_face64(const double* wl, const double* wr, 
   double cr = gpr * rsqrt64(gpr * rr);
   double a = dmaxp(dabs(ul) + cl, dabs(ur) + cr);
   double hl = ul + a, hr = ur - a;
-  double gl = rl * hl, gr = rr * hr;
+  gl = rl * hl;
+  gr = rr * hr;
   fout[0] = dhalf(gl + gr);
   double pp = pl + pr;
 #pragma unroll
@@ -299,9 +303,6 @@ __device__ __forceinline__ double kt_face64(const double* wl, const double* wr, 
     fout[(1 + c) * fstride] = dhalf(c == d ? t + pp : t);
   }
   fout[4 * fstride] = dhalf(fma(El, hl, fma(pl, ul, fma(Er, hr, pr * ur))));
-#pragma unroll
-  for (int f = 5; f < MAXF; f++)
-    if (f < F) fout[f * fstride] = dhalf(fma(wl[f], gl, wr[f] * gr));
   return a;
 }
 
@@ -383,7 +384,11 @@ __device__ __forceinline__ bool prim_mixed(const double* u, double gamma, float 
 }
 
 // ------------------------------------------------------ step A2, mixed --
-__device__ __forceinline__ void ppm_line32(const float* q, float* left, float* right) {  // left/right: shared memory
+// The same steps as ppm_line64 in binary32.
+__device__ __forceinline__ bool fsame(float a, float b) {  // a*b > 0, on the signs
+  return ((__float_as_int(a) ^ __float_as_int(b)) >= 0) && a != 0.0f && b != 0.0f;
+}
+__device__ __forceinline__ void ppm_line32(const float* q, float* left, float* right) {
   float dq[LL - 1];
 #pragma unroll
   for (int c = 0; c < LL - 1; c++) dq[c] = q[c + 1] - q[c];
@@ -393,8 +398,7 @@ __device__ __forceinline__ void ppm_line32(const float* q, float* left, float* r
     float dp = dq[c], dm = dq[c - 1];
     float dbar = 0.5f * (q[c + 1] - q[c - 1]);
     float m = fminf(fabsf(dbar), 2.0f * fminf(fabsf(dm), fabsf(dp)));
-    bool mono = ((__float_as_int(dp) ^ __float_as_int(dm)) >= 0) && dp != 0.0f && dm != 0.0f;
-    del[c] = mono ? copysignf(m, dbar) : 0.0f;
+    del[c] = fsame(dp, dm) ? copysignf(m, dbar) : 0.0f;
   }
   float fc[LL];
 #pragma unroll
@@ -403,11 +407,10 @@ __device__ __forceinline__ void ppm_line32(const float* q, float* left, float* r
   for (int c = 2; c <= LL - 3; c++) {
     float qc = q[c], lo = fc[c - 1], hi = fc[c];
     float up = hi - qc, dn = qc - lo;
-    bool ext = !(((__float_as_int(up) ^ __float_as_int(dn)) >= 0) && up != 0.0f && dn != 0.0f);
-    float D = up + dn, X = dn - up;
-    float Y = D * X, Z = D * (D * (1.0f / 3.0f));
-    bool A = Y > Z;
-    bool B = !A && Y < -Z;
+    bool ext = !fsame(up, dn);
+    float t1 = fmaf(-2.0f, up, dn), t2 = fmaf(2.0f, dn, -up);
+    bool A = fsame(t1, up);
+    bool B = !A && fsame(-t2, up);
     float lo2 = fmaf(-2.0f, up, qc), hi2 = fmaf(2.0f, dn, qc);
     lo = ext ? qc : (A ? lo2 : lo);
     hi = ext ? qc : (B ? hi2 : hi);
@@ -418,8 +421,9 @@ __device__ __forceinline__ void ppm_line32(const float* q, float* left, float* r
 }
 
 // ------------------------------------------------------ step A3, mixed --
-__device__ __forceinline__ float kt_face32(const float* wl, const float* wr, int F, int d,
-                                           float gamma, float inv_gm1, float* fout, int fstride) {
+__device__ __forceinline__ float kt_hydro32(const float* wl, const float* wr, int d, float gamma,
+                                            float inv_gm1, float* fout, int fstride, float& gl,
+                                            float& gr) {
   float rl = wl[0], rr = wr[0], pl = wl[4], pr = wr[4];
   float ul = d == 0 ? wl[1] : (d == 1 ? wl[2] : wl[3]);
   float ur = d == 0 ? wr[1] : (d == 1 ? wr[2] : wr[3]);
@@ -432,7 +436,8 @@ __device__ __forceinline__ float kt_face32(const float* wl, const float* wr, int
   float cr = gpr * rsqrtf(gpr * rr);
   float a = fmaxf(fabsf(ul) + cl, fabsf(ur) + cr);
   float hl = ul + a, hr = ur - a;
-  float gl = rl * hl, gr = rr * hr;
+  gl = rl * hl;
+  gr = rr * hr;
   fout[0] = 0.5f * (gl + gr);
   float pp = pl + pr;
 #pragma unroll
@@ -441,9 +446,6 @@ __device__ __forceinline__ float kt_face32(const float* wl, const float* wr, int
     fout[(1 + c) * fstride] = 0.5f * (c == d ? t + pp : t);
   }
   fout[4 * fstride] = 0.5f * fmaf(El, hl, fmaf(pl, ul, fmaf(Er, hr, pr * ur)));
-#pragma unroll
-  for (int f = 5; f < MAXF; f++)
-    if (f < F) fout[f * fstride] = 0.5f * fmaf(wl[f], gl, wr[f] * gr);
   return a;
 }
 
@@ -527,12 +529,185 @@ struct TileList {
   __device__ __forceinline__ Tile operator()(int t) const { return tiles[t]; }
 };
 
-// Shared memory (R = element type of the mode):
-//   W  [Fmax][STAR]          primitives of the read region
-//   QS [2][Fmax][lch][NFC]   left/right face states, then fluxes in place
-// The persistent tile loop; `fetch(t)` returns tile t's descriptor.
-template <int MODE, int NT, class Fetch>
-__device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int Fmax, int lch,
+// Addressing of line l along direction d in the read-region layout: three
+// segments (3 low ghosts, TE interior cells, 3 high ghosts), each with a
+// base slot and a constant stride.
+struct LineAddr {
+  int lo, in, hi, sg, si;
+  __device__ __forceinline__ int at(int c) const {
+    return c < 3 ? lo + c * sg : (c < 3 + TE ? in + (c - 3) * si : hi + (c - 3 - TE) * sg);
+  }
+};
+__device__ __forceinline__ LineAddr line_addr(int d, int l) {
+  int a = l % TE, b = l / TE;
+  if (d == 0) {
+    int base = (b * TE + a) * LL;
+    return {base, base + 3, base + 3 + TE, 1, 1};
+  }
+  if (d == 1)
+    return {XROWS + b * 6 * TE + a, b * TE * LL + a + 3, XROWS + b * 6 * TE + 3 * TE + a, TE, LL};
+  return {XROWS + YSLAB + b * TE + a, b * LL + a + 3, XROWS + YSLAB + 3 * TE * TE + b * TE + a,
+          TE * TE, TE * LL};
+}
+
+constexpr int NHYD = 5;  // hydro group: rho, vx, vy, vz, p
+constexpr int NW = 6;    // primitive slots in shared memory
+
+// Shared memory of one CTA (R = element type of the mode):
+//   W  [NW][STAR]           primitives of the read region: hydro group in
+//                           slots 0-4 and phi = tau/rho in slot 5; after the
+//                           hydro pass the species overwrite slots 0..
+//   RR [STAR]               1/rho of every read cell
+//   GG [3][NLN][NFC][2]     per face the factors g_l, g_r of the passive fluxes
+//   QS [2][NW][lch][NFC]    face states of a chunk of lines, then its fluxes
+template <int MODE>
+__host__ __device__ constexpr size_t smem_layout_bytes(int lch) {
+  return (MODE == 0 ? 8 : 4) *
+         ((size_t)NW * STAR + STAR + 3 * NLN * NFC * 2 + 2 * (size_t)NW * lch * NFC);
+}
+
+// One pass of steps A2-A4 over a group of `nf` fields for all three
+// directions.  HYD: the hydro group (flux of Kurganov-Tadmor, records g_l,
+// g_r and the signal speed); else the passive group (flux from g_l, g_r).
+// slot(j): shared-memory slot of group field j.  acc[k][j] receives, for the
+// thread's owned cells k, the sum of the flux differences x, then y, then z.
+template <int MODE, int NT, bool HYD, class Slot>
+__device__ __forceinline__ void group_pass(const typename Prec<MODE>::R* W, typename Prec<MODE>::R* GG,
+                                           typename Prec<MODE>::R* QS, int lch, int nf, Slot slot,
+                                           int ex, int ey, int ez, typename Prec<MODE>::R gamma,
+                                           typename Prec<MODE>::R inv_gm1,
+                                           typename Prec<MODE>::Acc (&acc)[(TE * TE * TE + NT - 1) / NT][NW],
+                                           typename Prec<MODE>::R& amax) {
+  typedef typename Prec<MODE>::R R;
+  constexpr int CPT = (TE * TE * TE + NT - 1) / NT;
+  const int tid = threadIdx.x;
+  const int fs = lch * NFC;  // field stride of QS
+  R* QR = QS + NW * fs;      // right states
+  for (int d = 0; d < 3; d++) {
+    const int e_d = d == 0 ? ex : (d == 1 ? ey : ez);
+    const int e_a = d == 0 ? ey : ex;  // first tangential axis extent
+    const int e_b = d == 2 ? ey : ez;  // second tangential axis extent
+    R* gg = GG + d * NLN * NFC * 2;
+    for (int l0 = 0; l0 < NLN; l0 += lch) {
+      // ---- A2: PPM per (line, field)
+      for (int task = tid; task < lch * nf; task += NT) {
+        int ll = task % lch, j = task / lch;
+        LineAddr la = line_addr(d, l0 + ll);
+        const R* w = W + slot(j) * STAR;
+        R q[LL];
+#pragma unroll
+        for (int c = 0; c < LL; c++) q[c] = w[la.at(c)];
+        if constexpr (MODE == 0) ppm_line64(q, QS + j * fs + ll * NFC, QR + j * fs + ll * NFC);
+        else ppm_line32(q, QS + j * fs + ll * NFC, QR + j * fs + ll * NFC);
+      }
+      __syncthreads();
+      // ---- A3: flux per face, written over the left states
+      for (int task = tid; task < lch * NFC; task += NT) {
+        int ll = task / NFC, i = task - ll * NFC;
+        int l = l0 + ll;
+        R* fo = QS + ll * NFC + i;
+        const R* fr = QR + ll * NFC + i;
+        R* g = gg + (l * NFC + i) * 2;
+        if constexpr (HYD) {
+          R wl[NHYD], wr[NHYD], gl, gr;
+#pragma unroll
+          for (int f = 0; f < NHYD; f++) {
+            wl[f] = fo[f * fs];
+            wr[f] = fr[f * fs];
+          }
+          R a;
+          if constexpr (MODE == 0) a = kt_hydro64(wl, wr, d, gamma, inv_gm1, fo, fs, gl, gr);
+          else a = kt_hydro32(wl, wr, d, gamma, inv_gm1, fo, fs, gl, gr);
+          g[0] = gl;
+          g[1] = gr;
+          bool fvalid = (l % TE) < e_a && (l / TE) < e_b && i <= e_d;
+          if constexpr (MODE == 0) {
+            if (fvalid) amax = dmaxp(amax, a);
+          } else {
+            if (fvalid) amax = fmaxf(amax, a);
+          }
+        } else {
+          R gl = g[0], gr = g[1];
+#pragma unroll
+          for (int j = 0; j < NW; j++)
+            if (j < nf) {
+              if constexpr (MODE == 0) fo[j * fs] = dhalf(fma(fo[j * fs], gl, fr[j * fs] * gr));
+              else fo[j * fs] = 0.5f * fmaf(fo[j * fs], gl, fr[j * fs] * gr);
+            }
+        }
+      }
+      __syncthreads();
+      // ---- A4: flux differences into the owned cells, x then y then z
+#pragma unroll
+      for (int k = 0; k < CPT; k++) {
+        int m = tid + k * NT;
+        if (m < TE * TE * TE) {
+          int x = m % TE, y = (m / TE) % TE, z = m / (TE * TE);
+          int l = d == 0 ? z * TE + y : (d == 1 ? z * TE + x : y * TE + x);
+          int pos = d == 0 ? x : (d == 1 ? y : z);
+          if (l >= l0 && l < l0 + lch) {
+            const R* fl = QS + (l - l0) * NFC + pos;
+#pragma unroll
+            for (int j = 0; j < NW; j++)
+              if (j < nf) {
+                R hi = fl[j * fs + 1], lo = fl[j * fs];
+                if constexpr (MODE == 0) {
+                  acc[k][j] = d == 0 ? hi - lo : acc[k][j] + (hi - lo);
+                } else {
+                  acc_pair(acc[k][j], hi, lo, d == 0);
+                }
+              }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Store dU/dt = -(sum of differences)/dx of a group's fields.
+template <int MODE, int NT>
+__device__ __forceinline__ void store_group(double* __restrict__ out, const Tile& tile, int ex,
+                                            int ey, int ez, int f0, int nf,
+                                            const typename Prec<MODE>::Acc (&acc)[(TE * TE * TE + NT - 1) / NT][NW]) {
+  constexpr int CPT = (TE * TE * TE + NT - 1) / NT;
+  const int tid = threadIdx.x, N = tile.N;
+  const long long n3 = (long long)N * N * N;
+  const double scale = -tile.inv_dx;
+  const bool pow2 = (tile.flags & 2) != 0;
+#pragma unroll
+  for (int k = 0; k < CPT; k++) {
+    int m = tid + k * NT;
+    if (m < TE * TE * TE) {
+      int x = m % TE, y = (m / TE) % TE, z = m / (TE * TE);
+      if (x < ex && y < ey && z < ez) {
+        double* o = out + tile.out_off + f0 * n3 +
+                    ((long long)(tile.oz + z) * N + (tile.oy + y)) * N + (tile.ox + x);
+#pragma unroll
+        for (int j = 0; j < NW; j++)
+          if (j < nf) {
+            double v;
+            if constexpr (MODE == 0) {
+              v = acc[k][j] * scale;
+            } else {
+              if (pow2) {  // scaling by a power of two is exact in binary32
+                float sf = (float)scale;
+                v = f2d_int(acc[k][j].h * sf) + f2d_int(acc[k][j].l * sf);
+              } else {
+                v = (f2d_int(acc[k][j].h) + f2d_int(acc[k][j].l)) * scale;
+              }
+            }
+            o[j * n3] = v;
+          }
+      }
+    }
+  }
+}
+
+// The persistent tile loop; `fetch(t)` returns tile t's descriptor; KC read-
+// region slots of a thread are loaded per batch.
+template <int MODE, int NT, int KC, class Fetch>
+__device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int lch,
                                           double* __restrict__ out, double* __restrict__ amax_out,
                                           Status* __restrict__ status, double gamma_d,
                                           int write_status, int prefetch) {
@@ -540,7 +715,9 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int F
   typedef typename Prec<MODE>::Acc Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* W = reinterpret_cast<R*>(smem_raw);
-  R* QS = W + (size_t)Fmax * STAR;
+  R* RR = W + NW * STAR;
+  R* GG = RR + STAR;
+  R* QS = GG + 3 * NLN * NFC * 2;
   __shared__ double red[NT / 32];
   const int tid = threadIdx.x;
   const R gamma = R(gamma_d);
@@ -556,194 +733,109 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int F
     const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
     const long long plane = (long long)G * G * G;
 
-    // ---- A0/A1: stage the read region as primitives.  Two passes over the
-    // thread's slots (hydro fields, then species); in each pass every load is
-    // issued before any result is used.
+    // ---- A0/A1 (hydro fields): stage rho, s, E, tau as primitives.  In each
+    // batch every load is issued before any result is used.
+    // offset of read-region slot s within a field of the stored block; -1 if
+    // the slot is outside the (possibly partial) tile's read region: at most
+    // one coordinate outside the tile, and that one at most 3 cells out
+    auto slot_offset = [&](int s) -> int {
+      int x, y, z;
+      cell_of(s < STAR ? s : 0, x, y, z);
+      int outside = (x < 0 || x >= ex) + (y < 0 || y >= ey) + (z < 0 || z >= ez);
+      bool valid = s < STAR && outside <= 1 && x < ex + 3 && y < ey + 3 && z < ez + 3;
+      return valid ? ((tile.oz + z + gh) * G + (tile.oy + y + gh)) * G + (tile.ox + x + gh) : -1;
+    };
     bool bad = false;
-    {
-      int off[SPT];
-      bool valid[SPT];
 #pragma unroll
-      for (int k = 0; k < SPT; k++) {
-        int s = tid + k * NT;
-        int x, y, z;
-        cell_of(s < STAR ? s : 0, x, y, z);
-        // read region of a (possibly partial) tile: at most one coordinate
-        // outside the tile, and that one at most 3 cells out
-        int outside = (x < 0 || x >= ex) + (y < 0 || y >= ey) + (z < 0 || z >= ez);
-        valid[k] = s < STAR && outside <= 1 && x < ex + 3 && y < ey + 3 && z < ez + 3;
-        off[k] = ((tile.oz + z + gh) * G + (tile.oy + y + gh)) * G + (tile.ox + x + gh);
+    for (int k0 = 0; k0 < SPT; k0 += KC) {
+      double u[KC][6];
+      int off[KC];
+#pragma unroll
+      for (int kk = 0; kk < KC; kk++) {
+        off[kk] = slot_offset(tid + (k0 + kk) * NT);
+#pragma unroll
+        for (int f = 0; f < 6; f++)
+          if (k0 + kk < SPT && off[kk] >= 0) u[kk][f] = __ldg(tile.U + f * plane + off[kk]);
       }
-      R rr[SPT];
-      constexpr int KC = 4;  // slots per load batch
+#pragma unroll
+      for (int kk = 0; kk < KC; kk++) {
+        int k = k0 + kk;
+        int s = tid + k * NT;
+        if (k >= SPT || s >= STAR) continue;
+        R w[6], r;
+        if (off[kk] >= 0) {
+          if constexpr (MODE == 0) bad |= prim64(u[kk], gamma_d, g53, w, r);
+          else bad |= prim_mixed(u[kk], gamma_d, gm1f, g53, w, r);
+        } else {
+#pragma unroll
+          for (int f = 0; f < 6; f++) w[f] = (f == 0 || f == 4) ? R(1) : R(0);
+          r = R(1);
+        }
+#pragma unroll
+        for (int f = 0; f < 6; f++) W[f * STAR + s] = w[f];
+        RR[s] = r;
+      }
+    }
+    bad = __syncthreads_or(bad);
+    if (prefetch && t + (int)gridDim.x < n_tiles) prefetch_tile_l2(fetch(t + gridDim.x), tid, NT, prefetch);
+
+    // ---- hydro group: rho, momentum, E
+    R amax = R(0);
+    {
+      Acc acc[CPT][NW];
+      group_pass<MODE, NT, true>(W, GG, QS, lch, NHYD, [](int j) { return j; }, ex, ey, ez, gamma,
+                                 inv_gm1, acc, amax);
+      store_group<MODE, NT>(out, tile, ex, ey, ez, 0, NHYD, acc);
+    }
+
+    // ---- A0/A1 (species): X_k = rho_k / rho into slots 0 .. F-7
+    const int nsp = F - 6;
+    if (nsp > 0) {
 #pragma unroll
       for (int k0 = 0; k0 < SPT; k0 += KC) {
-        double u[KC][6];
+        double v[KC][MAXF - 6];
+        int off[KC];
 #pragma unroll
-        for (int kk = 0; kk < KC; kk++)
+        for (int kk = 0; kk < KC; kk++) {
+          off[kk] = slot_offset(tid + (k0 + kk) * NT);
 #pragma unroll
-          for (int f = 0; f < 6; f++)
-            if (k0 + kk < SPT && valid[k0 + kk]) u[kk][f] = __ldg(tile.U + f * plane + off[k0 + kk]);
+          for (int f = 0; f < MAXF - 6; f++)
+            if (k0 + kk < SPT && off[kk] >= 0 && f < nsp)
+              v[kk][f] = __ldg(tile.U + (6 + f) * plane + off[kk]);
+        }
 #pragma unroll
         for (int kk = 0; kk < KC; kk++) {
           int k = k0 + kk;
           int s = tid + k * NT;
           if (k >= SPT || s >= STAR) continue;
-          R w[6];
-          if (valid[k]) {
-            if constexpr (MODE == 0) {
-              bad |= prim64(u[kk], gamma_d, g53, w, rr[k]);
-            } else {
-              bad |= prim_mixed(u[kk], gamma_d, gm1f, g53, w, rr[k]);
-            }
-          } else {
+          R r = RR[s];
 #pragma unroll
-            for (int f = 0; f < 6; f++) w[f] = (f == 0 || f == 4) ? R(1) : R(0);
-            rr[k] = R(1);
-          }
-#pragma unroll
-          for (int f = 0; f < 6; f++) W[f * STAR + s] = w[f];
-        }
-      }
-      if (F > 6) {
-#pragma unroll
-        for (int k0 = 0; k0 < SPT; k0 += KC) {
-          double v[KC][MAXF - 6];
-#pragma unroll
-          for (int kk = 0; kk < KC; kk++)
-#pragma unroll
-            for (int f = 6; f < MAXF; f++)
-              if (k0 + kk < SPT && valid[k0 + kk] && f < F)
-                v[kk][f - 6] = __ldg(tile.U + f * plane + off[k0 + kk]);
-#pragma unroll
-          for (int kk = 0; kk < KC; kk++) {
-            int k = k0 + kk;
-            int s = tid + k * NT;
-            if (k >= SPT || s >= STAR) continue;
-#pragma unroll
-            for (int f = 6; f < MAXF; f++)
-              if (f < F) {
-                R x = R(0);
-                if (valid[k]) {
-                  bad |= !dfinite(v[kk][f - 6]);
-                  if constexpr (MODE == 0) x = v[kk][f - 6] * rr[k]; else x = d2f_int(v[kk][f - 6]) * rr[k];
-                }
-                W[f * STAR + s] = x;
+          for (int f = 0; f < MAXF - 6; f++)
+            if (f < nsp) {
+              R x = R(0);
+              if (off[kk] >= 0) {
+                bad |= !dfinite(v[kk][f]);
+                if constexpr (MODE == 0) x = v[kk][f] * r; else x = d2f_int(v[kk][f]) * r;
               }
-          }
+              W[f * STAR + s] = x;
+            }
         }
       }
     }
     bad = __syncthreads_or(bad);
-    if (prefetch && t + (int)gridDim.x < n_tiles) prefetch_tile_l2(fetch(t + gridDim.x), tid, NT, prefetch);
     if (bad && tid == 0 && write_status) {
       atomicOr(&status->flags, 1u);
       atomicMin(&status->first_bad, (unsigned long long)tile.sub);
     }
 
-    Acc acc[CPT][MAXF];
-    R amax = R(0);
-    for (int d = 0; d < 3; d++) {
-      const int e_d = d == 0 ? ex : (d == 1 ? ey : ez);
-      const int e_a = d == 0 ? ey : ex;  // first tangential axis extent
-      const int e_b = d == 2 ? ey : ez;  // second tangential axis extent
-      const int fs = lch * NFC;          // field stride of QS
-      for (int l0 = 0; l0 < NLN; l0 += lch) {
-        // ---- A2: PPM per (line, field)
-        for (int task = tid; task < lch * F; task += NT) {
-          int ll = task % lch, f = task / lch;
-          int l = l0 + ll;
-          R q[LL];
-#pragma unroll
-          for (int c = 0; c < LL; c++) q[c] = W[f * STAR + line_slot(d, l, c)];
-          R* qs = QS + f * fs + ll * NFC;
-          R* qr = QS + (Fmax + f) * fs + ll * NFC;
-          if constexpr (MODE == 0) ppm_line64(q, qs, qr); else ppm_line32(q, qs, qr);
-        }
-        __syncthreads();
-        // ---- A3: central flux per face, written over the left states
-        for (int task = tid; task < lch * NFC; task += NT) {
-          int ll = task / NFC, i = task - ll * NFC;
-          int l = l0 + ll;
-          R wl[MAXF], wr[MAXF];
-          R* fo = QS + ll * NFC + i;
-          const R* fr = fo + Fmax * fs;
-#pragma unroll
-          for (int f = 0; f < MAXF; f++)
-            if (f < F) {
-              wl[f] = fo[f * fs];
-              wr[f] = fr[f * fs];
-            }
-          R a;
-          if constexpr (MODE == 0) {
-            a = kt_face64(wl, wr, F, d, gamma, inv_gm1, fo, fs);
-          } else {
-            a = kt_face32(wl, wr, F, d, gamma, inv_gm1, fo, fs);
-          }
-          bool fvalid = (l % TE) < e_a && (l / TE) < e_b && i <= e_d;
-          if constexpr (MODE == 0) {
-            if (fvalid) amax = dmaxp(amax, a);
-          } else {
-            if (fvalid) amax = fmaxf(amax, a);
-          }
-        }
-        __syncthreads();
-        // ---- A4: flux differences into the owned cells, x then y then z
-#pragma unroll
-        for (int k = 0; k < CPT; k++) {
-          int m = tid + k * NT;
-          if (m < TE * TE * TE) {
-            int x = m % TE, y = (m / TE) % TE, z = m / (TE * TE);
-            int l = d == 0 ? z * TE + y : (d == 1 ? z * TE + x : y * TE + x);
-            int pos = d == 0 ? x : (d == 1 ? y : z);
-            if (l >= l0 && l < l0 + lch) {
-              const R* fl = QS + (l - l0) * NFC + pos;
-#pragma unroll
-              for (int f = 0; f < MAXF; f++)
-                if (f < F) {
-                  R hi = fl[f * fs + 1], lo = fl[f * fs];
-                  if constexpr (MODE == 0) {
-                    acc[k][f] = d == 0 ? hi - lo : acc[k][f] + (hi - lo);
-                  } else {
-                    acc_pair(acc[k][f], hi, lo, d == 0);
-                  }
-                }
-            }
-          }
-        }
-        __syncthreads();
-      }
+    // ---- passive group: tau (slot 5), then the species (slots 0 ..)
+    {
+      Acc acc[CPT][NW];
+      group_pass<MODE, NT, false>(W, GG, QS, lch, 1 + nsp, [](int j) { return j == 0 ? 5 : j - 1; },
+                                  ex, ey, ez, gamma, inv_gm1, acc, amax);
+      store_group<MODE, NT>(out, tile, ex, ey, ez, 5, 1 + nsp, acc);
     }
-    // ---- store dU/dt = -(sum of differences)/dx
-    const long long n3 = (long long)N * N * N;
-    const double scale = -tile.inv_dx;
-    const bool pow2 = (tile.flags & 2) != 0;
-#pragma unroll
-    for (int k = 0; k < CPT; k++) {
-      int m = tid + k * NT;
-      if (m < TE * TE * TE) {
-        int x = m % TE, y = (m / TE) % TE, z = m / (TE * TE);
-        if (x < ex && y < ey && z < ez) {
-          double* o = out + tile.out_off + ((long long)(tile.oz + z) * N + (tile.oy + y)) * N + (tile.ox + x);
-#pragma unroll
-          for (int f = 0; f < MAXF; f++)
-            if (f < F) {
-              double v;
-              if constexpr (MODE == 0) {
-                v = acc[k][f] * scale;
-              } else {
-                if (pow2) {  // scaling by a power of two is exact in binary32
-                  float sf = (float)scale;
-                  v = f2d_int(acc[k][f].h * sf) + f2d_int(acc[k][f].l * sf);
-                } else {
-                  v = (f2d_int(acc[k][f].h) + f2d_int(acc[k][f].l)) * scale;
-                }
-              }
-              o[f * n3] = v;
-            }
-        }
-      }
-    }
+
     // ---- A5: largest signal speed of the tile
     double am = (double)amax;
 #pragma unroll
@@ -768,8 +860,11 @@ __global__ void __launch_bounds__(NT, MINB)
 rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
                  double* __restrict__ out, double* __restrict__ amax_out,
                  Status* __restrict__ status, double gamma_d, int write_status, int prefetch) {
-  tile_loop<MODE, NT>(TileList{tiles}, n_tiles, Fmax, lch, out, amax_out, status, gamma_d,
-                      write_status, prefetch);
+  (void)Fmax;  // the shared-memory layout no longer depends on the field count
+  // KC: read-region slots per load batch (more loads in flight with more
+  // registers per thread)
+  tile_loop<MODE, NT, MINB == 1 ? 4 : 2>(TileList{tiles}, n_tiles, lch, out, amax_out, status,
+                                         gamma_d, write_status, prefetch);
 }
 
 }  // namespace hydro_dev

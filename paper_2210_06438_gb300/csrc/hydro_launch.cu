@@ -12,13 +12,17 @@ using hydro_dev::rhs_tiles_kernel;
 struct Variant {
   int threads, minb;
 };
-static const Variant kVariants[] = {{256, 1}, {128, 1}, {512, 1}, {256, 2}, {128, 2}};
+static const Variant kVariants[] = {{256, 1}, {128, 1}, {512, 1}, {256, 2}, {128, 2}, {256, 3}, {128, 4}};
 static constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int MODE>
 static void* kfunc(int threads, int minb) {
-  if (threads == 128) return minb == 2 ? (void*)&rhs_tiles_kernel<MODE, 128, 2> : (void*)&rhs_tiles_kernel<MODE, 128, 1>;
+  if (threads == 128) {
+    if (minb == 4) return (void*)&rhs_tiles_kernel<MODE, 128, 4>;
+    return minb == 2 ? (void*)&rhs_tiles_kernel<MODE, 128, 2> : (void*)&rhs_tiles_kernel<MODE, 128, 1>;
+  }
   if (threads == 512) return (void*)&rhs_tiles_kernel<MODE, 512, 1>;
+  if (minb == 3) return (void*)&rhs_tiles_kernel<MODE, 256, 3>;
   return minb == 2 ? (void*)&rhs_tiles_kernel<MODE, 256, 2> : (void*)&rhs_tiles_kernel<MODE, 256, 1>;
 }
 
@@ -43,8 +47,9 @@ cudaError_t kernels_init(int smem_optin) {
 }
 
 int smem_bytes(hydro_precision_t prec, int Fmax, int lch) {
-  int es = prec == HYDRO_FP64 ? 8 : 4;
-  return es * (Fmax * hydro_dev::STAR + 2 * Fmax * lch * hydro_dev::NFC);
+  (void)Fmax;
+  return (int)(prec == HYDRO_FP64 ? hydro_dev::smem_layout_bytes<0>(lch)
+                                  : hydro_dev::smem_layout_bytes<1>(lch));
 }
 
 int occupancy(hydro_precision_t prec, int threads, int minb, int smem) {

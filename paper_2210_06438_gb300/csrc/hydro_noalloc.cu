@@ -66,7 +66,7 @@ rhs_uniform_kernel(const hydro_subgrid_t* __restrict__ desc, int N, int F, int G
                    int n_tiles, int lch, double* __restrict__ out, double* __restrict__ amax_out,
                    double gamma_d, int prefetch) {
   // no status word: nonphysical inputs are not recorded by this entry point
-  tile_loop<MODE, NT>(UniformDesc{desc, N, F, G, tpe}, n_tiles, F, lch, out, amax_out, nullptr,
+  tile_loop<MODE, NT, 4>(UniformDesc{desc, N, F, G, tpe}, n_tiles, lch, out, amax_out, nullptr,
                       gamma_d, 0, prefetch);
 }
 
