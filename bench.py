@@ -208,6 +208,21 @@ def max_over_ranks(values, world, device="cuda"):
     return [float(x) for x in t.cpu()]
 
 
+def recorded_traffic(form, n_tiles):
+    """DRAM bytes of one launch from the committed ncu record, scaled to
+    n_tiles; None unless the kernel source still matches the record."""
+    import hashlib
+
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        src = os.path.join(ROOT, "paper_2210_06438_gb300", "csrc", "hydro_kernels.cuh")
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["kernel_source_sha256"]:
+            return None
+        return rec["forms"][form]["bytes_per_tile"] * n_tiles
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -457,7 +472,7 @@ def run_ours(args, rank, world):
     ach = flops / (ms64 * 1e-3) * 1e-9
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     roof = {"bound": "alu", "achieved": ach, "peak": peak_fp64, "unit": "GFLOP/s (fp64)",
-            "frac": ach / peak_fp64, "traffic": None,
+            "frac": ach / peak_fp64, "traffic": recorded_traffic("fp64", info64["n_tiles"]),
             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz" %
             peaks.get("sm_max_mhz", 2070.0),
             "hbm": {"achieved_gbs": batch.alg_bytes / (ms64 * 1e-3) * 1e-9, "peak_gbs": hbm_peak,
@@ -465,6 +480,8 @@ def run_ours(args, rank, world):
                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}}
     mixed_roof = {"bound": "hbm", "achieved": batch.alg_bytes / (msmx * 1e-3) * 1e-9,
                   "peak": hbm_peak, "unit": "GB/s",
+                  "traffic": recorded_traffic("mixed", infomx["n_tiles"]),
+                  "alg_bytes": batch.alg_bytes,
                   "frac": batch.alg_bytes / (msmx * 1e-3) * 1e-9 / hbm_peak,
                   "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
 
