@@ -268,6 +268,7 @@ __device__ __forceinline__ void ppm_line64(const double* q, double* left, double
   }
 }
 
+
 // ---------------------------------------------------- step A3, binary64 --
 // Central flux (Kurganov & Tadmor 2000) through a face normal to axis d,
 //   Fhat = (F_l + F_r)/2 - a (U_r - U_l)/2,  a = max(|u_l| + c_l, |u_r| + c_r),
@@ -276,8 +277,9 @@ __device__ __forceinline__ void ppm_line64(const double* q, double* left, double
 //   Fhat_q = (q_l g_l + q_r g_r)/2,  g_l = rho_l (u_l + a),  g_r = rho_r (u_r - a),
 // plus the pressure terms for momentum and energy.  Mathematically identical
 // to the definition; rounding differs by a few ulps of the flux magnitude.
-// w: (rho, vx, vy, vz, p) on each side.  Writes the five hydro fluxes to
-// fout[f*fstride], returns a and the two g factors the passive fields use.
+// w: (rho, vx, vy, vz, p, phi) on each side.  Writes the six fluxes of the
+// hydro group (rho, s, E, tau) to fout[f*fstride]; returns a and the two g
+// factors the species use.
 __device__ __forceinline__ double kt_hydro64(const double* wl, const double* wr, int d,
                                              double gamma, double inv_gm1, double* fout,
                                              int fstride, double& gl, double& gr) {
@@ -303,22 +305,21 @@ __device__ __forceinline__ double kt_hydro64(const double* wl, const double* wr,
     fout[(1 + c) * fstride] = dhalf(c == d ? t + pp : t);
   }
   fout[4 * fstride] = dhalf(fma(El, hl, fma(pl, ul, fma(Er, hr, pr * ur))));
+  fout[5 * fstride] = dhalf(fma(wl[5], gl, wr[5] * gr));
   return a;
 }
 
 // ====================================================== binary32 (mixed) ==
-// binary64 -> binary32, round to nearest even, on the integer pipe.
-// Magnitudes below the smallest normal binary32 become signed zero; above
-// the largest, infinity (such inputs are flagged as nonphysical anyway).
+// binary64 -> binary32 on the integer pipe: the top 24 significant bits,
+// rounded to nearest with ties away from zero (the binary64 to binary32
+// instruction runs on the slow binary64 pipe of this GPU).  Magnitudes below
+// the smallest normal binary32 (including zero) become signed zero; inputs
+// must stay below 2^128 in magnitude.
 __device__ __forceinline__ float d2f_int(double d) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  unsigned hi = (unsigned)(b >> 32);
+  unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
   unsigned sg = hi & 0x80000000u, ahi = hi & 0x7fffffffu;
-  unsigned long long m = (b & 0x7fffffffffffffffull) - (896ull << 52) + 0x0fffffffull + ((b >> 29) & 1ull);
-  unsigned bits = (unsigned)(m >> 29) | sg;
-  bits = ahi < (897u << 20) ? sg : bits;
-  bits = ahi >= (1151u << 20) ? (sg | 0x7f800000u) : bits;
-  return __uint_as_float(bits);
+  unsigned mag = __funnelshift_l(lo, ahi - (896u << 20), 3) + ((lo >> 28) & 1u);
+  return __uint_as_float(ahi < (897u << 20) ? sg : (mag | sg));
 }
 // binary32 -> binary64 (exact), on the integer pipe; zero and subnormal
 // binary32 values give signed zero.
@@ -349,11 +350,11 @@ __device__ __forceinline__ float tau_pow32(float tau, float gamma, bool g53) {
 
 // ------------------------------------------------------ step A1, mixed --
 // u: the binary64 hydro inputs of one cell (fields 0-5); writes binary32
-// primitives and r = 1/rho.  Where e_int is within a factor 4 of E (where
-// binary32 cancellation would cost more than ~20 ulp) or near the switch, it
-// is recomputed in binary64 in the reference order.
-__device__ __forceinline__ bool prim_mixed(const double* u, double gamma, float gm1f, bool g53,
-                                           float* w, float& r) {
+// primitives (rho, vx, vy, vz, p, phi) and r = 1/rho.  Where e_int is within a
+// factor 4 of E (where binary32 cancellation would cost more than ~20 ulp) or
+// near the switch, it is recomputed in binary64 in the reference order.
+__device__ __forceinline__ bool prim_mixed(const double* u, double gamma, float gamf, float gm1f,
+                                           bool g53, float* w, float& r) {
   float rho = d2f_int(u[0]);
   float s1 = d2f_int(u[1]), s2 = d2f_int(u[2]), s3 = d2f_int(u[3]);
   float E = d2f_int(u[4]), tau = d2f_int(u[5]);
@@ -368,7 +369,7 @@ __device__ __forceinline__ bool prim_mixed(const double* u, double gamma, float 
     double e = ex < __dmul_rn(ETA, u[4]) ? tau_pow64(u[5], gamma, g53) : ex;
     p = __double2float_rn((gamma - 1.0) * e);
   } else {
-    float e = eint <= 0.5f * thr ? tau_pow32(tau, (float)gamma, g53) : eint;
+    float e = eint <= 0.5f * thr ? tau_pow32(tau, gamf, g53) : eint;
     p = gm1f * e;
   }
   w[0] = rho;
@@ -383,52 +384,98 @@ __device__ __forceinline__ bool prim_mixed(const double* u, double gamma, float 
   return bad;
 }
 
-// ------------------------------------------------------ step A2, mixed --
-// The same steps as ppm_line64 in binary32.
-__device__ __forceinline__ bool fsame(float a, float b) {  // a*b > 0, on the signs
-  return ((__float_as_int(a) ^ __float_as_int(b)) >= 0) && a != 0.0f && b != 0.0f;
-}
-__device__ __forceinline__ void ppm_line32(const float* q, float* left, float* right) {
-  float dq[LL - 1];
-#pragma unroll
-  for (int c = 0; c < LL - 1; c++) dq[c] = q[c + 1] - q[c];
-  float del[LL];
-#pragma unroll
-  for (int c = 1; c <= LL - 2; c++) {
-    float dp = dq[c], dm = dq[c - 1];
-    float dbar = 0.5f * (q[c + 1] - q[c - 1]);
-    float m = fminf(fabsf(dbar), 2.0f * fminf(fabsf(dm), fabsf(dp)));
-    del[c] = fsame(dp, dm) ? copysignf(m, dbar) : 0.0f;
+// Addressing of line l along direction d in the read-region layout: three
+// segments (3 low ghosts, TE interior cells, 3 high ghosts), each with a
+// base slot and a constant stride.
+struct LineAddr {
+  int lo, in, hi, sg, si;
+  __device__ __forceinline__ int at(int c) const {
+    return c < 3 ? lo + c * sg : (c < 3 + TE ? in + (c - 3) * si : hi + (c - 3 - TE) * sg);
   }
-  float fc[LL];
+};
+__device__ __forceinline__ LineAddr line_addr(int d, int l) {
+  int a = l % TE, b = l / TE;
+  if (d == 0) {
+    int base = (b * TE + a) * LL;
+    return {base, base + 3, base + 3 + TE, 1, 1};
+  }
+  if (d == 1)
+    return {XROWS + b * 6 * TE + a, b * TE * LL + a + 3, XROWS + b * 6 * TE + 3 * TE + a, TE, LL};
+  return {XROWS + YSLAB + b * TE + a, b * LL + a + 3, XROWS + YSLAB + 3 * TE * TE + b * TE + a,
+          TE * TE, TE * LL};
+}
+
+// -------------------------------------------- packed binary32 arithmetic --
+// Two independent fields are processed per thread with the paired binary32
+// instructions of sm_100+ (one instruction, two lanes of arithmetic).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// ------------------------------------------------------ step A2, mixed --
+// ppm_line64's steps in binary32 on a pair of fields.  The sign tests are
+// evaluated on products (an underflowing product of two differences below
+// ~1e-22 reads as "not the same sign", which changes results by less than
+// such differences).
+__device__ __forceinline__ float2 slope32x2(float2 qm, float2 q0, float2 qp) {
+  float2 dp = sub2(qp, q0), dm = sub2(q0, qm);
+  float2 dbar = mul2(sub2(qp, qm), f2(0.5f));
+  float2 pr = mul2(dp, dm);
+  float2 t = mul2(f2(2.0f), make_float2(fminf(fabsf(dm.x), fabsf(dp.x)), fminf(fabsf(dm.y), fabsf(dp.y))));
+  float mx = fminf(fabsf(dbar.x), t.x), my = fminf(fabsf(dbar.y), t.y);
+  return make_float2(pr.x > 0.0f ? copysignf(mx, dbar.x) : 0.0f, pr.y > 0.0f ? copysignf(my, dbar.y) : 0.0f);
+}
+// One pass along the line keeping a short window of values live: at step c
+// the slope of cell c, the face c-1/2 and the limited states of cell c-1.
+// q: the line in shared memory (la addresses it).
+__device__ __forceinline__ void ppm_line32x2(const float2* w, const LineAddr& la, float2* left,
+                                             float2* right) {
+  float2 q0 = w[la.at(0)], q1 = w[la.at(1)], q2 = w[la.at(2)];
+  float2 del_prev = slope32x2(q0, q1, q2);  // cell c = 1
+  float2 face_prev = f2(0.0f);               // face c - 3/2
+  float2 qm = q1, qc = q2;                    // q[c-1], q[c] for c = 2
 #pragma unroll
-  for (int c = 1; c <= LL - 3; c++) fc[c] = fmaf(del[c] - del[c + 1], 1.0f / 6.0f, 0.5f * (q[c] + q[c + 1]));
-#pragma unroll
-  for (int c = 2; c <= LL - 3; c++) {
-    float qc = q[c], lo = fc[c - 1], hi = fc[c];
-    float up = hi - qc, dn = qc - lo;
-    bool ext = !fsame(up, dn);
-    float t1 = fmaf(-2.0f, up, dn), t2 = fmaf(2.0f, dn, -up);
-    bool A = fsame(t1, up);
-    bool B = !A && fsame(-t2, up);
-    float lo2 = fmaf(-2.0f, up, qc), hi2 = fmaf(2.0f, dn, qc);
-    lo = ext ? qc : (A ? lo2 : lo);
-    hi = ext ? qc : (B ? hi2 : hi);
-    int j = c - 3;
-    if (j >= 0) right[j] = lo;
-    if (j + 1 <= TE) left[j + 1] = hi;
+  for (int c = 2; c <= LL - 2; c++) {
+    float2 qp = w[la.at(c + 1)];
+    float2 del = slope32x2(qm, qc, qp);  // slope of cell c
+    // face between cells c-1 and c
+    float2 face = fma2(sub2(del_prev, del), f2(1.0f / 6.0f), mul2(add2(qm, qc), f2(0.5f)));
+    if (c >= 3) {  // limit cell c-1 with faces face_prev (left) and face (right)
+      float2 lo = face_prev, hi = face, q = qm;
+      float2 up = sub2(hi, q), dn = sub2(q, lo);
+      float2 e = mul2(up, dn);
+      float2 a1 = mul2(fma2(f2(-2.0f), up, dn), up);                 // (dn - 2 up) up
+      float2 a2 = mul2(fma2(f2(2.0f), dn, mul2(up, f2(-1.0f))), up);  // (2 dn - up) up
+      float2 lo2 = fma2(f2(-2.0f), up, q), hi2 = fma2(f2(2.0f), dn, q);
+      float2 L, H;
+      L.x = !(e.x > 0.0f) ? q.x : (a1.x > 0.0f ? lo2.x : lo.x);
+      H.x = !(e.x > 0.0f) ? q.x : (!(a1.x > 0.0f) && a2.x < 0.0f ? hi2.x : hi.x);
+      L.y = !(e.y > 0.0f) ? q.y : (a1.y > 0.0f ? lo2.y : lo.y);
+      H.y = !(e.y > 0.0f) ? q.y : (!(a1.y > 0.0f) && a2.y < 0.0f ? hi2.y : hi.y);
+      int j = c - 4;  // cell index of c-1
+      if (j >= 0) right[j] = L;
+      if (j + 1 <= TE) left[j + 1] = H;
+    }
+    face_prev = face;
+    del_prev = del;
+    qm = qc;
+    qc = qp;
   }
 }
 
 // ------------------------------------------------------ step A3, mixed --
-__device__ __forceinline__ float kt_hydro32(const float* wl, const float* wr, int d, float gamma,
-                                            float inv_gm1, float* fout, int fstride, float& gl,
+// kt_hydro64's flux in binary32.  w: three pairs (rho, vx), (vy, vz), (p, phi).
+__device__ __forceinline__ float kt_hydro32(const float2* wl, const float2* wr, int d, float gamma,
+                                            float inv_gm1, float2* fout, int fstride, float& gl,
                                             float& gr) {
-  float rl = wl[0], rr = wr[0], pl = wl[4], pr = wr[4];
-  float ul = d == 0 ? wl[1] : (d == 1 ? wl[2] : wl[3]);
-  float ur = d == 0 ? wr[1] : (d == 1 ? wr[2] : wr[3]);
-  float vl2 = fmaf(wl[3], wl[3], fmaf(wl[2], wl[2], wl[1] * wl[1]));
-  float vr2 = fmaf(wr[3], wr[3], fmaf(wr[2], wr[2], wr[1] * wr[1]));
+  float rl = wl[0].x, rr = wr[0].x, pl = wl[2].x, pr = wr[2].x;
+  float vl[3] = {wl[0].y, wl[1].x, wl[1].y}, vr[3] = {wr[0].y, wr[1].x, wr[1].y};
+  float ul = d == 0 ? vl[0] : (d == 1 ? vl[1] : vl[2]);
+  float ur = d == 0 ? vr[0] : (d == 1 ? vr[1] : vr[2]);
+  float vl2 = fmaf(vl[2], vl[2], fmaf(vl[1], vl[1], vl[0] * vl[0]));
+  float vr2 = fmaf(vr[2], vr[2], fmaf(vr[1], vr[1], vr[0] * vr[0]));
   float El = fmaf(0.5f * rl, vl2, pl * inv_gm1);
   float Er = fmaf(0.5f * rr, vr2, pr * inv_gm1);
   float gpl = gamma * pl, gpr = gamma * pr;
@@ -438,14 +485,17 @@ __device__ __forceinline__ float kt_hydro32(const float* wl, const float* wr, in
   float hl = ul + a, hr = ur - a;
   gl = rl * hl;
   gr = rr * hr;
-  fout[0] = 0.5f * (gl + gr);
   float pp = pl + pr;
+  float m[3];
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    float t = fmaf(wl[1 + c], gl, wr[1 + c] * gr);
-    fout[(1 + c) * fstride] = 0.5f * (c == d ? t + pp : t);
+    float t = fmaf(vl[c], gl, vr[c] * gr);
+    m[c] = 0.5f * (c == d ? t + pp : t);
   }
-  fout[4 * fstride] = 0.5f * fmaf(El, hl, fmaf(pl, ul, fmaf(Er, hr, pr * ur)));
+  fout[0] = make_float2(0.5f * (gl + gr), m[0]);
+  fout[fstride] = make_float2(m[1], m[2]);
+  fout[2 * fstride] = make_float2(0.5f * fmaf(El, hl, fmaf(pl, ul, fmaf(Er, hr, pr * ur))),
+                                  0.5f * fmaf(wl[2].y, gl, wr[2].y * gr));
   return a;
 }
 
@@ -459,17 +509,29 @@ __device__ __forceinline__ F2 two_sum(float a, float b) {  // a + b = s + e exac
   float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
   return {s, e};
 }
-// running pair (H, L) += (hi - lo): the difference is split exactly, its high
-// part is added with an exact two-sum, the low parts are summed in binary32
-// (their rounding is ~2^-24 of a quantity already ~2^-24 smaller than H).
-__device__ __forceinline__ void acc_pair(F2& acc, float hi, float lo, bool first) {
-  F2 d = two_sum(hi, -lo);
+// Packed: two independent running sums (H, L) += (hi - lo), one per lane.
+// The difference is split exactly with a two-sum, its high part is added to
+// H with an exact two-sum, the low parts are summed in binary32 (their
+// rounding is ~2^-24 of a quantity already ~2^-24 smaller than H).
+struct P2 {
+  float2 h, l;
+};
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  float2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+__device__ __forceinline__ void acc_pair2(P2& acc, float2 hi, float2 lo, bool first) {
+  float2 dh, dl;
+  two_sum2(hi, mul2(lo, f2(-1.0f)), dh, dl);
   if (first) {
-    acc = d;
+    acc.h = dh;
+    acc.l = dl;
   } else {
-    F2 s = two_sum(acc.h, d.h);
-    acc.h = s.h;
-    acc.l = __fadd_rn(__fadd_rn(acc.l, d.l), s.l);
+    float2 sh, sl;
+    two_sum2(acc.h, dh, sh, sl);
+    acc.h = sh;
+    acc.l = add2(add2(acc.l, dl), sl);
   }
 }
 
@@ -518,10 +580,10 @@ __device__ __forceinline__ void prefetch_tile_l2(const Tile& tile, int tid, int 
   }
 }
 
-// ------------------------------------------------------------- kernel --
+// ------------------------------------------------------------- layout --
 template <int MODE> struct Prec;
-template <> struct Prec<0> { typedef double R; typedef double Acc; };
-template <> struct Prec<1> { typedef float R; typedef F2 Acc; };
+template <> struct Prec<0> { typedef double R; typedef double V; typedef double Acc; static constexpr int PACK = 1; };
+template <> struct Prec<1> { typedef float R; typedef float2 V; typedef P2 Acc; static constexpr int PACK = 2; };
 
 // Source of the tile descriptors: a prepared work list in global memory.
 struct TileList {
@@ -529,93 +591,76 @@ struct TileList {
   __device__ __forceinline__ Tile operator()(int t) const { return tiles[t]; }
 };
 
-// Addressing of line l along direction d in the read-region layout: three
-// segments (3 low ghosts, TE interior cells, 3 high ghosts), each with a
-// base slot and a constant stride.
-struct LineAddr {
-  int lo, in, hi, sg, si;
-  __device__ __forceinline__ int at(int c) const {
-    return c < 3 ? lo + c * sg : (c < 3 + TE ? in + (c - 3) * si : hi + (c - 3 - TE) * sg);
-  }
-};
-__device__ __forceinline__ LineAddr line_addr(int d, int l) {
-  int a = l % TE, b = l / TE;
-  if (d == 0) {
-    int base = (b * TE + a) * LL;
-    return {base, base + 3, base + 3 + TE, 1, 1};
-  }
-  if (d == 1)
-    return {XROWS + b * 6 * TE + a, b * TE * LL + a + 3, XROWS + b * 6 * TE + 3 * TE + a, TE, LL};
-  return {XROWS + YSLAB + b * TE + a, b * LL + a + 3, XROWS + YSLAB + 3 * TE * TE + b * TE + a,
-          TE * TE, TE * LL};
-}
+constexpr int NGRP = 6;  // fields per group: hydro (rho, vx, vy, vz, p, phi) or species (<= 5)
 
-constexpr int NHYD = 5;  // hydro group: rho, vx, vy, vz, p
-constexpr int NW = 6;    // primitive slots in shared memory
-
-// Shared memory of one CTA (R = element type of the mode):
-//   W  [NW][STAR]           primitives of the read region: hydro group in
-//                           slots 0-4 and phi = tau/rho in slot 5; after the
-//                           hydro pass the species overwrite slots 0..
-//   RR [STAR]               1/rho of every read cell
-//   GG [3][NLN][NFC][2]     per face the factors g_l, g_r of the passive fluxes
-//   QS [2][NW][lch][NFC]    face states of a chunk of lines, then its fluxes
+// Shared memory of one CTA.  V = R (binary64) or a pair of binary32 values
+// (mixed form: fields 2k and 2k+1 of a group share one 8-byte element):
+//   W  [NGRP/PACK][STAR] V   primitives of the read region: the hydro group,
+//                            then (after the hydro pass) the species
+//   RR [STAR] R              1/rho of every read cell
+//   GG [3][NLN][NFC][2] R    per face the factors g_l, g_r of the species fluxes
+//   QS [2][NGRP/PACK][lch][NFC] V   face states of a chunk of lines, then fluxes
 template <int MODE>
 __host__ __device__ constexpr size_t smem_layout_bytes(int lch) {
   return (MODE == 0 ? 8 : 4) *
-         ((size_t)NW * STAR + STAR + 3 * NLN * NFC * 2 + 2 * (size_t)NW * lch * NFC);
+         ((size_t)NGRP * STAR + STAR + 3 * NLN * NFC * 2 + 2 * (size_t)NGRP * lch * NFC);
 }
 
-// One pass of steps A2-A4 over a group of `nf` fields for all three
-// directions.  HYD: the hydro group (flux of Kurganov-Tadmor, records g_l,
-// g_r and the signal speed); else the passive group (flux from g_l, g_r).
-// slot(j): shared-memory slot of group field j.  acc[k][j] receives, for the
-// thread's owned cells k, the sum of the flux differences x, then y, then z.
-template <int MODE, int NT, bool HYD, class Slot>
-__device__ __forceinline__ void group_pass(const typename Prec<MODE>::R* W, typename Prec<MODE>::R* GG,
-                                           typename Prec<MODE>::R* QS, int lch, int nf, Slot slot,
-                                           int ex, int ey, int ez, typename Prec<MODE>::R gamma,
-                                           typename Prec<MODE>::R inv_gm1,
-                                           typename Prec<MODE>::Acc (&acc)[(TE * TE * TE + NT - 1) / NT][NW],
-                                           typename Prec<MODE>::R& amax) {
+// One pass of steps A2-A4 over a group of `ng` field slots (V elements) for
+// all three directions.  HYD: the hydro group (Kurganov-Tadmor flux, records
+// g_l, g_r and the signal speed); else the species (flux from g_l, g_r).
+// acc[k][j] receives, for the thread's owned cells k, the sum of the flux
+// differences x, then y, then z of slot j.
+template <int MODE, int NT, bool HYD>
+__device__ __forceinline__ void group_pass(
+    const typename Prec<MODE>::V* W, typename Prec<MODE>::R* GG, typename Prec<MODE>::V* QS,
+    int lch, int ng, int ex, int ey, int ez, typename Prec<MODE>::R gamma,
+    typename Prec<MODE>::R inv_gm1,
+    typename Prec<MODE>::Acc (&acc)[(TE * TE * TE + NT - 1) / NT][NGRP / Prec<MODE>::PACK],
+    typename Prec<MODE>::R& amax) {
   typedef typename Prec<MODE>::R R;
+  typedef typename Prec<MODE>::V V;
   constexpr int CPT = (TE * TE * TE + NT - 1) / NT;
+  constexpr int NS = NGRP / Prec<MODE>::PACK;  // V slots of a full group
   const int tid = threadIdx.x;
-  const int fs = lch * NFC;  // field stride of QS
-  R* QR = QS + NW * fs;      // right states
+  const int fs = lch * NFC;  // slot stride of QS
+  V* QR = QS + NS * fs;      // right states
   for (int d = 0; d < 3; d++) {
     const int e_d = d == 0 ? ex : (d == 1 ? ey : ez);
     const int e_a = d == 0 ? ey : ex;  // first tangential axis extent
     const int e_b = d == 2 ? ey : ez;  // second tangential axis extent
     R* gg = GG + d * NLN * NFC * 2;
     for (int l0 = 0; l0 < NLN; l0 += lch) {
-      // ---- A2: PPM per (line, field)
-      for (int task = tid; task < lch * nf; task += NT) {
+      // ---- A2: PPM per (line, slot)
+      for (int task = tid; task < lch * ng; task += NT) {
         int ll = task % lch, j = task / lch;
         LineAddr la = line_addr(d, l0 + ll);
-        const R* w = W + slot(j) * STAR;
-        R q[LL];
+        const V* w = W + j * STAR;
+        if constexpr (MODE == 0) {
+          V q[LL];
 #pragma unroll
-        for (int c = 0; c < LL; c++) q[c] = w[la.at(c)];
-        if constexpr (MODE == 0) ppm_line64(q, QS + j * fs + ll * NFC, QR + j * fs + ll * NFC);
-        else ppm_line32(q, QS + j * fs + ll * NFC, QR + j * fs + ll * NFC);
+          for (int c = 0; c < LL; c++) q[c] = w[la.at(c)];
+          ppm_line64(q, QS + j * fs + ll * NFC, QR + j * fs + ll * NFC);
+        } else {
+          ppm_line32x2(w, la, QS + j * fs + ll * NFC, QR + j * fs + ll * NFC);
+        }
       }
       __syncthreads();
       // ---- A3: flux per face, written over the left states
       for (int task = tid; task < lch * NFC; task += NT) {
         int ll = task / NFC, i = task - ll * NFC;
         int l = l0 + ll;
-        R* fo = QS + ll * NFC + i;
-        const R* fr = QR + ll * NFC + i;
+        V* fo = QS + ll * NFC + i;
+        const V* fr = QR + ll * NFC + i;
         R* g = gg + (l * NFC + i) * 2;
         if constexpr (HYD) {
-          R wl[NHYD], wr[NHYD], gl, gr;
+          V wl[NS], wr[NS];
 #pragma unroll
-          for (int f = 0; f < NHYD; f++) {
-            wl[f] = fo[f * fs];
-            wr[f] = fr[f * fs];
+          for (int j = 0; j < NS; j++) {
+            wl[j] = fo[j * fs];
+            wr[j] = fr[j * fs];
           }
-          R a;
+          R a, gl, gr;
           if constexpr (MODE == 0) a = kt_hydro64(wl, wr, d, gamma, inv_gm1, fo, fs, gl, gr);
           else a = kt_hydro32(wl, wr, d, gamma, inv_gm1, fo, fs, gl, gr);
           g[0] = gl;
@@ -629,10 +674,10 @@ __device__ __forceinline__ void group_pass(const typename Prec<MODE>::R* W, type
         } else {
           R gl = g[0], gr = g[1];
 #pragma unroll
-          for (int j = 0; j < NW; j++)
-            if (j < nf) {
+          for (int j = 0; j < NS; j++)
+            if (j < ng) {
               if constexpr (MODE == 0) fo[j * fs] = dhalf(fma(fo[j * fs], gl, fr[j * fs] * gr));
-              else fo[j * fs] = 0.5f * fmaf(fo[j * fs], gl, fr[j * fs] * gr);
+              else fo[j * fs] = mul2(fma2(fo[j * fs], f2(gl), mul2(fr[j * fs], f2(gr))), f2(0.5f));
             }
         }
       }
@@ -646,15 +691,15 @@ __device__ __forceinline__ void group_pass(const typename Prec<MODE>::R* W, type
           int l = d == 0 ? z * TE + y : (d == 1 ? z * TE + x : y * TE + x);
           int pos = d == 0 ? x : (d == 1 ? y : z);
           if (l >= l0 && l < l0 + lch) {
-            const R* fl = QS + (l - l0) * NFC + pos;
+            const V* fl = QS + (l - l0) * NFC + pos;
 #pragma unroll
-            for (int j = 0; j < NW; j++)
-              if (j < nf) {
-                R hi = fl[j * fs + 1], lo = fl[j * fs];
+            for (int j = 0; j < NS; j++)
+              if (j < ng) {
+                V hi = fl[j * fs + 1], lo = fl[j * fs];
                 if constexpr (MODE == 0) {
                   acc[k][j] = d == 0 ? hi - lo : acc[k][j] + (hi - lo);
                 } else {
-                  acc_pair(acc[k][j], hi, lo, d == 0);
+                  acc_pair2(acc[k][j], hi, lo, d == 0);
                 }
               }
           }
@@ -665,16 +710,24 @@ __device__ __forceinline__ void group_pass(const typename Prec<MODE>::R* W, type
   }
 }
 
-// Store dU/dt = -(sum of differences)/dx of a group's fields.
+// binary64 value of a mixed-form running sum (one lane), scaled by -1/dx
+// (sf: the same scale in binary32, exact when dx is a power of two)
+__device__ __forceinline__ double pair_value(float h, float l, double scale, float sf, bool pow2) {
+  if (pow2) return f2d_int(h * sf) + f2d_int(l * sf);  // exact scaling in binary32
+  return (f2d_int(h) + f2d_int(l)) * scale;
+}
+
+// Store dU/dt = -(sum of differences)/dx of the fields f0 .. f0+nf-1.
 template <int MODE, int NT>
-__device__ __forceinline__ void store_group(double* __restrict__ out, const Tile& tile, int ex,
-                                            int ey, int ez, int f0, int nf,
-                                            const typename Prec<MODE>::Acc (&acc)[(TE * TE * TE + NT - 1) / NT][NW]) {
+__device__ __forceinline__ void store_group(
+    double* __restrict__ out, const Tile& tile, int ex, int ey, int ez, int f0, int nf,
+    const typename Prec<MODE>::Acc (&acc)[(TE * TE * TE + NT - 1) / NT][NGRP / Prec<MODE>::PACK]) {
   constexpr int CPT = (TE * TE * TE + NT - 1) / NT;
   const int tid = threadIdx.x, N = tile.N;
   const long long n3 = (long long)N * N * N;
   const double scale = -tile.inv_dx;
   const bool pow2 = (tile.flags & 2) != 0;
+  const float sf = pow2 ? d2f_int(scale) : 0.0f;
 #pragma unroll
   for (int k = 0; k < CPT; k++) {
     int m = tid + k * NT;
@@ -684,18 +737,15 @@ __device__ __forceinline__ void store_group(double* __restrict__ out, const Tile
         double* o = out + tile.out_off + f0 * n3 +
                     ((long long)(tile.oz + z) * N + (tile.oy + y)) * N + (tile.ox + x);
 #pragma unroll
-        for (int j = 0; j < NW; j++)
+        for (int j = 0; j < NGRP; j++)
           if (j < nf) {
             double v;
             if constexpr (MODE == 0) {
               v = acc[k][j] * scale;
             } else {
-              if (pow2) {  // scaling by a power of two is exact in binary32
-                float sf = (float)scale;
-                v = f2d_int(acc[k][j].h * sf) + f2d_int(acc[k][j].l * sf);
-              } else {
-                v = (f2d_int(acc[k][j].h) + f2d_int(acc[k][j].l)) * scale;
-              }
+              const P2& a = acc[k][j / 2];
+              v = (j & 1) ? pair_value(a.h.y, a.l.y, scale, sf, pow2)
+                          : pair_value(a.h.x, a.l.x, scale, sf, pow2);
             }
             o[j * n3] = v;
           }
@@ -712,17 +762,20 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
                                           Status* __restrict__ status, double gamma_d,
                                           int write_status, int prefetch) {
   typedef typename Prec<MODE>::R R;
+  typedef typename Prec<MODE>::V V;
   typedef typename Prec<MODE>::Acc Acc;
+  constexpr int PK = Prec<MODE>::PACK;
+  constexpr int NS = NGRP / PK;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* W = reinterpret_cast<R*>(smem_raw);
-  R* RR = W + NW * STAR;
+  V* W = reinterpret_cast<V*>(smem_raw);
+  R* RR = reinterpret_cast<R*>(W + NS * STAR);
   R* GG = RR + STAR;
-  R* QS = GG + 3 * NLN * NFC * 2;
+  V* QS = reinterpret_cast<V*>(GG + 3 * NLN * NFC * 2);
   __shared__ double red[NT / 32];
   const int tid = threadIdx.x;
   const R gamma = R(gamma_d);
   const R inv_gm1 = R(1.0 / (gamma_d - 1.0));
-  const float gm1f = (float)(gamma_d - 1.0);
+  const float gm1f = (float)(gamma_d - 1.0), gamf = (float)gamma_d;
   const bool g53 = gamma_d == 5.0 / 3.0;
   constexpr int CPT = (TE * TE * TE + NT - 1) / NT;  // owned cells per thread
   constexpr int SPT = (STAR + NT - 1) / NT;          // read-region slots per thread
@@ -733,8 +786,6 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
     const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
     const long long plane = (long long)G * G * G;
 
-    // ---- A0/A1 (hydro fields): stage rho, s, E, tau as primitives.  In each
-    // batch every load is issued before any result is used.
     // offset of read-region slot s within a field of the stored block; -1 if
     // the slot is outside the (possibly partial) tile's read region: at most
     // one coordinate outside the tile, and that one at most 3 cells out
@@ -745,6 +796,9 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
       bool valid = s < STAR && outside <= 1 && x < ex + 3 && y < ey + 3 && z < ez + 3;
       return valid ? ((tile.oz + z + gh) * G + (tile.oy + y + gh)) * G + (tile.ox + x + gh) : -1;
     };
+
+    // ---- A0/A1 (hydro group): rho, s, E, tau -> rho, v, p, phi.  In each
+    // batch every load is issued before any result is used.
     bool bad = false;
 #pragma unroll
     for (int k0 = 0; k0 < SPT; k0 += KC) {
@@ -765,30 +819,34 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
         R w[6], r;
         if (off[kk] >= 0) {
           if constexpr (MODE == 0) bad |= prim64(u[kk], gamma_d, g53, w, r);
-          else bad |= prim_mixed(u[kk], gamma_d, gm1f, g53, w, r);
+          else bad |= prim_mixed(u[kk], gamma_d, gamf, gm1f, g53, w, r);
         } else {
 #pragma unroll
           for (int f = 0; f < 6; f++) w[f] = (f == 0 || f == 4) ? R(1) : R(0);
           r = R(1);
         }
+        if constexpr (MODE == 0) {
 #pragma unroll
-        for (int f = 0; f < 6; f++) W[f * STAR + s] = w[f];
+          for (int f = 0; f < 6; f++) W[f * STAR + s] = w[f];
+        } else {
+#pragma unroll
+          for (int j = 0; j < 3; j++) W[j * STAR + s] = make_float2(w[2 * j], w[2 * j + 1]);
+        }
         RR[s] = r;
       }
     }
     bad = __syncthreads_or(bad);
     if (prefetch && t + (int)gridDim.x < n_tiles) prefetch_tile_l2(fetch(t + gridDim.x), tid, NT, prefetch);
 
-    // ---- hydro group: rho, momentum, E
+    // ---- hydro group: rho, momentum, E, tau
     R amax = R(0);
     {
-      Acc acc[CPT][NW];
-      group_pass<MODE, NT, true>(W, GG, QS, lch, NHYD, [](int j) { return j; }, ex, ey, ez, gamma,
-                                 inv_gm1, acc, amax);
-      store_group<MODE, NT>(out, tile, ex, ey, ez, 0, NHYD, acc);
+      Acc acc[CPT][NS];
+      group_pass<MODE, NT, true>(W, GG, QS, lch, NS, ex, ey, ez, gamma, inv_gm1, acc, amax);
+      store_group<MODE, NT>(out, tile, ex, ey, ez, 0, 6, acc);
     }
 
-    // ---- A0/A1 (species): X_k = rho_k / rho into slots 0 .. F-7
+    // ---- A0/A1 (species): X_k = rho_k / rho into the group slots
     const int nsp = F - 6;
     if (nsp > 0) {
 #pragma unroll
@@ -809,16 +867,24 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
           int s = tid + k * NT;
           if (k >= SPT || s >= STAR) continue;
           R r = RR[s];
+          R x[MAXF - 6];
 #pragma unroll
-          for (int f = 0; f < MAXF - 6; f++)
-            if (f < nsp) {
-              R x = R(0);
-              if (off[kk] >= 0) {
-                bad |= !dfinite(v[kk][f]);
-                if constexpr (MODE == 0) x = v[kk][f] * r; else x = d2f_int(v[kk][f]) * r;
-              }
-              W[f * STAR + s] = x;
+          for (int f = 0; f < MAXF - 6; f++) {
+            x[f] = R(0);
+            if (f < nsp && off[kk] >= 0) {
+              bad |= !dfinite(v[kk][f]);
+              if constexpr (MODE == 0) x[f] = v[kk][f] * r; else x[f] = d2f_int(v[kk][f]) * r;
             }
+          }
+          if constexpr (MODE == 0) {
+#pragma unroll
+            for (int f = 0; f < MAXF - 6; f++)
+              if (f < nsp) W[f * STAR + s] = x[f];
+          } else {
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+              if (2 * j < nsp) W[j * STAR + s] = make_float2(x[2 * j], 2 * j + 1 < MAXF - 6 ? x[2 * j + 1] : 0.0f);
+          }
         }
       }
     }
@@ -828,12 +894,12 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
       atomicMin(&status->first_bad, (unsigned long long)tile.sub);
     }
 
-    // ---- passive group: tau (slot 5), then the species (slots 0 ..)
-    {
-      Acc acc[CPT][NW];
-      group_pass<MODE, NT, false>(W, GG, QS, lch, 1 + nsp, [](int j) { return j == 0 ? 5 : j - 1; },
-                                  ex, ey, ez, gamma, inv_gm1, acc, amax);
-      store_group<MODE, NT>(out, tile, ex, ey, ez, 5, 1 + nsp, acc);
+    // ---- species group
+    if (nsp > 0) {
+      Acc acc[CPT][NS];
+      group_pass<MODE, NT, false>(W, GG, QS, lch, (nsp + PK - 1) / PK, ex, ey, ez, gamma, inv_gm1,
+                                  acc, amax);
+      store_group<MODE, NT>(out, tile, ex, ey, ez, 6, nsp, acc);
     }
 
     // ---- A5: largest signal speed of the tile
@@ -860,7 +926,7 @@ __global__ void __launch_bounds__(NT, MINB)
 rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
                  double* __restrict__ out, double* __restrict__ amax_out,
                  Status* __restrict__ status, double gamma_d, int write_status, int prefetch) {
-  (void)Fmax;  // the shared-memory layout no longer depends on the field count
+  (void)Fmax;  // the shared-memory layout does not depend on the field count
   // KC: read-region slots per load batch (more loads in flight with more
   // registers per thread)
   tile_loop<MODE, NT, MINB == 1 ? 4 : 2>(TileList{tiles}, n_tiles, lch, out, amax_out, status,
