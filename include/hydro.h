@@ -95,6 +95,9 @@ int hydro_rhs(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t N, in
 /* hydro_rhs with a precision, a stream (cudaStream_t as void*) and flags
  * (HYDRO_F_* below, 0 for defaults). */
 #define HYDRO_F_NO_STATUS 1u /* skip the nonphysical-input checks' status writes */
+#define HYDRO_F_KNP 2u       /* central-upwind flux with one-sided local speeds (Kurganov,
+                                Noelle & Petrova 2001) instead of the single-speed
+                                Kurganov-Tadmor flux; same signal speed for amax */
 int hydro_rhs_ex(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t N, int32_t ghost,
                  int32_t n_fields, double gamma, double* out_dUdt, double* out_amax,
                  hydro_precision_t prec, void* stream, uint32_t flags);
@@ -119,6 +122,7 @@ int hydro_rhs_per_subgrid(const hydro_subgrid_t* subgrids, int64_t n_subgrids, i
 typedef struct hydro_plan hydro_plan_t;
 #define HYDRO_PLAN_AUTOTUNE 1u /* time candidate launch shapes and keep the fastest */
 #define HYDRO_PLAN_NO_GRAPH 2u /* launch directly instead of replaying a graph */
+#define HYDRO_PLAN_KNP 4u      /* the flux of HYDRO_F_KNP */
 
 typedef struct {
   int64_t n_subgrids;
@@ -190,6 +194,7 @@ typedef struct {
   int32_t per_task;       /* 1: never aggregate; one launch per task (the comparison form) */
   int64_t dry_run_ns;     /* > 0: no GPU work at all; a launch "completes" this many ns after
                              it starts (host-only testing of admission, order and timeouts) */
+  uint32_t flags;         /* HYDRO_F_KNP or 0 */
 } hydro_server_cfg_t;
 
 typedef struct {

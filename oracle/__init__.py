@@ -36,6 +36,8 @@ NONPHYS = 1
 EINVAL = 2
 MODE_FP64 = 0
 MODE_MIXED = 1
+FLUX_KT = 0   # Kurganov-Tadmor (single speed)
+FLUX_KNP = 2  # Kurganov-Noelle-Petrova (one-sided speeds); add to the mode
 
 _lock = threading.Lock()
 _lib = None

@@ -200,7 +200,7 @@ static void ppm_line_f(const float* q, int n, float* qm, float* qp, float* delta
  *   Fhat = (F_l + F_r)/2 - a (U_r - U_l)/2
  * Returns a. */
 static void cons_flux_d(const double* w, int nf, int d, double gamma, double* U, double* F,
-                        double* speed) {
+                        double* speed, double* un, double* cs) {
   double rho = w[0], vx = w[1], vy = w[2], vz = w[3], p = w[4];
   double v[3] = {vx, vy, vz};
   double u = v[d];
@@ -217,21 +217,46 @@ static void cons_flux_d(const double* w, int nf, int d, double gamma, double* U,
   for (int c = 0; c < 3; c++) F[1 + c] = U[1 + c] * u + (c == d ? p : 0.0);
   F[4] = (E + p) * u;
   for (int f = 5; f < nf; f++) F[f] = U[f] * u;
-  *speed = fabs(u) + sqrt(gamma * p / rho);
+  *cs = sqrt(gamma * p / rho);
+  *un = u;
+  *speed = fabs(u) + *cs;
 }
 
 static double kt_flux_d(const double* wl, const double* wr, int nf, int d, double gamma,
                         double* fhat) {
-  double Ul[ORA_MAXF], Fl[ORA_MAXF], Ur[ORA_MAXF], Fr[ORA_MAXF], al, ar;
-  cons_flux_d(wl, nf, d, gamma, Ul, Fl, &al);
-  cons_flux_d(wr, nf, d, gamma, Ur, Fr, &ar);
+  double Ul[ORA_MAXF], Fl[ORA_MAXF], Ur[ORA_MAXF], Fr[ORA_MAXF], al, ar, ul, ur, cl, cr;
+  cons_flux_d(wl, nf, d, gamma, Ul, Fl, &al, &ul, &cl);
+  cons_flux_d(wr, nf, d, gamma, Ur, Fr, &ar, &ur, &cr);
   double a = fmax(al, ar);
   for (int f = 0; f < nf; f++) fhat[f] = 0.5 * (Fl[f] + Fr[f]) - 0.5 * a * (Ur[f] - Ul[f]);
   return a;
 }
 
+/* Central-upwind flux with one-sided local speeds (Kurganov, Noelle &
+ * Petrova 2001):
+ *   ap = max(u_l + c_l, u_r + c_r, 0),  am = min(u_l - c_l, u_r - c_r, 0)
+ *   Fhat = (ap F_l - am F_r)/(ap - am) + ap am (U_r - U_l)/(ap - am)
+ * (if ap = am = 0, Fhat = (F_l + F_r)/2).  The signal speed returned for the
+ * Courant condition is max(ap, -am) = max(|u_l| + c_l, |u_r| + c_r). */
+static double knp_flux_d(const double* wl, const double* wr, int nf, int d, double gamma,
+                         double* fhat) {
+  double Ul[ORA_MAXF], Fl[ORA_MAXF], Ur[ORA_MAXF], Fr[ORA_MAXF], al, ar, ul, ur, cl, cr;
+  cons_flux_d(wl, nf, d, gamma, Ul, Fl, &al, &ul, &cl);
+  cons_flux_d(wr, nf, d, gamma, Ur, Fr, &ar, &ur, &cr);
+  double ap = fmax(fmax(ul + cl, ur + cr), 0.0);
+  double am = fmin(fmin(ul - cl, ur - cr), 0.0);
+  double den = ap - am;
+  for (int f = 0; f < nf; f++) {
+    if (den > 0.0)
+      fhat[f] = (ap * Fl[f] - am * Fr[f]) / den + ap * am * (Ur[f] - Ul[f]) / den;
+    else
+      fhat[f] = 0.5 * (Fl[f] + Fr[f]);
+  }
+  return fmax(al, ar);
+}
+
 static void cons_flux_f(const float* w, int nf, int d, float gamma, float* U, float* F,
-                        float* speed) {
+                        float* speed, float* un, float* cs) {
   float rho = w[0], vx = w[1], vy = w[2], vz = w[3], p = w[4];
   float v[3] = {vx, vy, vz};
   float u = v[d];
@@ -248,22 +273,42 @@ static void cons_flux_f(const float* w, int nf, int d, float gamma, float* U, fl
   for (int c = 0; c < 3; c++) F[1 + c] = U[1 + c] * u + (c == d ? p : 0.0f);
   F[4] = (E + p) * u;
   for (int f = 5; f < nf; f++) F[f] = U[f] * u;
-  *speed = fabsf(u) + sqrtf(gamma * p / rho);
+  *cs = sqrtf(gamma * p / rho);
+  *un = u;
+  *speed = fabsf(u) + *cs;
 }
 
 static float kt_flux_f(const float* wl, const float* wr, int nf, int d, float gamma,
                        float* fhat) {
-  float Ul[ORA_MAXF], Fl[ORA_MAXF], Ur[ORA_MAXF], Fr[ORA_MAXF], al, ar;
-  cons_flux_f(wl, nf, d, gamma, Ul, Fl, &al);
-  cons_flux_f(wr, nf, d, gamma, Ur, Fr, &ar);
+  float Ul[ORA_MAXF], Fl[ORA_MAXF], Ur[ORA_MAXF], Fr[ORA_MAXF], al, ar, ul, ur, cl, cr;
+  cons_flux_f(wl, nf, d, gamma, Ul, Fl, &al, &ul, &cl);
+  cons_flux_f(wr, nf, d, gamma, Ur, Fr, &ar, &ur, &cr);
   float a = fmaxf(al, ar);
   for (int f = 0; f < nf; f++) fhat[f] = 0.5f * (Fl[f] + Fr[f]) - 0.5f * a * (Ur[f] - Ul[f]);
   return a;
 }
 
+static float knp_flux_f(const float* wl, const float* wr, int nf, int d, float gamma,
+                        float* fhat) {
+  float Ul[ORA_MAXF], Fl[ORA_MAXF], Ur[ORA_MAXF], Fr[ORA_MAXF], al, ar, ul, ur, cl, cr;
+  cons_flux_f(wl, nf, d, gamma, Ul, Fl, &al, &ul, &cl);
+  cons_flux_f(wr, nf, d, gamma, Ur, Fr, &ar, &ur, &cr);
+  float ap = fmaxf(fmaxf(ul + cl, ur + cr), 0.0f);
+  float am = fminf(fminf(ul - cl, ur - cr), 0.0f);
+  float den = ap - am;
+  for (int f = 0; f < nf; f++) {
+    if (den > 0.0f)
+      fhat[f] = (ap * Fl[f] - am * Fr[f]) / den + ap * am * (Ur[f] - Ul[f]) / den;
+    else
+      fhat[f] = 0.5f * (Fl[f] + Fr[f]);
+  }
+  return fmaxf(al, ar);
+}
+
 /* --------------------------------------------------------- steps 1 - 5 --
  * One block (a sub-grid, or any nx*ny*nz box used by the tests).
- *   mode 0: all binary64.   mode 1: steps 2-3 in binary32, step 4 binary64.
+ *   mode bit 0: 0 all binary64, 1 steps 2-3 in binary32 and step 4 binary64.
+ *   mode bit 1: 0 Kurganov-Tadmor flux, 1 Kurganov-Noelle-Petrova flux.
  * face_out (optional, may be NULL): receives the face fluxes as doubles,
  *   x faces [nf][nz][ny][nx+1], then y faces [nf][nz][ny+1][nx], then z
  *   faces [nf][nz+1][ny][nx].
@@ -271,9 +316,11 @@ static float kt_flux_f(const float* wl, const float* wr, int nf, int d, float ga
 int ora_rhs_block(const double* U, int nx, int ny, int nz, int ghost, int nf, double gamma,
                   double dx, int mode, double* dUdt, double* amax_out, double* face_out) {
   if (nx < 1 || ny < 1 || nz < 1 || nx > ORA_MAXN || ny > ORA_MAXN || nz > ORA_MAXN || ghost < 3 || nf < 6 ||
-      nf > ORA_MAXF || !(gamma > 1.0) || !(dx > 0.0) || (mode != 0 && mode != 1))
+      nf > ORA_MAXF || !(gamma > 1.0) || !(dx > 0.0) || mode < 0 || mode > 3)
     return ORA_EINVAL;
   ora_geom g = {nx, ny, nz, ghost, nx + 2 * ghost, ny + 2 * ghost, nz + 2 * ghost, nf};
+  const int knp = (mode >> 1) & 1;
+  mode &= 1;
   int flags = 0;
   size_t ncell = (size_t)g.gx * g.gy * g.gz;
 
@@ -357,7 +404,7 @@ int ora_rhs_block(const double* U, int nx, int ny, int nz, int ghost, int nf, do
               wl[f] = qpd[f][i];
               wr[f] = qmd[f][i + 1];
             }
-            double sp = kt_flux_d(wl, wr, nf, d, gamma, fh);
+            double sp = knp ? knp_flux_d(wl, wr, nf, d, gamma, fh) : kt_flux_d(wl, wr, nf, d, gamma, fh);
             if (sp > amax) amax = sp;
             if (!isfinite(sp)) flags |= ORA_NONPHYS;
             for (int f = 0; f < nf; f++) FH[d][(size_t)f * nface[d] + fidx] = fh[f];
@@ -367,7 +414,8 @@ int ora_rhs_block(const double* U, int nx, int ny, int nz, int ghost, int nf, do
               wl[f] = qpf[f][i];
               wr[f] = qmf[f][i + 1];
             }
-            float sp = kt_flux_f(wl, wr, nf, d, (float)gamma, fh);
+            float sp = knp ? knp_flux_f(wl, wr, nf, d, (float)gamma, fh)
+                           : kt_flux_f(wl, wr, nf, d, (float)gamma, fh);
             if (sp > amax_f) amax_f = sp;
             if (!isfinite(sp)) flags |= ORA_NONPHYS;
             for (int f = 0; f < nf; f++) FH[d][(size_t)f * nface[d] + fidx] = (double)fh[f];

@@ -31,7 +31,9 @@ FP64 = 0
 FP32_FLUX_FP64_ACC = 1
 PLAN_AUTOTUNE = 1
 PLAN_NO_GRAPH = 2
+PLAN_KNP = 4
 F_NO_STATUS = 1
+F_KNP = 2
 
 
 
@@ -54,7 +56,7 @@ class ServerCfg(ctypes.Structure):
                 ("n_streams", ctypes.c_int32), ("ghost", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("gamma", ctypes.c_double),
                 ("prec", ctypes.c_int), ("per_task", ctypes.c_int32),
-                ("dry_run_ns", ctypes.c_int64)]
+                ("dry_run_ns", ctypes.c_int64), ("flags", ctypes.c_uint32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -223,11 +225,12 @@ class Plan:
     """hydro_plan_*: fixed batch, tuned launch shape, CUDA-graph replay."""
 
     def __init__(self, desc, ghost=3, gamma=5.0 / 3.0, prec=FP64, autotune=False, graph=True,
-                 stream=None, n=None):
+                 stream=None, n=None, knp=False):
         n = len(desc) if n is None else n
         self._desc = desc  # keep the pointers' owner alive
         h = ctypes.c_void_p()
-        flags = (PLAN_AUTOTUNE if autotune else 0) | (0 if graph else PLAN_NO_GRAPH)
+        flags = ((PLAN_AUTOTUNE if autotune else 0) | (0 if graph else PLAN_NO_GRAPH)
+                 | (PLAN_KNP if knp else 0))
         _check(load().hydro_plan_create(desc, n, ghost, float(gamma), int(prec), flags,
                                         _stream(stream), ctypes.byref(h)), "hydro_plan_create")
         self._h = h
@@ -258,10 +261,10 @@ class Server:
 
     def __init__(self, budget_bytes=40 << 30, max_batch=4096, n_streams=4, ghost=3,
                  queue_capacity=1 << 20, gamma=5.0 / 3.0, prec=FP64, per_task=False,
-                 dry_run_ns=0):
+                 dry_run_ns=0, knp=False):
         cfg = ServerCfg(int(budget_bytes), int(max_batch), int(n_streams), int(ghost),
                         int(queue_capacity), float(gamma), int(prec), 1 if per_task else 0,
-                        int(dry_run_ns))
+                        int(dry_run_ns), F_KNP if knp else 0)
         h = ctypes.c_void_p()
         _check(load().hydro_server_create(ctypes.byref(cfg), ctypes.byref(h)), "hydro_server_create")
         self._h = h

@@ -33,9 +33,10 @@ int occupancy(hydro_precision_t prec, int threads, int minb, int smem);
 int num_variants();
 void variant(int i, int* threads, int* minb);
 LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin, int64_t n_tiles);
+// scheme: 0 Kurganov-Tadmor flux, 1 Kurganov-Noelle-Petrova
 cudaError_t launch_tiles(const LaunchCfg& cfg, hydro_precision_t prec, const hydro_dev::Tile* tiles,
                          int n_tiles, int Fmax, double* out, double* amax, hydro_dev::Status* status,
-                         double gamma, int write_status, cudaStream_t st);
+                         double gamma, int write_status, cudaStream_t st, int scheme = 0);
 // kernel entry and argument block, for graph nodes
 void kernel_node(const LaunchCfg& cfg, hydro_precision_t prec, void** func);
 

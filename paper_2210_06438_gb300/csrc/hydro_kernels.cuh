@@ -150,6 +150,7 @@ __device__ __forceinline__ double dmaxp(double a, double b) {  // a, b >= 0
   return __double_as_longlong(a) > __double_as_longlong(b) ? a : b;
 }
 __device__ __forceinline__ bool dfinite(double x) { return (hiw(x) & 0x7ff00000) != 0x7ff00000; }
+__device__ __forceinline__ double dmax_s(double a, double b) { return dgt(a, b) ? a : b; }  // any signs
 
 // Reciprocal and reciprocal square root: the hardware seed refined by two
 // Newton-Raphson steps (quadratic convergence; Markstein 1990), ~1 ulp.
@@ -281,7 +282,7 @@ __device__ __forceinline__ void ppm_line64(const double* q, double* left, double
 // hydro group (rho, s, E, tau) to fout[f*fstride]; returns a and the two g
 // factors the species use.
 __device__ __forceinline__ double kt_hydro64(const double* wl, const double* wr, int d,
-                                             double gamma, double inv_gm1, double* fout,
+                                             double gamma, double inv_gm1, bool knp, double* fout,
                                              int fstride, double& gl, double& gr) {
   double rl = wl[0], rr = wr[0], pl = wl[4], pr = wr[4];
   double ul = d == 0 ? wl[1] : (d == 1 ? wl[2] : wl[3]);
@@ -294,18 +295,46 @@ __device__ __forceinline__ double kt_hydro64(const double* wl, const double* wr,
   double cl = gpl * rsqrt64(gpl * rl);
   double cr = gpr * rsqrt64(gpr * rr);
   double a = dmaxp(dabs(ul) + cl, dabs(ur) + cr);
-  double hl = ul + a, hr = ur - a;
-  gl = rl * hl;
-  gr = rr * hr;
-  fout[0] = dhalf(gl + gr);
-  double pp = pl + pr;
+  if (!knp) {
+    double hl = ul + a, hr = ur - a;
+    gl = rl * hl;
+    gr = rr * hr;
+    fout[0] = dhalf(gl + gr);
+    double pp = pl + pr;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      double t = fma(wl[1 + c], gl, wr[1 + c] * gr);
+      fout[(1 + c) * fstride] = dhalf(c == d ? t + pp : t);
+    }
+    fout[4 * fstride] = dhalf(fma(El, hl, fma(pl, ul, fma(Er, hr, pr * ur))));
+    fout[5 * fstride] = dhalf(fma(wl[5], gl, wr[5] * gr));
+    gl = dhalf(gl);  // the species use Fhat_q = q_l gl + q_r gr
+    gr = dhalf(gr);
+    return a;
+  }
+  // Kurganov-Noelle-Petrova: one-sided speeds ap >= 0 >= am,
+  //   Fhat = (ap F_l - am F_r + ap am (U_r - U_l)) / (ap - am)
+  // which for advected quantities is q_l g_l + q_r g_r with
+  //   wl = ap/(ap - am), wr = -am/(ap - am), k_l = wl (u_l - am),
+  //   k_r = wr (u_r - ap), g = rho k; pressure enters with weights wl, wr.
+  double ap = dmaxp(dmax_s(ul + cl, ur + cr), 0.0);
+  double am = -dmaxp(dmax_s(cl - ul, cr - ur), 0.0);
+  double den = ap - am;
+  double rd = rcp64(den);
+  bool ok = dgt(den, 0.0);
+  double wL = ok ? ap * rd : 0.5, wR = ok ? -am * rd : 0.5;
+  double kl = wL * (ul - am), kr = wR * (ur - ap);
+  gl = rl * kl;
+  gr = rr * kr;
+  fout[0] = gl + gr;
+  double pw = fma(pl, wL, pr * wR);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
     double t = fma(wl[1 + c], gl, wr[1 + c] * gr);
-    fout[(1 + c) * fstride] = dhalf(c == d ? t + pp : t);
+    fout[(1 + c) * fstride] = c == d ? t + pw : t;
   }
-  fout[4 * fstride] = dhalf(fma(El, hl, fma(pl, ul, fma(Er, hr, pr * ur))));
-  fout[5 * fstride] = dhalf(fma(wl[5], gl, wr[5] * gr));
+  fout[4 * fstride] = fma(El, kl, fma(Er, kr, fma(wL, pl * ul, wR * (pr * ur))));
+  fout[5 * fstride] = fma(wl[5], gl, wr[5] * gr);
   return a;
 }
 
@@ -468,8 +497,8 @@ __device__ __forceinline__ void ppm_line32x2(const float2* w, const LineAddr& la
 // ------------------------------------------------------ step A3, mixed --
 // kt_hydro64's flux in binary32.  w: three pairs (rho, vx), (vy, vz), (p, phi).
 __device__ __forceinline__ float kt_hydro32(const float2* wl, const float2* wr, int d, float gamma,
-                                            float inv_gm1, float2* fout, int fstride, float& gl,
-                                            float& gr) {
+                                            float inv_gm1, bool knp, float2* fout, int fstride,
+                                            float& gl, float& gr) {
   float rl = wl[0].x, rr = wr[0].x, pl = wl[2].x, pr = wr[2].x;
   float vl[3] = {wl[0].y, wl[1].x, wl[1].y}, vr[3] = {wr[0].y, wr[1].x, wr[1].y};
   float ul = d == 0 ? vl[0] : (d == 1 ? vl[1] : vl[2]);
@@ -482,20 +511,33 @@ __device__ __forceinline__ float kt_hydro32(const float2* wl, const float2* wr, 
   float cl = gpl * rsqrtf(gpl * rl);
   float cr = gpr * rsqrtf(gpr * rr);
   float a = fmaxf(fabsf(ul) + cl, fabsf(ur) + cr);
-  float hl = ul + a, hr = ur - a;
-  gl = rl * hl;
-  gr = rr * hr;
-  float pp = pl + pr;
+  // weights of the left and right states (kt_hydro64): KT wl = wr = 1/2
+  float wL = 0.5f, wR = 0.5f, kl = 0.5f * (ul + a), kr = 0.5f * (ur - a);
+  if (knp) {
+    float ap = fmaxf(fmaxf(ul + cl, ur + cr), 0.0f);
+    float am = fminf(fminf(ul - cl, ur - cr), 0.0f);
+    float den = ap - am;
+    if (den > 0.0f) {
+      float rd = rcp32(den);
+      wL = ap * rd;
+      wR = -am * rd;
+    }
+    kl = wL * (ul - am);
+    kr = wR * (ur - ap);
+  }
+  gl = rl * kl;
+  gr = rr * kr;
+  float pw = fmaf(pl, wL, pr * wR);
   float m[3];
 #pragma unroll
   for (int c = 0; c < 3; c++) {
     float t = fmaf(vl[c], gl, vr[c] * gr);
-    m[c] = 0.5f * (c == d ? t + pp : t);
+    m[c] = c == d ? t + pw : t;
   }
-  fout[0] = make_float2(0.5f * (gl + gr), m[0]);
+  fout[0] = make_float2(gl + gr, m[0]);
   fout[fstride] = make_float2(m[1], m[2]);
-  fout[2 * fstride] = make_float2(0.5f * fmaf(El, hl, fmaf(pl, ul, fmaf(Er, hr, pr * ur))),
-                                  0.5f * fmaf(wl[2].y, gl, wr[2].y * gr));
+  fout[2 * fstride] = make_float2(fmaf(El, kl, fmaf(Er, kr, fmaf(wL, pl * ul, wR * (pr * ur)))),
+                                  fmaf(wl[2].y, gl, wr[2].y * gr));
   return a;
 }
 
@@ -615,7 +657,7 @@ template <int MODE, int NT, bool HYD>
 __device__ __forceinline__ void group_pass(
     const typename Prec<MODE>::V* W, typename Prec<MODE>::R* GG, typename Prec<MODE>::V* QS,
     int lch, int ng, int ex, int ey, int ez, typename Prec<MODE>::R gamma,
-    typename Prec<MODE>::R inv_gm1,
+    typename Prec<MODE>::R inv_gm1, bool knp,
     typename Prec<MODE>::Acc (&acc)[(TE * TE * TE + NT - 1) / NT][NGRP / Prec<MODE>::PACK],
     typename Prec<MODE>::R& amax) {
   typedef typename Prec<MODE>::R R;
@@ -661,8 +703,8 @@ __device__ __forceinline__ void group_pass(
             wr[j] = fr[j * fs];
           }
           R a, gl, gr;
-          if constexpr (MODE == 0) a = kt_hydro64(wl, wr, d, gamma, inv_gm1, fo, fs, gl, gr);
-          else a = kt_hydro32(wl, wr, d, gamma, inv_gm1, fo, fs, gl, gr);
+          if constexpr (MODE == 0) a = kt_hydro64(wl, wr, d, gamma, inv_gm1, knp, fo, fs, gl, gr);
+          else a = kt_hydro32(wl, wr, d, gamma, inv_gm1, knp, fo, fs, gl, gr);
           g[0] = gl;
           g[1] = gr;
           bool fvalid = (l % TE) < e_a && (l / TE) < e_b && i <= e_d;
@@ -676,8 +718,8 @@ __device__ __forceinline__ void group_pass(
 #pragma unroll
           for (int j = 0; j < NS; j++)
             if (j < ng) {
-              if constexpr (MODE == 0) fo[j * fs] = dhalf(fma(fo[j * fs], gl, fr[j * fs] * gr));
-              else fo[j * fs] = mul2(fma2(fo[j * fs], f2(gl), mul2(fr[j * fs], f2(gr))), f2(0.5f));
+              if constexpr (MODE == 0) fo[j * fs] = fma(fo[j * fs], gl, fr[j * fs] * gr);
+              else fo[j * fs] = fma2(fo[j * fs], f2(gl), mul2(fr[j * fs], f2(gr)));
             }
         }
       }
@@ -760,7 +802,7 @@ template <int MODE, int NT, int KC, class Fetch>
 __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int lch,
                                           double* __restrict__ out, double* __restrict__ amax_out,
                                           Status* __restrict__ status, double gamma_d,
-                                          int write_status, int prefetch) {
+                                          int write_status, int prefetch, bool knp) {
   typedef typename Prec<MODE>::R R;
   typedef typename Prec<MODE>::V V;
   typedef typename Prec<MODE>::Acc Acc;
@@ -842,7 +884,7 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
     R amax = R(0);
     {
       Acc acc[CPT][NS];
-      group_pass<MODE, NT, true>(W, GG, QS, lch, NS, ex, ey, ez, gamma, inv_gm1, acc, amax);
+      group_pass<MODE, NT, true>(W, GG, QS, lch, NS, ex, ey, ez, gamma, inv_gm1, knp, acc, amax);
       store_group<MODE, NT>(out, tile, ex, ey, ez, 0, 6, acc);
     }
 
@@ -898,7 +940,7 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
     if (nsp > 0) {
       Acc acc[CPT][NS];
       group_pass<MODE, NT, false>(W, GG, QS, lch, (nsp + PK - 1) / PK, ex, ey, ez, gamma, inv_gm1,
-                                  acc, amax);
+                                  knp, acc, amax);
       store_group<MODE, NT>(out, tile, ex, ey, ez, 6, nsp, acc);
     }
 
@@ -925,12 +967,13 @@ template <int MODE, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
                  double* __restrict__ out, double* __restrict__ amax_out,
-                 Status* __restrict__ status, double gamma_d, int write_status, int prefetch) {
+                 Status* __restrict__ status, double gamma_d, int write_status, int prefetch,
+                 int scheme) {
   (void)Fmax;  // the shared-memory layout does not depend on the field count
   // KC: read-region slots per load batch (more loads in flight with more
-  // registers per thread)
+  // registers per thread).  scheme: 0 Kurganov-Tadmor, 1 Kurganov-Noelle-Petrova.
   tile_loop<MODE, NT, MINB == 1 ? 4 : 2>(TileList{tiles}, n_tiles, lch, out, amax_out, status,
-                                         gamma_d, write_status, prefetch);
+                                         gamma_d, write_status, prefetch, scheme == 1);
 }
 
 }  // namespace hydro_dev

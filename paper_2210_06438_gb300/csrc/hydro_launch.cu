@@ -81,10 +81,11 @@ LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin
 
 cudaError_t launch_tiles(const LaunchCfg& cfg, hydro_precision_t prec, const hydro_dev::Tile* tiles,
                          int n_tiles, int Fmax, double* out, double* amax, hydro_dev::Status* status,
-                         double gamma, int write_status, cudaStream_t st) {
+                         double gamma, int write_status, cudaStream_t st, int scheme) {
   int lch = cfg.lch, pf = cfg.prefetch;
   void* args[] = {(void*)&tiles, (void*)&n_tiles, (void*)&Fmax, (void*)&lch, (void*)&out,
-                  (void*)&amax, (void*)&status, (void*)&gamma, (void*)&write_status, (void*)&pf};
+                  (void*)&amax, (void*)&status, (void*)&gamma, (void*)&write_status, (void*)&pf,
+                  (void*)&scheme};
   return cudaLaunchKernel(pick(prec, cfg.threads, cfg.minb), dim3(cfg.grid), dim3(cfg.threads), args,
                           (size_t)cfg.smem, st);
 }

@@ -64,10 +64,12 @@ template <int MODE, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 rhs_uniform_kernel(const hydro_subgrid_t* __restrict__ desc, int N, int F, int G, int tpe,
                    int n_tiles, int lch, double* __restrict__ out, double* __restrict__ amax_out,
-                   double gamma_d, int prefetch) {
-  // no status word: nonphysical inputs are not recorded by this entry point
+                   double gamma_d, int prefetch, int scheme) {
+  // no status word: nonphysical inputs are not recorded by this entry point;
+  // the flux scheme is a run-time argument as in rhs_tiles_kernel (always 0,
+  // Kurganov-Tadmor, here), so both kernels compile the same arithmetic
   tile_loop<MODE, NT, 4>(UniformDesc{desc, N, F, G, tpe}, n_tiles, lch, out, amax_out, nullptr,
-                      gamma_d, 0, prefetch);
+                         gamma_d, 0, prefetch, scheme == 1);
 }
 
 }  // namespace hydro_dev
@@ -157,12 +159,13 @@ extern "C" int hydro_rhs_noalloc(const hydro_subgrid_t* subgrids, int64_t n_subg
   if (n_tiles > 0x7fffffff) return HYDRO_EINVAL;
   if (tpe > 1 && (e = cudaMemsetAsync(out_amax, 0, (size_t)n_subgrids * sizeof(double), st)) != cudaSuccess)
     return hydro_host::cuda_fail(e, "cudaMemsetAsync(amax)");
-  int G = N + 2 * ghost, F = n_fields, nt = (int)n_tiles, lch = kLch, pf = 0, ntpe = tpe;
+  int G = N + 2 * ghost, F = n_fields, nt = (int)n_tiles, lch = kLch, pf = 0, ntpe = tpe, scheme = 0;
   int64_t grid64 = (int64_t)D->occ[prec == HYDRO_FP64 ? 0 : 1] * D->n_sm;
   int grid = (int)(n_tiles < grid64 ? n_tiles : grid64);
   size_t smem = (size_t)hydro_host::smem_bytes(prec, F, lch);
   void* args[] = {(void*)&ddesc, (void*)&N, (void*)&F, (void*)&G, (void*)&ntpe, (void*)&nt,
-                  (void*)&lch, (void*)&out_dUdt, (void*)&out_amax, (void*)&gamma, (void*)&pf};
+                  (void*)&lch, (void*)&out_dUdt, (void*)&out_amax, (void*)&gamma, (void*)&pf,
+                  (void*)&scheme};
   if ((e = cudaLaunchKernel(noalloc_func(prec), dim3(grid), dim3(kThreads), args, smem, st)) != cudaSuccess)
     return hydro_host::cuda_fail(e, "launch");
   return HYDRO_OK;

@@ -45,7 +45,8 @@ struct hydro_plan {
   double a_gamma = 0;
   int a_ws = 1;
   int a_pf = 0;
-  void* args[10];
+  int a_scheme = 0;
+  void* args[11];
   void* func = nullptr;
   bool use_graph = true;
   cudaGraph_t graph = nullptr;
@@ -106,7 +107,7 @@ static cudaError_t direct_launch(hydro_plan* p, cudaStream_t st) {
   if (p->multi && (e = cudaMemsetAsync(p->a_amax, 0, p->n * sizeof(double), st)) != cudaSuccess)
     return e;
   return launch_tiles(p->cfg, p->prec, p->a_tiles, p->a_n, p->a_F, p->a_out, p->a_amax,
-                      p->a_status, p->a_gamma, p->a_ws, st);
+                      p->a_status, p->a_gamma, p->a_ws, st, p->a_scheme);
 }
 
 // Time `reps` launches of configuration c; returns ms per launch or -1.
@@ -188,8 +189,9 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
   p->a_gamma = gamma;
   p->a_ws = 1;
   p->a_pf = p->cfg.prefetch;
-  void* a[10] = {&p->a_tiles, &p->a_n, &p->a_F, &p->a_lch, &p->a_out,
-                 &p->a_amax, &p->a_status, &p->a_gamma, &p->a_ws, &p->a_pf};
+  p->a_scheme = (flags & HYDRO_PLAN_KNP) ? 1 : 0;
+  void* a[11] = {&p->a_tiles, &p->a_n, &p->a_F, &p->a_lch, &p->a_out,
+                 &p->a_amax, &p->a_status, &p->a_gamma, &p->a_ws, &p->a_pf, &p->a_scheme};
   memcpy(p->args, a, sizeof a);
 
   if (flags & HYDRO_PLAN_AUTOTUNE) {

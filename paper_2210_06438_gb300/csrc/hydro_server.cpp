@@ -169,7 +169,7 @@ static int launch_batch(hydro_server* S, Slot& s, const std::vector<int64_t>& id
     return cuda_fail(e, "cudaMemcpyAsync(work list)");
   LaunchCfg c = default_cfg(S->cfg.prec, Fmax, S->n_sm, S->smem_optin, (int64_t)k);
   if ((e = launch_tiles(c, S->cfg.prec, s.dev_tiles, (int)k, Fmax, obase, abase, S->status,
-                        S->cfg.gamma, 1, s.stream)) != cudaSuccess)
+                        S->cfg.gamma, 1, s.stream, (S->cfg.flags & HYDRO_F_KNP) ? 1 : 0)) != cudaSuccess)
     return cuda_fail(e, "launch");
   if ((e = cudaEventRecord(s.done, s.stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   return HYDRO_OK;

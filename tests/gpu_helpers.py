@@ -28,7 +28,7 @@ def to_dev(blocks):
 
 
 def run_gpu(dev_blocks, dxs, prec=hydro.FP64, ghost=3, gamma=G53, form="rhs", streams=None,
-            plan_kw=None):
+            plan_kw=None, flags=0):
     items = []
     for U, dx in zip(dev_blocks, dxs):
         F = U.shape[0]
@@ -40,7 +40,7 @@ def run_gpu(dev_blocks, dxs, prec=hydro.FP64, ghost=3, gamma=G53, form="rhs", st
     out = torch.full((max(tot, 1),), float("nan"), dtype=torch.float64, device="cuda")
     amax = torch.full((max(n, 1),), float("nan"), dtype=torch.float64, device="cuda")
     if form == "rhs":
-        hydro.rhs(desc, out, amax, ghost=ghost, gamma=gamma, prec=prec, n=n)
+        hydro.rhs(desc, out, amax, ghost=ghost, gamma=gamma, prec=prec, n=n, flags=flags)
     elif form == "per_subgrid":
         hydro.rhs_per_subgrid(desc, out, amax, streams or [None], ghost=ghost, gamma=gamma,
                               prec=prec, n=n)
