@@ -228,6 +228,32 @@ int hydro_server_destroy(hydro_server_t* srv);
 int64_t hydro_now_ns(void);
 
 /* ---------------------------------------------------------------------------
+ * Domains: nb^3 same-level sub-grids of N^3 cells tiling a periodic cube,
+ * stored WITHOUT ghost layers: U[s][f][z][y][x] (DEVICE, binary64), sub-grid
+ * s = bx + nb (by + nb bz) holding cells [bx N, bx N + N) ... of the cube.
+ * Each sub-grid's 3-deep ghost shell is gathered inside the kernel from its
+ * neighbours (the ghost exchange that precedes every hydro iteration,
+ * Sec. V-A), so no ghosted copy exists.  nb * N >= 6; nb^3 N^3 n_fields
+ * < 2^31; dx the cell width of every sub-grid.
+ *
+ * hydro_domain_rhs -- dU/dt (packed exactly like U) and amax per sub-grid,
+ * the arithmetic of hydro_rhs_ex on the equivalent ghosted sub-grids.
+ * hydro_domain_stage -- one explicit stage in the same launch:
+ *   U_out = alpha * U0 + beta * (U + dt * dU/dt(U))
+ * (SSP-RK3 of Shu & Osher: (alpha, beta) = (0,1), (3/4,1/4), (1/3,2/3) with
+ * U0 the state at the start of the step; the paper's time step has three
+ * hydro iterations, Sec. VI-A).  U_out must not alias U; U0 may alias U or
+ * U_out.  flags: HYDRO_F_KNP or 0.  Both launch asynchronously on `stream`,
+ * allocate nothing, and record nonphysical input in the hydro_status word. */
+int hydro_domain_rhs(const double* U, int32_t nb, int32_t N, int32_t n_fields, double dx,
+                     double gamma, double* out_dUdt, double* out_amax, hydro_precision_t prec,
+                     void* stream, uint32_t flags);
+int hydro_domain_stage(const double* U, const double* U0, double alpha, double beta, double dt,
+                       int32_t nb, int32_t N, int32_t n_fields, double dx, double gamma,
+                       double* U_out, double* out_amax, hydro_precision_t prec, void* stream,
+                       uint32_t flags);
+
+/* ---------------------------------------------------------------------------
  * hydro_rhs_noalloc -- hydro_rhs_ex for callers that cannot allocate memory.
  * The paper has no counterpart: this is a service of the library.
  *

@@ -127,6 +127,9 @@ def load(build_if_missing: bool = False):
         "hydro_server_destroy": (ctypes.c_int, [P]),
         "hydro_now_ns": (i64, []),
         "hydro_rhs_noalloc": (ctypes.c_int, [SG, i64, i32, i32, i32, dbl, P, P, ctypes.c_int, P]),
+        "hydro_domain_rhs": (ctypes.c_int, [P, i32, i32, i32, dbl, dbl, P, P, ctypes.c_int, P, u32]),
+        "hydro_domain_stage": (ctypes.c_int, [P, P, dbl, dbl, dbl, i32, i32, i32, dbl, dbl, P, P,
+                                              ctypes.c_int, P, u32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -200,6 +203,23 @@ def rhs_noalloc(desc, out, amax, N, n_fields, ghost=3, gamma=5.0 / 3.0, prec=FP6
     n = len(desc) if n is None else n
     _check(load().hydro_rhs_noalloc(desc, n, int(N), ghost, int(n_fields), float(gamma), _ptr(out),
                                     _ptr(amax), int(prec), _stream(stream)), "hydro_rhs_noalloc")
+
+
+def domain_rhs(U, nb, N, n_fields, dx, out, amax, gamma=5.0 / 3.0, prec=FP64, stream=None,
+               flags=0):
+    """hydro_domain_rhs: periodic domain stored without ghosts ([s][f][N^3])."""
+    _check(load().hydro_domain_rhs(_ptr(U), int(nb), int(N), int(n_fields), float(dx),
+                                   float(gamma), _ptr(out), _ptr(amax), int(prec),
+                                   _stream(stream), int(flags)), "hydro_domain_rhs")
+
+
+def domain_stage(U, U0, alpha, beta, dt, nb, N, n_fields, dx, U_out, amax, gamma=5.0 / 3.0,
+                 prec=FP64, stream=None, flags=0):
+    """hydro_domain_stage: U_out = alpha U0 + beta (U + dt dU/dt(U)) in one launch."""
+    _check(load().hydro_domain_stage(_ptr(U), _ptr(U0), float(alpha), float(beta), float(dt),
+                                     int(nb), int(N), int(n_fields), float(dx), float(gamma),
+                                     _ptr(U_out), _ptr(amax), int(prec), _stream(stream),
+                                     int(flags)), "hydro_domain_stage")
 
 
 def rhs_per_subgrid(desc, out, amax, streams: Iterable, ghost=3, gamma=5.0 / 3.0, prec=FP64,

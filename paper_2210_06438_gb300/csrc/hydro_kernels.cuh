@@ -61,7 +61,7 @@ struct __align__(16) Tile {
   int G;               // stored edge N + 2*ghost
   short ox, oy, oz;    // tile origin (cells)
   short flags;         // bit 0: the sub-grid has more than one tile; bit 1: dx is a power of 2
-  int pad[2];
+  int pad[2];          // domain tiles: pad[0] = sub-grids per domain edge
 };
 static_assert(sizeof(Tile) == 64, "tile descriptor is 64 bytes");
 
@@ -759,11 +759,22 @@ __device__ __forceinline__ double pair_value(float h, float l, double scale, flo
   return (f2d_int(h) + f2d_int(l)) * scale;
 }
 
-// Store dU/dt = -(sum of differences)/dx of the fields f0 .. f0+nf-1.
-template <int MODE, int NT>
+// A fused explicit stage: out = alpha U0 + beta (U + dt dU/dt), with U, U0
+// and out in the domain layout (the packed output layout of the sub-grids).
+struct StageArgs {
+  const double* __restrict__ U;
+  const double* __restrict__ U0;
+  double alpha, beta, dt;
+  int on;
+};
+
+// Store dU/dt = -(sum of differences)/dx of the fields f0 .. f0+nf-1 (or,
+// with a stage, the updated state).
+template <int MODE, int NT, bool STAGE = false>
 __device__ __forceinline__ void store_group(
     double* __restrict__ out, const Tile& tile, int ex, int ey, int ez, int f0, int nf,
-    const typename Prec<MODE>::Acc (&acc)[(TE * TE * TE + NT - 1) / NT][NGRP / Prec<MODE>::PACK]) {
+    const typename Prec<MODE>::Acc (&acc)[(TE * TE * TE + NT - 1) / NT][NGRP / Prec<MODE>::PACK],
+    const StageArgs& stage = StageArgs{nullptr, nullptr, 0.0, 0.0, 0.0, 0}) {
   constexpr int CPT = (TE * TE * TE + NT - 1) / NT;
   const int tid = threadIdx.x, N = tile.N;
   const long long n3 = (long long)N * N * N;
@@ -789,6 +800,12 @@ __device__ __forceinline__ void store_group(
               v = (j & 1) ? pair_value(a.h.y, a.l.y, scale, sf, pow2)
                           : pair_value(a.h.x, a.l.x, scale, sf, pow2);
             }
+            if constexpr (STAGE) {
+              if (stage.on) {
+                long long e = (o - out) + j * n3;  // same index in U, U0 and out
+                v = fma(stage.alpha, __ldg(stage.U0 + e), stage.beta * fma(stage.dt, v, __ldg(stage.U + e)));
+              }
+            }
             o[j * n3] = v;
           }
       }
@@ -798,11 +815,16 @@ __device__ __forceinline__ void store_group(
 
 // The persistent tile loop; `fetch(t)` returns tile t's descriptor; KC read-
 // region slots of a thread are loaded per batch.
-template <int MODE, int NT, int KC, class Fetch>
+// DOMAIN: the tiles belong to a periodic cube of pad[0]^3 sub-grids stored
+// without ghosts ([s][f][N^3], s = bx + nb (by + nb bz)); each tile's read
+// region is gathered from the neighbouring sub-grids' interiors, and `stage`
+// may turn the output into an explicit stage update.
+template <int MODE, int NT, int KC, class Fetch, bool DOMAIN = false>
 __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int lch,
                                           double* __restrict__ out, double* __restrict__ amax_out,
                                           Status* __restrict__ status, double gamma_d,
-                                          int write_status, int prefetch, bool knp) {
+                                          int write_status, int prefetch, bool knp,
+                                          const StageArgs& stage = StageArgs{nullptr, nullptr, 0.0, 0.0, 0.0, 0}) {
   typedef typename Prec<MODE>::R R;
   typedef typename Prec<MODE>::V V;
   typedef typename Prec<MODE>::Acc Acc;
@@ -826,17 +848,29 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
     const Tile tile = fetch(t);
     const int F = tile.F, G = tile.G, N = tile.N, gh = (tile.G - tile.N) >> 1;
     const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
-    const long long plane = (long long)G * G * G;
+    const long long plane = DOMAIN ? (long long)N * N * N : (long long)G * G * G;  // field stride
+    const int nb = DOMAIN ? tile.pad[0] : 0;
 
     // offset of read-region slot s within a field of the stored block; -1 if
     // the slot is outside the (possibly partial) tile's read region: at most
-    // one coordinate outside the tile, and that one at most 3 cells out
+    // one coordinate outside the tile, and that one at most 3 cells out.  In
+    // a domain the cell is located by its periodic global coordinates.
     auto slot_offset = [&](int s) -> int {
       int x, y, z;
       cell_of(s < STAR ? s : 0, x, y, z);
       int outside = (x < 0 || x >= ex) + (y < 0 || y >= ey) + (z < 0 || z >= ez);
       bool valid = s < STAR && outside <= 1 && x < ex + 3 && y < ey + 3 && z < ez + 3;
-      return valid ? ((tile.oz + z + gh) * G + (tile.oy + y + gh)) * G + (tile.ox + x + gh) : -1;
+      if (!valid) return -1;
+      if constexpr (DOMAIN) {
+        const int L = nb * N, sb = tile.sub;
+        int gx = ((sb % nb) * N + tile.ox + x + L) % L;
+        int gy = (((sb / nb) % nb) * N + tile.oy + y + L) % L;
+        int gz = ((sb / (nb * nb)) * N + tile.oz + z + L) % L;
+        int blk = ((gz / N) * nb + gy / N) * nb + gx / N;
+        return blk * F * N * N * N + ((gz % N) * N + gy % N) * N + gx % N;
+      } else {
+        return ((tile.oz + z + gh) * G + (tile.oy + y + gh)) * G + (tile.ox + x + gh);
+      }
     };
 
     // ---- A0/A1 (hydro group): rho, s, E, tau -> rho, v, p, phi.  In each
@@ -878,14 +912,15 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
       }
     }
     bad = __syncthreads_or(bad);
-    if (prefetch && t + (int)gridDim.x < n_tiles) prefetch_tile_l2(fetch(t + gridDim.x), tid, NT, prefetch);
+    if (!DOMAIN && prefetch && t + (int)gridDim.x < n_tiles)
+      prefetch_tile_l2(fetch(t + gridDim.x), tid, NT, prefetch);
 
     // ---- hydro group: rho, momentum, E, tau
     R amax = R(0);
     {
       Acc acc[CPT][NS];
       group_pass<MODE, NT, true>(W, GG, QS, lch, NS, ex, ey, ez, gamma, inv_gm1, knp, acc, amax);
-      store_group<MODE, NT>(out, tile, ex, ey, ez, 0, 6, acc);
+      store_group<MODE, NT, DOMAIN>(out, tile, ex, ey, ez, 0, 6, acc, stage);
     }
 
     // ---- A0/A1 (species): X_k = rho_k / rho into the group slots
@@ -941,7 +976,7 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
       Acc acc[CPT][NS];
       group_pass<MODE, NT, false>(W, GG, QS, lch, (nsp + PK - 1) / PK, ex, ey, ez, gamma, inv_gm1,
                                   knp, acc, amax);
-      store_group<MODE, NT>(out, tile, ex, ey, ez, 6, nsp, acc);
+      store_group<MODE, NT, DOMAIN>(out, tile, ex, ey, ez, 6, nsp, acc, stage);
     }
 
     // ---- A5: largest signal speed of the tile
@@ -974,6 +1009,44 @@ rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
   // registers per thread).  scheme: 0 Kurganov-Tadmor, 1 Kurganov-Noelle-Petrova.
   tile_loop<MODE, NT, MINB == 1 ? 4 : 2>(TileList{tiles}, n_tiles, lch, out, amax_out, status,
                                          gamma_d, write_status, prefetch, scheme == 1);
+}
+
+// Tiles of a periodic domain of nb^3 sub-grids of N^3 (F fields each),
+// stored without ghosts; computed on the fly, no work list.
+struct DomainTiles {
+  const double* __restrict__ U;
+  int nb, N, F, tpe;  // tpe: tiles per sub-grid edge
+  double inv_dx;
+  short flags;        // bit 1: dx a power of two
+  __device__ __forceinline__ Tile operator()(int t) const {
+    const int tps = tpe * tpe * tpe;
+    const int s = t / tps, k = t - s * tps;
+    Tile tile;
+    tile.U = U;
+    tile.out_off = (long long)s * F * N * N * N;
+    tile.amax_off = s;
+    tile.inv_dx = inv_dx;
+    tile.sub = s;
+    tile.N = N;
+    tile.F = F;
+    tile.G = N;
+    tile.ox = (short)((k % tpe) * TE);
+    tile.oy = (short)(((k / tpe) % tpe) * TE);
+    tile.oz = (short)((k / (tpe * tpe)) * TE);
+    tile.flags = (short)((tps > 1 ? 1 : 0) | (flags & 2));
+    tile.pad[0] = nb;
+    tile.pad[1] = 0;
+    return tile;
+  }
+};
+
+template <int MODE, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+rhs_domain_kernel(DomainTiles dom, int n_tiles, int lch, double* __restrict__ out,
+                  double* __restrict__ amax_out, Status* __restrict__ status, double gamma_d,
+                  int write_status, int scheme, StageArgs stage) {
+  tile_loop<MODE, NT, MINB == 1 ? 4 : 2, DomainTiles, true>(dom, n_tiles, lch, out, amax_out, status,
+                                                            gamma_d, write_status, 0, scheme == 1, stage);
 }
 
 }  // namespace hydro_dev
