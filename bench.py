@@ -390,6 +390,8 @@ def run_ours(args, rank, world):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    hbm_peak_early = measured_peaks().get("hbm_gbs", 6800.0)
+
     # ---- headline: binary64 aggregated form
     for _ in range(args.warmup):
         plan64.execute(out, amax, stream)
@@ -431,6 +433,32 @@ def run_ours(args, rank, world):
     ms_ps64 = timed_pool(hydro.FP64, ps_steps)
     ms_psmx = timed_pool(hydro.FP32_FLUX_FP64_ACC, ps_steps)
 
+    # ---- domain form: the same cells stored without ghosts, ghost shells
+    # gathered in the kernel; and one SSP-RK3 step of three fused stages
+    dom = batch.blocks[:, :, 3:-3, 3:-3, 3:-3].contiguous()
+    dout = torch.empty_like(dom)
+    dtmp = torch.empty_like(dom)
+    nbd = args.domain // 8
+
+    def dom_rhs(prec):
+        hydro.domain_rhs(dom, nbd, 8, batch.nf, batch.dx, dout, amax, prec=prec, stream=stream)
+
+    def rk3_step(prec):
+        dt = 1e-4
+        hydro.domain_stage(dom, dom, 0.0, 1.0, dt, nbd, 8, batch.nf, batch.dx, dout, amax, prec=prec,
+                           stream=stream)
+        hydro.domain_stage(dout, dom, 0.75, 0.25, dt, nbd, 8, batch.nf, batch.dx, dtmp, amax, prec=prec,
+                           stream=stream)
+        hydro.domain_stage(dtmp, dom, 1.0 / 3.0, 2.0 / 3.0, dt, nbd, 8, batch.nf, batch.dx, dout, amax,
+                           prec=prec, stream=stream)
+
+    ms_dom64 = time_steps(lambda: dom_rhs(hydro.FP64), args.steps, args.warmup, stream)
+    ms_dommx = time_steps(lambda: dom_rhs(hydro.FP32_FLUX_FP64_ACC), args.steps, args.warmup, stream)
+    ms_rk64 = time_steps(lambda: rk3_step(hydro.FP64), max(1, args.steps // 2), 1, stream)
+    ms_rkmx = time_steps(lambda: rk3_step(hydro.FP32_FLUX_FP64_ACC), max(1, args.steps // 2), 1, stream)
+    dom_bytes = batch.n * (synth.star_cells(8) + 512) * batch.nf * 8
+    del dom, dout, dtmp
+
     # ---- end to end through the C ABI with host buffers
     host_in = torch.empty(batch.blocks.shape, dtype=torch.float64, pin_memory=True)
     host_in.copy_(batch.blocks)
@@ -459,8 +487,8 @@ def run_ours(args, rank, world):
         }
 
     # ---- max over ranks
-    ms64, msmx, ms_ps64, ms_psmx, ms_e2e = max_over_ranks([ms64, msmx, ms_ps64, ms_psmx, ms_e2e],
-                                                          world, device=dev)
+    (ms64, msmx, ms_ps64, ms_psmx, ms_e2e, ms_dom64, ms_dommx, ms_rk64, ms_rkmx) = max_over_ranks(
+        [ms64, msmx, ms_ps64, ms_psmx, ms_e2e, ms_dom64, ms_dommx, ms_rk64, ms_rkmx], world, device=dev)
     if rank != 0:
         return
 
@@ -516,6 +544,13 @@ def run_ours(args, rank, world):
                                  "conservation_drift": drift},
             "fp64_per_subgrid": {"value": cells * world / (ms_ps64 * 1e-3), "ms": ms_ps64,
                                  "streams": args.streams, "launches": batch.n},
+            "fp64_domain": {"value": cells * world / (ms_dom64 * 1e-3), "ms": ms_dom64,
+                            "note": "ghost shells gathered in the kernel from ghost-free storage"},
+            "mixed_domain": {"value": cells * world / (ms_dommx * 1e-3), "ms": ms_dommx,
+                             "hbm_frac": dom_bytes / (ms_dommx * 1e-3) * 1e-9 / hbm_peak_early},
+            "fp64_rk3_step": {"value": 3 * cells * world / (ms_rk64 * 1e-3), "ms": ms_rk64,
+                              "note": "three fused SSP-RK3 stages; value = stage cell-updates/s"},
+            "mixed_rk3_step": {"value": 3 * cells * world / (ms_rkmx * 1e-3), "ms": ms_rkmx},
             "mixed_per_subgrid": {"value": cells * world / (ms_psmx * 1e-3), "ms": ms_psmx,
                                   "streams": args.streams, "launches": batch.n},
         },
