@@ -98,6 +98,10 @@ int hydro_rhs(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t N, in
 #define HYDRO_F_KNP 2u       /* central-upwind flux with one-sided local speeds (Kurganov,
                                 Noelle & Petrova 2001) instead of the single-speed
                                 Kurganov-Tadmor flux; same signal speed for amax */
+#define HYDRO_F_REGISTER_LOADS 4u /* mixed form: the kernel that loads the read region
+                                     through registers instead of the default pipelined
+                                     kernel (asynchronous copies into shared memory,
+                                     one CTA of 576 threads per SM); same results */
 int hydro_rhs_ex(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t N, int32_t ghost,
                  int32_t n_fields, double gamma, double* out_dUdt, double* out_amax,
                  hydro_precision_t prec, void* stream, uint32_t flags);
@@ -123,6 +127,8 @@ typedef struct hydro_plan hydro_plan_t;
 #define HYDRO_PLAN_AUTOTUNE 1u /* time candidate launch shapes and keep the fastest */
 #define HYDRO_PLAN_NO_GRAPH 2u /* launch directly instead of replaying a graph */
 #define HYDRO_PLAN_KNP 4u      /* the flux of HYDRO_F_KNP */
+#define HYDRO_PLAN_PIPELINED 8u       /* mixed form: consider only the pipelined kernel */
+#define HYDRO_PLAN_REGISTER_LOADS 16u /* mixed form: consider only the register-load kernels */
 
 typedef struct {
   int64_t n_subgrids;

@@ -47,7 +47,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(OBJDIR, exist_ok=True)
     nvcc = _nvcc()
-    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC]
+    # -fmad=false: no implicit multiply-add contraction; every fused operation
+    # is written out in the source, so all kernel variants (launch shapes, the
+    # pipelined and register-load mixed kernels) compute the same bits.
+    common = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE,
+              "-I", CSRC]
 
     def compile_one(src):
         obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")

@@ -32,8 +32,11 @@ FP32_FLUX_FP64_ACC = 1
 PLAN_AUTOTUNE = 1
 PLAN_NO_GRAPH = 2
 PLAN_KNP = 4
+PLAN_PIPELINED = 8
+PLAN_REGISTER_LOADS = 16
 F_NO_STATUS = 1
 F_KNP = 2
+F_REGISTER_LOADS = 4
 
 
 
@@ -245,11 +248,11 @@ class Plan:
     """hydro_plan_*: fixed batch, tuned launch shape, CUDA-graph replay."""
 
     def __init__(self, desc, ghost=3, gamma=5.0 / 3.0, prec=FP64, autotune=False, graph=True,
-                 stream=None, n=None, knp=False):
+                 stream=None, n=None, knp=False, flags=0):
         n = len(desc) if n is None else n
         self._desc = desc  # keep the pointers' owner alive
         h = ctypes.c_void_p()
-        flags = ((PLAN_AUTOTUNE if autotune else 0) | (0 if graph else PLAN_NO_GRAPH)
+        flags = (int(flags) | (PLAN_AUTOTUNE if autotune else 0) | (0 if graph else PLAN_NO_GRAPH)
                  | (PLAN_KNP if knp else 0))
         _check(load().hydro_plan_create(desc, n, ghost, float(gamma), int(prec), flags,
                                         _stream(stream), ctypes.byref(h)), "hydro_plan_create")

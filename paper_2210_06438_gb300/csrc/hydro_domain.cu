@@ -29,12 +29,13 @@ namespace {
 struct Shape {
   int threads, minb, lch;
 };
-// the launch shapes the autotuner picks for the sub-grid batches
-const Shape kShape[2] = {{512, 1, 64}, {256, 2, 64}};
+// the launch shapes the autotuner picks for the sub-grid batches: binary64
+// 512 threads, mixed the pipelined kernel
+const Shape kShape[2] = {{512, 1, 64}, {hydro_host::kPipeThreads, 1, 64}};
 
 void* domain_func(hydro_precision_t prec) {
   return prec == HYDRO_FP64 ? (void*)&hydro_dev::rhs_domain_kernel<0, 512, 1>
-                            : (void*)&hydro_dev::rhs_domain_kernel<1, 256, 2>;
+                            : (void*)&hydro_dev::rhs_domain_pipe_kernel<hydro_host::kPipeThreads>;
 }
 
 struct DomDev {
@@ -58,7 +59,7 @@ int domain_setup(DomDev** out) {
       return hydro_host::cuda_fail(e, "cudaDeviceGetAttribute");
     for (int m = 0; m < 2; m++) {
       hydro_precision_t prec = (hydro_precision_t)m;
-      int smem = hydro_host::smem_bytes(prec, HYDRO_MAX_FIELDS, kShape[m].lch);
+      int smem = hydro_host::smem_bytes(prec, HYDRO_MAX_FIELDS, kShape[m].lch, kShape[m].threads);
       if ((e = cudaFuncSetAttribute(domain_func(prec), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     optin - 1024)) != cudaSuccess)
         return hydro_host::cuda_fail(e, "cudaFuncSetAttribute");
@@ -112,7 +113,7 @@ int domain_launch(const double* U, const double* U0, double alpha, double beta, 
   int nt = (int)n_tiles, lch = sh.lch, ws = 1, scheme = (flags & HYDRO_F_KNP) ? 1 : 0;
   long long g64 = (long long)D->occ[prec == HYDRO_FP64 ? 0 : 1] * D->n_sm;
   int grid = (int)(n_tiles < g64 ? n_tiles : g64);
-  size_t smem = (size_t)hydro_host::smem_bytes(prec, F, lch);
+  size_t smem = (size_t)hydro_host::smem_bytes(prec, F, lch, sh.threads);
   void* args[] = {(void*)&dom, (void*)&nt, (void*)&lch, (void*)&out, (void*)&amax, (void*)&status,
                   (void*)&gamma, (void*)&ws, (void*)&scheme, (void*)&sa};
   if ((e = cudaLaunchKernel(domain_func(prec), dim3(grid), dim3(sh.threads), args, smem, st)) != cudaSuccess)

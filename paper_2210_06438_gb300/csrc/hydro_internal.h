@@ -18,7 +18,7 @@ namespace hydro_host {
 
 // Launch shape of the tile kernel.
 struct LaunchCfg {
-  int threads = 256;   // threads per CTA (128, 256 or 512)
+  int threads = 256;   // threads per CTA (128, 256 or 512; 576: the pipelined mixed kernel)
   int minb = 1;        // kernel variant: minimum resident CTAs per SM it was compiled for
   int lch = 32;        // lines per chunk of the reconstruct/flux phases (16, 32 or 64)
   int grid = 0;        // CTAs (persistent: a multiple of the SM count)
@@ -28,11 +28,16 @@ struct LaunchCfg {
 };
 
 cudaError_t kernels_init(int smem_optin);
-int smem_bytes(hydro_precision_t prec, int Fmax, int lch);
+// threads == kPipeThreads selects the pipelined mixed kernel's layout
+int smem_bytes(hydro_precision_t prec, int Fmax, int lch, int threads = 256);
 int occupancy(hydro_precision_t prec, int threads, int minb, int smem);
 int num_variants();
 void variant(int i, int* threads, int* minb);
-LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin, int64_t n_tiles);
+bool variant_exists(hydro_precision_t prec, int threads, int minb);
+constexpr int kPipeThreads = 576;
+// pipelined: use the pipelined mixed kernel (ignored for binary64)
+LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin, int64_t n_tiles,
+                      bool pipelined = true);
 // scheme: 0 Kurganov-Tadmor flux, 1 Kurganov-Noelle-Petrova
 cudaError_t launch_tiles(const LaunchCfg& cfg, hydro_precision_t prec, const hydro_dev::Tile* tiles,
                          int n_tiles, int Fmax, double* out, double* amax, hydro_dev::Status* status,

@@ -1011,6 +1011,311 @@ rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
                                          gamma_d, write_status, prefetch, scheme == 1);
 }
 
+// ================================================ pipelined mixed kernel ==
+// The mixed form with the read region moved by asynchronous copies
+// (cp.async, global -> shared, no registers held) into a staging buffer, one
+// field group ahead: the species of tile t arrive while its hydro group is
+// reconstructed and fluxed, and the hydro group of the CTA's next tile while
+// its species are.  One CTA of PNT threads per SM; the three directions are
+// reconstructed together, so every phase divides evenly over the threads:
+//   PPM   3 directions x 64 lines x 3 field pairs = 576 tasks
+//   flux  3 rounds (one per direction) of 64 lines x 9 faces = 576 faces
+//   A4    one interior cell per thread (threads 0..511)
+// Shared memory (bytes): S  [6][STAR] binary64 staging      79872
+//                        W  [3][STAR] float2 primitives     39936
+//                        RR [STAR] float 1/rho               6656
+//                        GG [3][NLN][NFC][2] float          13824
+//                        QS [3][2][3][NLN][NFC] float2      82944
+constexpr int PNT = 3 * NLN * 3;  // 576
+constexpr int PSPT = (STAR + PNT - 1) / PNT;  // read-region slots per thread: 3
+__host__ __device__ constexpr size_t pipe_smem_bytes() {
+  return (size_t)6 * STAR * 8 + 3 * STAR * 8 + STAR * 4 + 3 * NLN * NFC * 2 * 4 + 3 * 2 * 3 * NLN * NFC * 8;
+}
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Read-region geometry of one thread's slots, computed once per kernel:
+// tile-local (x, y, z) packed as three signed bytes.
+struct SlotXYZ {
+  int p[PSPT];
+  __device__ __forceinline__ void init(int tid) {
+#pragma unroll
+    for (int k = 0; k < PSPT; k++) {
+      int s = tid + k * PNT, x = 0, y = 0, z = 0;
+      if (s < STAR) cell_of(s, x, y, z);
+      p[k] = (x & 0xff) | ((y & 0xff) << 8) | ((z & 0xff) << 16);
+    }
+  }
+  __device__ __forceinline__ void get(int k, int& x, int& y, int& z) const {
+    x = (int)(signed char)(p[k] & 0xff);
+    y = (int)(signed char)((p[k] >> 8) & 0xff);
+    z = (int)(signed char)((p[k] >> 16) & 0xff);
+  }
+};
+
+// Offset (doubles, within one field) of read-region cell (x, y, z) of the
+// tile, or -1 if the (possibly partial) tile does not read it.
+__device__ __forceinline__ bool pipe_valid(int x, int y, int z, int ex, int ey, int ez) {
+  int outside = (x < 0 || x >= ex) + (y < 0 || y >= ey) + (z < 0 || z >= ez);
+  return outside <= 1 && x < ex + 3 && y < ey + 3 && z < ez + 3;
+}
+template <bool DOMAIN>
+__device__ __forceinline__ int pipe_offset(const Tile& tile, int x, int y, int z, int ex, int ey, int ez) {
+  if (!pipe_valid(x, y, z, ex, ey, ez)) return -1;
+  const int N = tile.N;
+  if constexpr (DOMAIN) {
+    const int nb = tile.pad[0], L = nb * N, sb = tile.sub;
+    int gx = ((sb % nb) * N + tile.ox + x + L) % L;
+    int gy = (((sb / nb) % nb) * N + tile.oy + y + L) % L;
+    int gz = ((sb / (nb * nb)) * N + tile.oz + z + L) % L;
+    int blk = ((gz / N) * nb + gy / N) * nb + gx / N;
+    return blk * tile.F * N * N * N + ((gz % N) * N + gy % N) * N + gx % N;
+  } else {
+    const int G = tile.G, gh = (G - N) >> 1;
+    return ((tile.oz + z + gh) * G + (tile.oy + y + gh)) * G + (tile.ox + x + gh);
+  }
+}
+
+// Issue the copies of fields f0 .. f0+nf-1 of the tile's read region into S.
+template <bool DOMAIN>
+__device__ __forceinline__ void pipe_issue(const Tile& tile, const SlotXYZ& sx, double* S, int f0, int nf) {
+  const int N = tile.N;
+  const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
+  const long long plane = DOMAIN ? (long long)N * N * N : (long long)tile.G * tile.G * tile.G;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < PSPT; k++) {
+    int s = tid + k * PNT;
+    if (s >= STAR) continue;
+    int x, y, z;
+    sx.get(k, x, y, z);
+    int off = pipe_offset<DOMAIN>(tile, x, y, z, ex, ey, ez);
+    if (off < 0) continue;
+    const double* src = tile.U + (long long)f0 * plane + off;
+#pragma unroll
+    for (int f = 0; f < 6; f++)
+      if (f < nf) cp_async8(S + f * STAR + s, src + f * plane);
+  }
+  cp_async_commit();
+}
+
+template <class Fetch, bool DOMAIN>
+__device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, double* __restrict__ out,
+                                               double* __restrict__ amax_out, Status* __restrict__ status,
+                                               double gamma_d, int write_status, bool knp,
+                                               const StageArgs& stage) {
+  typedef P2 Acc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* S = reinterpret_cast<double*>(smem_raw);
+  float2* W = reinterpret_cast<float2*>(S + 6 * STAR);
+  float* RR = reinterpret_cast<float*>(W + 3 * STAR);
+  float* GG = RR + STAR;
+  float2* QS = reinterpret_cast<float2*>(GG + 3 * NLN * NFC * 2);
+  __shared__ double red[PNT / 32];
+  const int tid = threadIdx.x;
+  const float gamma = (float)gamma_d;
+  const float inv_gm1 = (float)(1.0 / (gamma_d - 1.0));
+  const float gm1f = (float)(gamma_d - 1.0);
+  const bool g53 = gamma_d == 5.0 / 3.0;
+  constexpr int FS = NLN * NFC;  // stride between pair slots of QS (576)
+  // QS block of (direction d, side 0 left / 1 right, pair j)
+  auto qs = [&](int d, int side, int j) { return QS + ((d * 2 + side) * 3 + j) * FS; };
+  SlotXYZ sx;
+  sx.init(tid);
+
+  int t = blockIdx.x;
+  if (t < n_tiles) pipe_issue<DOMAIN>(fetch(t), sx, S, 0, 6);
+  for (; t < n_tiles; t += gridDim.x) {
+    const Tile tile = fetch(t);
+    const int F = tile.F, N = tile.N, nsp = F - 6;
+    const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
+    const bool full = ex == TE && ey == TE && ez == TE;
+    const int tn = t + (int)gridDim.x;
+
+    // ---- A0/A1 hydro: staged binary64 (rho, s, E, tau) -> binary32 primitives
+    cp_async_wait_all();
+    __syncthreads();
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < PSPT; k++) {
+      int s = tid + k * PNT;
+      if (s >= STAR) continue;
+      int x, y, z;
+      sx.get(k, x, y, z);
+      bool valid = full || pipe_valid(x, y, z, ex, ey, ez);
+      float w[6], r;
+      if (valid) {
+        double u[6];
+#pragma unroll
+        for (int f = 0; f < 6; f++) u[f] = S[f * STAR + s];
+        bad |= prim_mixed(u, gamma_d, gamma, gm1f, g53, w, r);
+      } else {
+#pragma unroll
+        for (int f = 0; f < 6; f++) w[f] = (f == 0 || f == 4) ? 1.0f : 0.0f;
+        r = 1.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < 3; j++) W[j * STAR + s] = make_float2(w[2 * j], w[2 * j + 1]);
+      RR[s] = r;
+    }
+    bad = __syncthreads_or(bad);
+    // the staging buffer is free: species of this tile, or the next tile
+    if (nsp > 0) pipe_issue<DOMAIN>(tile, sx, S, 6, nsp);
+    else if (tn < n_tiles) pipe_issue<DOMAIN>(fetch(tn), sx, S, 0, 6);
+
+    float amax = 0.0f;
+    Acc acc[1][3];
+    // ---- A2 hydro, three directions at once
+    {
+      const int d = tid / (3 * NLN), rem = tid - d * 3 * NLN, j = rem / NLN, l = rem - j * NLN;
+      LineAddr la = line_addr(d, l);
+      ppm_line32x2(W + j * STAR, la, qs(d, 0, j) + l * NFC, qs(d, 1, j) + l * NFC);
+    }
+    __syncthreads();
+    // ---- A3 hydro: one direction per round, 576 faces each
+    {
+      const int l = tid / NFC, i = tid - l * NFC;
+#pragma unroll 1
+      for (int d = 0; d < 3; d++) {
+        float2* fo = qs(d, 0, 0) + l * NFC + i;
+        const float2* fr = qs(d, 1, 0) + l * NFC + i;
+        float2 wl[3], wr[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+          wl[j] = fo[j * FS];
+          wr[j] = fr[j * FS];
+        }
+        float gl, gr;
+        float a = kt_hydro32(wl, wr, d, gamma, inv_gm1, knp, fo, FS, gl, gr);
+        float* g = GG + ((d * NLN + l) * NFC + i) * 2;
+        g[0] = gl;
+        g[1] = gr;
+        const int e_d = d == 0 ? ex : (d == 1 ? ey : ez);
+        const int e_a = d == 0 ? ey : ex;
+        const int e_b = d == 2 ? ey : ez;
+        if ((l % TE) < e_a && (l / TE) < e_b && i <= e_d) amax = fmaxf(amax, a);
+      }
+    }
+    __syncthreads();
+    // ---- A4 hydro: the flux differences of the thread's cell, x, y, z
+    auto diff_pass = [&](int npair) {
+      if (tid < TE * TE * TE) {
+        const int x = tid % TE, y = (tid / TE) % TE, z = tid / (TE * TE);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          const int l = d == 0 ? z * TE + y : (d == 1 ? z * TE + x : y * TE + x);
+          const int pos = d == 0 ? x : (d == 1 ? y : z);
+          const float2* fl = qs(d, 0, 0) + l * NFC + pos;
+#pragma unroll
+          for (int j = 0; j < 3; j++)
+            if (j < npair) acc_pair2(acc[0][j], fl[j * FS + 1], fl[j * FS], d == 0);
+        }
+      }
+    };
+    diff_pass(3);
+    store_group<1, PNT, DOMAIN>(out, tile, ex, ey, ez, 0, 6, acc, stage);
+
+    if (nsp > 0) {
+      const int npair = (nsp + 1) / 2;
+      // ---- A0/A1 species: X_k = rho_k / rho
+      cp_async_wait_all();
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < PSPT; k++) {
+        int s = tid + k * PNT;
+        if (s >= STAR) continue;
+        int x, y, z;
+        sx.get(k, x, y, z);
+        bool valid = full || pipe_valid(x, y, z, ex, ey, ez);
+        float r = RR[s];
+        float xs[6];
+#pragma unroll
+        for (int f = 0; f < 6; f++) {
+          xs[f] = 0.0f;
+          if (f < nsp && valid) {
+            double v = S[f * STAR + s];
+            bad |= !dfinite(v);
+            xs[f] = d2f_int(v) * r;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+          if (j < npair) W[j * STAR + s] = make_float2(xs[2 * j], xs[2 * j + 1]);
+      }
+      bad = __syncthreads_or(bad);
+      if (tn < n_tiles) pipe_issue<DOMAIN>(fetch(tn), sx, S, 0, 6);
+      // ---- A2 species
+      {
+        const int d = tid / (3 * NLN), rem = tid - d * 3 * NLN, j = rem / NLN, l = rem - j * NLN;
+        if (j < npair) {
+          LineAddr la = line_addr(d, l);
+          ppm_line32x2(W + j * STAR, la, qs(d, 0, j) + l * NFC, qs(d, 1, j) + l * NFC);
+        }
+      }
+      __syncthreads();
+      // ---- A3 species: q_l g_l + q_r g_r
+      {
+        const int l = tid / NFC, i = tid - l * NFC;
+#pragma unroll 1
+        for (int d = 0; d < 3; d++) {
+          float2* fo = qs(d, 0, 0) + l * NFC + i;
+          const float2* fr = qs(d, 1, 0) + l * NFC + i;
+          const float* g = GG + ((d * NLN + l) * NFC + i) * 2;
+          const float gl = g[0], gr = g[1];
+#pragma unroll
+          for (int j = 0; j < 3; j++)
+            if (j < npair) fo[j * FS] = fma2(fo[j * FS], f2(gl), mul2(fr[j * FS], f2(gr)));
+        }
+      }
+      __syncthreads();
+      diff_pass(npair);
+      store_group<1, PNT, DOMAIN>(out, tile, ex, ey, ez, 6, nsp, acc, stage);
+    }
+    if (bad && tid == 0 && write_status) {
+      atomicOr(&status->flags, 1u);
+      atomicMin(&status->first_bad, (unsigned long long)tile.sub);
+    }
+
+    // ---- A5: largest signal speed of the tile
+    double am = (double)amax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) am = dmaxp(am, __shfl_xor_sync(0xffffffffu, am, o));
+    if ((tid & 31) == 0) red[tid >> 5] = am;
+    __syncthreads();
+    if (tid == 0) {
+      double m = red[0];
+      for (int w = 1; w < PNT / 32; w++) m = dmaxp(m, red[w]);
+      if (tile.flags & 1)
+        atomicMax(reinterpret_cast<unsigned long long*>(amax_out + tile.amax_off),
+                  (unsigned long long)__double_as_longlong(m));
+      else
+        amax_out[tile.amax_off] = m;
+    }
+  }
+  cp_async_wait_all();
+}
+
+// Same arguments as rhs_tiles_kernel; lch and prefetch do not apply.
+// (A template so that every translation unit may instantiate it.)
+template <int NT>
+__global__ void __launch_bounds__(NT, 1)
+rhs_tiles_pipe_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
+                      double* __restrict__ out, double* __restrict__ amax_out,
+                      Status* __restrict__ status, double gamma_d, int write_status, int prefetch,
+                      int scheme) {
+  static_assert(NT == PNT, "the pipelined kernel runs PNT threads");
+  (void)Fmax;
+  (void)lch;
+  (void)prefetch;
+  tile_loop_pipe<TileList, false>(TileList{tiles}, n_tiles, out, amax_out, status, gamma_d, write_status,
+                                  scheme == 1, StageArgs{nullptr, nullptr, 0.0, 0.0, 0.0, 0});
+}
+
 // Tiles of a periodic domain of nb^3 sub-grids of N^3 (F fields each),
 // stored without ghosts; computed on the fly, no work list.
 struct DomainTiles {
@@ -1047,6 +1352,17 @@ rhs_domain_kernel(DomainTiles dom, int n_tiles, int lch, double* __restrict__ ou
                   int write_status, int scheme, StageArgs stage) {
   tile_loop<MODE, NT, MINB == 1 ? 4 : 2, DomainTiles, true>(dom, n_tiles, lch, out, amax_out, status,
                                                             gamma_d, write_status, 0, scheme == 1, stage);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1)
+rhs_domain_pipe_kernel(DomainTiles dom, int n_tiles, int lch, double* __restrict__ out,
+                       double* __restrict__ amax_out, Status* __restrict__ status, double gamma_d,
+                       int write_status, int scheme, StageArgs stage) {
+  static_assert(NT == PNT, "the pipelined kernel runs PNT threads");
+  (void)lch;
+  tile_loop_pipe<DomainTiles, true>(dom, n_tiles, out, amax_out, status, gamma_d, write_status, scheme == 1,
+                                    stage);
 }
 
 }  // namespace hydro_dev

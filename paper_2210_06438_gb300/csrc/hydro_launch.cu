@@ -8,15 +8,19 @@ using hydro_dev::rhs_tiles_kernel;
 
 // Kernel variants: (threads per CTA, minimum resident CTAs per SM).  The
 // second number caps registers per thread (65536 / (threads * minb)); the
-// autotuner picks among them per batch.
+// autotuner picks among them per batch.  {576, 1} is the pipelined mixed
+// kernel (no binary64 counterpart).
 struct Variant {
   int threads, minb;
 };
-static const Variant kVariants[] = {{256, 1}, {128, 1}, {512, 1}, {256, 2}, {128, 2}, {256, 3}, {128, 4}};
+static const Variant kVariants[] = {{256, 1}, {128, 1}, {512, 1}, {256, 2}, {128, 2}, {256, 3}, {128, 4},
+                                    {kPipeThreads, 1}};
+static_assert(kPipeThreads == hydro_dev::PNT, "pipelined kernel block size");
 static constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int MODE>
 static void* kfunc(int threads, int minb) {
+  if (threads == kPipeThreads) return MODE == 1 ? (void*)&hydro_dev::rhs_tiles_pipe_kernel<kPipeThreads> : nullptr;
   if (threads == 128) {
     if (minb == 4) return (void*)&rhs_tiles_kernel<MODE, 128, 4>;
     return minb == 2 ? (void*)&rhs_tiles_kernel<MODE, 128, 2> : (void*)&rhs_tiles_kernel<MODE, 128, 1>;
@@ -31,6 +35,9 @@ static void* pick(hydro_precision_t prec, int threads, int minb) {
 }
 
 int num_variants() { return kNumVariants; }
+bool variant_exists(hydro_precision_t prec, int threads, int minb) {
+  return pick(prec, threads, minb) != nullptr;
+}
 void variant(int i, int* threads, int* minb) {
   *threads = kVariants[i].threads;
   *minb = kVariants[i].minb;
@@ -39,30 +46,42 @@ void variant(int i, int* threads, int* minb) {
 cudaError_t kernels_init(int smem_optin) {
   for (int m = 0; m < 2; m++)
     for (int i = 0; i < kNumVariants; i++) {
-      cudaError_t e = cudaFuncSetAttribute(pick((hydro_precision_t)m, kVariants[i].threads, kVariants[i].minb),
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+      void* f = pick((hydro_precision_t)m, kVariants[i].threads, kVariants[i].minb);
+      if (!f) continue;
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
       if (e != cudaSuccess) return e;
     }
   return cudaSuccess;
 }
 
-int smem_bytes(hydro_precision_t prec, int Fmax, int lch) {
+int smem_bytes(hydro_precision_t prec, int Fmax, int lch, int threads) {
   (void)Fmax;
+  if (threads == kPipeThreads && prec != HYDRO_FP64) return (int)hydro_dev::pipe_smem_bytes();
   return (int)(prec == HYDRO_FP64 ? hydro_dev::smem_layout_bytes<0>(lch)
                                   : hydro_dev::smem_layout_bytes<1>(lch));
 }
 
 int occupancy(hydro_precision_t prec, int threads, int minb, int smem) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick(prec, threads, minb), threads, smem) !=
-      cudaSuccess)
+  void* f = pick(prec, threads, minb);
+  if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != cudaSuccess)
     return 0;
   return nb;
 }
 
 LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin,
-                      int64_t n_tiles) {
+                      int64_t n_tiles, bool pipelined) {
   LaunchCfg c;
+  if (prec != HYDRO_FP64 && pipelined && smem_bytes(prec, Fmax, 64, kPipeThreads) <= smem_optin) {
+    c.threads = kPipeThreads;
+    c.minb = 1;
+    c.lch = 64;
+    c.smem = smem_bytes(prec, Fmax, c.lch, c.threads);
+    c.ctas_per_sm = 1;
+    c.grid = (int)(n_tiles < n_sm ? n_tiles : n_sm);
+    if (c.grid < 1) c.grid = 1;
+    return c;
+  }
   c.threads = 256;
   c.minb = 1;
   c.lch = prec == HYDRO_FP64 ? 32 : 64;

@@ -180,7 +180,8 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
     p->info.interior_cells += N * N * N;
     p->info.alg_bytes += ((N * N * N + 6 * 3 * N * N) + N * N * N) * F * 8 + 8;
   }
-  p->cfg = default_cfg(prec, p->Fmax, n_sm, smem_optin, (int64_t)tiles.size());
+  p->cfg = default_cfg(prec, p->Fmax, n_sm, smem_optin, (int64_t)tiles.size(),
+                       !(flags & HYDRO_PLAN_REGISTER_LOADS));
   p->a_tiles = p->dev_tiles;
   p->a_n = (int)tiles.size();
   p->a_F = p->Fmax;
@@ -214,9 +215,14 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
       for (int pf = 0; pf < 3; pf += 2) {
         LaunchCfg c;
         variant(vi, &c.threads, &c.minb);
+        if (!variant_exists(prec, c.threads, c.minb)) continue;
+        const bool pipe = c.threads == kPipeThreads;
+        if (pipe && (li != 2 || pf != 0)) continue;  // chunking and prefetch do not apply
+        if (pipe && (flags & HYDRO_PLAN_REGISTER_LOADS)) continue;
+        if (!pipe && prec != HYDRO_FP64 && (flags & HYDRO_PLAN_PIPELINED)) continue;
         c.lch = lc[li];
         c.prefetch = pf;
-        c.smem = smem_bytes(prec, p->Fmax, c.lch);
+        c.smem = smem_bytes(prec, p->Fmax, c.lch, c.threads);
         if (c.smem > smem_optin) continue;
         int occ = occupancy(prec, c.threads, c.minb, c.smem);
         if (occ < 1) continue;

@@ -12,12 +12,13 @@ from tests import gpu_helpers as gh
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
-def test_knp_parity_uneven_batch(prec):
+@pytest.mark.parametrize("prec,flags", [(hydro.FP64, 0), (hydro.FP32_FLUX_FP64_ACC, 0),
+                                        (hydro.FP32_FLUX_FP64_ACC, hydro.F_REGISTER_LOADS)])
+def test_knp_parity_uneven_batch(prec, flags):
     leaves = synth.uneven_octree(n_subgrids=40)
     blocks = [synth.leaf_block(synth.BASE_SEED, l) for l in leaves]
     dxs = [l[2] for l in leaves]
-    got, gam = gh.run_gpu(gh.to_dev(blocks), dxs, prec=prec, flags=hydro.F_KNP)
+    got, gam = gh.run_gpu(gh.to_dev(blocks), dxs, prec=prec, flags=hydro.F_KNP | flags)
     mode = (0 if prec == hydro.FP64 else 1) + oracle.FLUX_KNP
     ref, ram, _ = gh.oracle_ref(blocks, dxs, mode=mode)
     if prec == hydro.FP64:

@@ -31,21 +31,28 @@ def test_one_subgrid_fp64(nf):
     assert rc == hydro.HYDRO_OK
 
 
+# the mixed form has two kernel families: the pipelined default and the
+# register-load kernels (HYDRO_F_REGISTER_LOADS)
+MIXED_KERNELS = [0, hydro.F_REGISTER_LOADS]
+
+
+@pytest.mark.parametrize("flags", MIXED_KERNELS)
 @pytest.mark.parametrize("nf", [6, 11])
-def test_one_subgrid_mixed(nf):
+def test_one_subgrid_mixed(nf, flags):
     U, dx = synth.one_subgrid(nf=nf)
-    got, gam = _both([U], [dx], prec=hydro.FP32_FLUX_FP64_ACC)
+    got, gam = _both([U], [dx], prec=hydro.FP32_FLUX_FP64_ACC, flags=flags)
     ref, ram, _ = gh.oracle_ref([U], [dx], mode=1)
     gh.check_mixed(got, ref, gam, ram, [U], [dx])
 
 
 # ------------------------------------------------------ plain domain --
-@pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
-def test_plain_aggregation_512_subgrids(prec):
+@pytest.mark.parametrize("prec,flags", [(hydro.FP64, 0)] +
+                         [(hydro.FP32_FLUX_FP64_ACC, f) for f in MIXED_KERNELS])
+def test_plain_aggregation_512_subgrids(prec, flags):
     glob = synth.plain_domain(n=64, nf=11)
     blocks = synth.gather_blocks(glob, 8)
     dxs = [1.0 / 64] * len(blocks)
-    got, gam = _both(list(blocks), dxs, prec=prec)
+    got, gam = _both(list(blocks), dxs, prec=prec, flags=flags)
     mode = 0 if prec == hydro.FP64 else 1
     ref, ram, fl = gh.oracle_ref(list(blocks), dxs, mode=mode)
     assert not fl.any()
@@ -66,13 +73,14 @@ def test_plain_aggregation_512_subgrids(prec):
 
 
 # ------------------------------------------------------- uneven batch --
-@pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
-def test_uneven_octree_batch(prec):
+@pytest.mark.parametrize("prec,flags", [(hydro.FP64, 0)] +
+                         [(hydro.FP32_FLUX_FP64_ACC, f) for f in MIXED_KERNELS])
+def test_uneven_octree_batch(prec, flags):
     leaves = synth.uneven_octree(n_subgrids=48)
     assert {l[0] for l in leaves} == {8, 16} and {l[1] for l in leaves} == {6, 11}
     blocks = [synth.leaf_block(synth.BASE_SEED, l) for l in leaves]
     dxs = [l[2] for l in leaves]
-    got, gam = _both(blocks, dxs, prec=prec)
+    got, gam = _both(blocks, dxs, prec=prec, flags=flags)
     mode = 0 if prec == hydro.FP64 else 1
     ref, ram, _ = gh.oracle_ref(blocks, dxs, mode=mode)
     if mode == 0:
@@ -89,6 +97,39 @@ def test_ragged_sizes_and_partial_tiles(N):
     got, gam = _both(blocks, dxs)
     ref, ram, _ = gh.oracle_ref(blocks, dxs)
     gh.check_fp64(got, ref, gam, ram, blocks, dxs)
+
+
+@pytest.mark.parametrize("flags", MIXED_KERNELS)
+@pytest.mark.parametrize("N", [2, 3, 5, 12, 16, 17])
+def test_ragged_sizes_and_partial_tiles_mixed(N, flags):
+    blocks = [synth.iid_block(synth.rng_for(7, N), N, 8 + N % 4),
+              synth.iid_block(synth.rng_for(70, N), N, 6)]
+    dxs = [0.3, 0.25]
+    got, gam = _both(blocks, dxs, prec=hydro.FP32_FLUX_FP64_ACC, flags=flags)
+    ref, ram, _ = gh.oracle_ref(blocks, dxs, mode=1)
+    gh.check_mixed(got, ref, gam, ram, blocks, dxs)
+
+
+def test_mixed_kernel_families_agree_bitwise():
+    """The pipelined and the register-load kernels run the same arithmetic in
+    the same order, so they agree bit for bit, as do the tuned plans that
+    are restricted to either family."""
+    leaves = synth.uneven_octree(n_subgrids=40)
+    blocks = [synth.leaf_block(synth.BASE_SEED + 1, l) for l in leaves]
+    blocks += [synth.iid_block(synth.rng_for(11, N), N, 7 + N % 5) for N in (3, 5, 12)]
+    dxs = [l[2] for l in leaves] + [0.2, 0.3, 0.125]
+    dev = gh.to_dev(blocks)
+    mx = hydro.FP32_FLUX_FP64_ACC
+    a, aam = gh.run_gpu(dev, dxs, prec=mx)
+    b, bam = gh.run_gpu(dev, dxs, prec=mx, flags=hydro.F_REGISTER_LOADS)
+    c, cam = gh.run_gpu(dev, dxs, prec=mx, form="plan",
+                        plan_kw={"autotune": True, "flags": hydro.PLAN_PIPELINED})
+    d, dam = gh.run_gpu(dev, dxs, prec=mx, form="plan",
+                        plan_kw={"autotune": True, "flags": hydro.PLAN_REGISTER_LOADS})
+    for other, oam in ((b, bam), (c, cam), (d, dam)):
+        for s in range(len(blocks)):
+            assert np.array_equal(other[s], a[s]), s
+        assert np.array_equal(oam, aam)
 
 
 def test_wider_ghost_layer_is_ignored_beyond_three():
