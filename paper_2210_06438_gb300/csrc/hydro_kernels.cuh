@@ -444,51 +444,65 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // ------------------------------------------------------ step A2, mixed --
-// ppm_line64's steps in binary32 on a pair of fields.  The sign tests are
-// evaluated on products (an underflowing product of two differences below
-// ~1e-22 reads as "not the same sign", which changes results by less than
-// such differences).
-__device__ __forceinline__ float2 slope32x2(float2 qm, float2 q0, float2 qp) {
-  float2 dp = sub2(qp, q0), dm = sub2(q0, qm);
-  float2 dbar = mul2(sub2(qp, qm), f2(0.5f));
-  float2 pr = mul2(dp, dm);
-  float2 t = mul2(f2(2.0f), make_float2(fminf(fabsf(dm.x), fabsf(dp.x)), fminf(fabsf(dm.y), fabsf(dp.y))));
-  float mx = fminf(fabsf(dbar.x), t.x), my = fminf(fabsf(dbar.y), t.y);
-  return make_float2(pr.x > 0.0f ? copysignf(mx, dbar.x) : 0.0f, pr.y > 0.0f ? copysignf(my, dbar.y) : 0.0f);
+// ppm_line64's steps in binary32 on a pair of fields, in half-slope form:
+// with dm = q - q_-1 and dp = q_+1 - q, half the monotonised central slope is
+//   h = sign(dm + dp) min(|dm + dp|/4, |dm|, |dp|)  if dm, dp have one sign,
+//   h = 0 otherwise,
+// and the face between cells c-1 and c is (q_c-1 + q_c)/2 - (h_c - h_c-1)/3.
+// The same-sign tests run on products (a product of two differences that
+// underflows reads as "not the same sign", which changes results by less
+// than those differences).  The parabola limiter in clamp form: with
+// up = q+ - q and dn = q - q- of one sign, q+ = q + 2dn where |up| > 2|dn|
+// and q- = q - 2up where |dn| > 2|up| (CW84 eq. 1.10); faces that are not
+// clamped keep their value exactly; a cell with up dn <= 0 is flattened.
+__device__ __forceinline__ float hslope1(float dm, float dp, float s4, float pr) {
+  float m = fminf(fminf(fabsf(s4), fabsf(dm)), fabsf(dp));
+  return pr > 0.0f ? copysignf(m, s4) : 0.0f;
+}
+__device__ __forceinline__ float2 hslope32x2(float2 dm, float2 dp) {
+  float2 s4 = mul2(add2(dm, dp), f2(0.25f));
+  float2 pr = mul2(dm, dp);
+  return make_float2(hslope1(dm.x, dp.x, s4.x, pr.x), hslope1(dm.y, dp.y, s4.y, pr.y));
+}
+__device__ __forceinline__ void limit1(float q, float lo, float hi, float up, float dn, float e, float uu,
+                                       float du, float lc, float hc, float& L, float& H) {
+  const bool ext = !(e > 0.0f);
+  L = ext ? q : (fabsf(dn) > fabsf(uu) ? lc : lo);
+  H = ext ? q : (fabsf(up) > fabsf(du) ? hc : hi);
 }
 // One pass along the line keeping a short window of values live: at step c
-// the slope of cell c, the face c-1/2 and the limited states of cell c-1.
-// q: the line in shared memory (la addresses it).
+// the half slope of cell c, the face c-1/2 and the limited states of cell
+// c-1.  w: the line in shared memory (la addresses it).
 __device__ __forceinline__ void ppm_line32x2(const float2* w, const LineAddr& la, float2* left,
                                              float2* right) {
   float2 q0 = w[la.at(0)], q1 = w[la.at(1)], q2 = w[la.at(2)];
-  float2 del_prev = slope32x2(q0, q1, q2);  // cell c = 1
+  float2 dm = sub2(q2, q1);                  // q2 - q1: the "dm" of cell 2
+  float2 h_prev = hslope32x2(sub2(q1, q0), dm);  // cell c = 1
   float2 face_prev = f2(0.0f);               // face c - 3/2
   float2 qm = q1, qc = q2;                    // q[c-1], q[c] for c = 2
 #pragma unroll
   for (int c = 2; c <= LL - 2; c++) {
     float2 qp = w[la.at(c + 1)];
-    float2 del = slope32x2(qm, qc, qp);  // slope of cell c
+    float2 dp = sub2(qp, qc);
+    float2 h = hslope32x2(dm, dp);  // half slope of cell c
     // face between cells c-1 and c
-    float2 face = fma2(sub2(del_prev, del), f2(1.0f / 6.0f), mul2(add2(qm, qc), f2(0.5f)));
+    float2 face = fma2(sub2(h_prev, h), f2(1.0f / 3.0f), mul2(add2(qm, qc), f2(0.5f)));
     if (c >= 3) {  // limit cell c-1 with faces face_prev (left) and face (right)
       float2 lo = face_prev, hi = face, q = qm;
       float2 up = sub2(hi, q), dn = sub2(q, lo);
       float2 e = mul2(up, dn);
-      float2 a1 = mul2(fma2(f2(-2.0f), up, dn), up);                 // (dn - 2 up) up
-      float2 a2 = mul2(fma2(f2(2.0f), dn, mul2(up, f2(-1.0f))), up);  // (2 dn - up) up
-      float2 lo2 = fma2(f2(-2.0f), up, q), hi2 = fma2(f2(2.0f), dn, q);
+      float2 uu = add2(up, up), du = add2(dn, dn);
+      float2 lc = sub2(q, uu), hc = add2(q, du);
       float2 L, H;
-      L.x = !(e.x > 0.0f) ? q.x : (a1.x > 0.0f ? lo2.x : lo.x);
-      H.x = !(e.x > 0.0f) ? q.x : (!(a1.x > 0.0f) && a2.x < 0.0f ? hi2.x : hi.x);
-      L.y = !(e.y > 0.0f) ? q.y : (a1.y > 0.0f ? lo2.y : lo.y);
-      H.y = !(e.y > 0.0f) ? q.y : (!(a1.y > 0.0f) && a2.y < 0.0f ? hi2.y : hi.y);
+      limit1(q.x, lo.x, hi.x, up.x, dn.x, e.x, uu.x, du.x, lc.x, hc.x, L.x, H.x);
+      limit1(q.y, lo.y, hi.y, up.y, dn.y, e.y, uu.y, du.y, lc.y, hc.y, L.y, H.y);
       int j = c - 4;  // cell index of c-1
       if (j >= 0) right[j] = L;
       if (j + 1 <= TE) left[j + 1] = H;
     }
     face_prev = face;
-    del_prev = del;
+    h_prev = h;
+    dm = dp;
     qm = qc;
     qc = qp;
   }
@@ -563,9 +577,15 @@ __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& 
   float2 bb = sub2(s, a);
   e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
 }
+// a - b = s + e exactly (Knuth's two-sum with the subtraction folded in)
+__device__ __forceinline__ void two_diff2(float2 a, float2 b, float2& s, float2& e) {
+  s = sub2(a, b);
+  float2 bb = sub2(s, a);  // ~ -b
+  e = sub2(sub2(a, sub2(s, bb)), add2(b, bb));
+}
 __device__ __forceinline__ void acc_pair2(P2& acc, float2 hi, float2 lo, bool first) {
   float2 dh, dl;
-  two_sum2(hi, mul2(lo, f2(-1.0f)), dh, dl);
+  two_diff2(hi, lo, dh, dl);
   if (first) {
     acc.h = dh;
     acc.l = dl;
