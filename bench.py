@@ -307,6 +307,65 @@ def serving_run(rate, duration, per_task, budget=40 << 30, n_streams=4, max_batc
             "peak_bytes_in_flight": st["peak_bytes_in_flight"], "per_task": per_task}
 
 
+# ------------------------------------------------------------- Sedov --
+def sedov_gpu_run(n=64, prec=0, cfl=0.3, t_end=None, dts=None, gamma=5.0 / 3.0, flags=0,
+                  stream=None):
+    """The Sedov point explosion (synth.sedov_domain, 11 fields) integrated on
+    the GPU with SSP-RK3 steps of three fused stages of the domain form
+    (ghost shells gathered in the kernel), to t_end or along `dts`.  The time
+    step follows the rule of tests/sedov_run.py (dt = cfl dx / the largest
+    signal speed of the previous step's stages).  Returns a dict with the
+    final state (device, domain layout), t, the steps' dt and the wall time."""
+    import torch
+
+    import paper_2210_06438_gb300 as hydro
+    from tests.sedov_run import to_domain
+
+    glob, dx = synth.sedov_domain(n=n, nf=11, gamma=gamma)
+    N, nf = 8, 11
+    nb = n // N
+    U = torch.from_numpy(to_domain(glob, N)).cuda()
+    W1, W2 = torch.empty_like(U), torch.empty_like(U)
+    am = torch.empty((3, nb ** 3), dtype=torch.float64, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    kw = dict(gamma=gamma, prec=prec, stream=st, flags=flags)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(st)
+    hydro.domain_rhs(U, nb, N, nf, dx, W1, am[0], **kw)
+    a_next = float(am[0].max())
+    t, used, k = 0.0, [], 0
+    while (dts is not None and k < len(dts)) or (dts is None and t < t_end):
+        dt = dts[k] if dts is not None else min(cfl * dx / a_next, t_end - t)
+        hydro.domain_stage(U, U, 0.0, 1.0, dt, nb, N, nf, dx, W1, am[0], **kw)
+        hydro.domain_stage(W1, U, 0.75, 0.25, dt, nb, N, nf, dx, W2, am[1], **kw)
+        hydro.domain_stage(W2, U, 1.0 / 3.0, 2.0 / 3.0, dt, nb, N, nf, dx, W1, am[2], **kw)
+        U, W1 = W1, U
+        a_next = float(am.max())  # host sync: the next step's dt
+        t += dt
+        used.append(dt)
+        k += 1
+    ev1.record(st)
+    torch.cuda.synchronize()
+    return {"U": U, "t": t, "dts": used, "steps": k, "ms": ev0.elapsed_time(ev1), "n": n, "dx": dx}
+
+
+def sedov_form(n, prec):
+    """One Sedov run at n^3 with its measures against the similarity solution."""
+    from tests.sedov_exact import Sedov
+    from tests.sedov_run import from_domain, shock_measures
+
+    ex = Sedov(5.0 / 3.0)
+    r = sedov_gpu_run(n=n, prec=prec, t_end=ex.time_for_radius(0.35))
+    rho = from_domain(r["U"].cpu().numpy(), n)[0]
+    Rp, L1 = shock_measures(rho, r["dx"], ex, r["t"])
+    return {"value": 3 * n ** 3 * r["steps"] / (r["ms"] * 1e-3), "unit": "stage cell-updates/s",
+            "steps": r["steps"], "ms": r["ms"], "t_end": r["t"], "R_peak": Rp,
+            "R_exact": ex.shock_radius(r["t"]), "L1_rho": L1,
+            "note": "Sedov blast to R = 0.35 on %d^3 cells (%d sub-grids of 8^3, 11 fields), "
+                    "SSP-RK3 of fused domain stages, dt from the signal speed (host sync per step)"
+                    % (n, (n // 8) ** 3)}
+
+
 # ---------------------------------------------------------- cpu baseline --
 def oracle_sample_rate(blocks_host, dx, seconds=10.0, threads=None, mode=0):
     """The oracle (as it stands) over a sample of sub-grids, repeated until
@@ -459,6 +518,12 @@ def run_ours(args, rank, world):
     dom_bytes = batch.n * (synth.star_cells(8) + 512) * batch.nf * 8
     del dom, dout, dtmp
 
+    # ---- the Sedov point explosion (the paper's scenario) on the 64^3 cube
+    sedov = {}
+    if not args.no_sedov:
+        sedov = {"sedov_fp64_64": sedov_form(64, hydro.FP64),
+                 "sedov_mixed_64": sedov_form(64, hydro.FP32_FLUX_FP64_ACC)}
+
     # ---- end to end through the C ABI with host buffers
     host_in = torch.empty(batch.blocks.shape, dtype=torch.float64, pin_memory=True)
     host_in.copy_(batch.blocks)
@@ -551,6 +616,7 @@ def run_ours(args, rank, world):
             "fp64_rk3_step": {"value": 3 * cells * world / (ms_rk64 * 1e-3), "ms": ms_rk64,
                               "note": "three fused SSP-RK3 stages; value = stage cell-updates/s"},
             "mixed_rk3_step": {"value": 3 * cells * world / (ms_rkmx * 1e-3), "ms": ms_rkmx},
+            **sedov,
             "mixed_per_subgrid": {"value": cells * world / (ms_psmx * 1e-3), "ms": ms_psmx,
                                   "streams": args.streams, "launches": batch.n},
         },
@@ -602,6 +668,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-sedov", action="store_true", help="skip the Sedov blast runs")
     ap.add_argument("--rate", type=float, default=20000.0, help="serving arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--profile", choices=["fp64", "mixed"], default=None,

@@ -20,6 +20,9 @@ with the shapes of the paper's workloads:
   polytropes       a 256^3 periodic domain (32768 sub-grids of 8^3) holding
                    two n = 1.5 polytropes on a 1e-10 atmosphere, 11 fields
   serving_trace    Poisson arrivals of tasks of 1..64 sub-grids
+  sedov_domain     the point explosion itself: a periodic cube of gas at rest
+                   with the blast energy put into the 8 cells at its centre
+                   (the scenario of Sec. VI-A, here with 5 passive species)
 """
 from __future__ import annotations
 
@@ -248,3 +251,32 @@ def kernel_calls_per_step(n_subgrids, kernels=5, iterations=3):
 def is_power_of_two_fraction(x):
     m, e = math.frexp(x)
     return m == 0.5
+
+
+# ---------------------------------------------------------------- Sedov --
+def sedov_domain(n=64, nf=11, gamma=GAMMA, E=1.0, rho0=1.0, p0=1e-5, seed=BASE_SEED):
+    """Point explosion on the periodic cube [-1/2, 1/2]^3 with n^3 cells
+    (dx = 1/n, n even): gas at rest with density rho0 and pressure p0, and the
+    energy E added as internal energy, evenly, to the 2^3 cells that touch the
+    centre.  Species (nf - 6 of them) carry uniform mass fractions drawn from a
+    Dirichlet(1) distribution.  Returns (global array [nf][n][n][n], dx)."""
+    if n % 2:
+        raise ValueError("n must be even (the centre is a cell corner)")
+    dx = 1.0 / n
+    shp = (n, n, n)
+    rho = np.full(shp, rho0)
+    p = np.full(shp, p0)
+    c = n // 2
+    p[c - 1:c + 1, c - 1:c + 1, c - 1:c + 1] += (gamma - 1.0) * E / (8.0 * dx ** 3)
+    X = None
+    if nf > 6:
+        x = rng_for(seed, 0xB1A57).dirichlet(np.ones(nf - 6))
+        X = np.broadcast_to(x[:, None, None, None], (nf - 6,) + shp).copy()
+    zero = np.zeros(shp)
+    return conserved_from_states(rho, zero, zero, zero, p, X, gamma), dx
+
+
+def cell_radii(n):
+    """Distance of every cell centre of sedov_domain's cube from its centre."""
+    x = (np.arange(n) + 0.5) / n - 0.5
+    return np.sqrt(x[None, None, :] ** 2 + x[None, :, None] ** 2 + x[:, None, None] ** 2)
