@@ -38,6 +38,7 @@ MODE_FP64 = 0
 MODE_MIXED = 1
 FLUX_KT = 0   # Kurganov-Tadmor (single speed)
 FLUX_KNP = 2  # Kurganov-Noelle-Petrova (one-sided speeds); add to the mode
+QUAD26 = 4    # fluxes at 9 points per face (26 per cell) with Simpson weights; add to the mode
 
 _lock = threading.Lock()
 _lib = None

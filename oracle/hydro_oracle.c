@@ -69,6 +69,19 @@ static int in_star(const ora_geom* g, int i, int j, int k) {
   return out <= 1;
 }
 
+/* The 26-point variant reads every cell within 3 of the interior along its
+ * face-normal axis and within 2 along the other two: each coordinate in
+ * [-3, n+2] with at most one of them at -3 or n+2 (the stencils of the
+ * lines through the cells next to interior faces, see quad26_face). */
+static int in_read26(const ora_geom* g, int i, int j, int k) {
+  int n[3] = {g->nx, g->ny, g->nz}, c[3] = {i, j, k}, far = 0;
+  for (int d = 0; d < 3; d++) {
+    if (c[d] < -3 || c[d] > n[d] + 2) return 0;
+    if (c[d] == -3 || c[d] == n[d] + 2) far++;
+  }
+  return far <= 1;
+}
+
 /* ---------------------------------------------------------------- step 1 --
  * Conserved -> primitive variables (declared reading; the paper names the
  * conserved quantities only).  Fields: 0 rho, 1..3 momentum s, 4 total energy
@@ -305,10 +318,96 @@ static float knp_flux_f(const float* wl, const float* wr, int nf, int d, float g
   return fmaxf(al, ar);
 }
 
+/* ------------------------------------------------ 26-point variant --
+ * Sec. IV-B: PPM values at 26 points on the surface of each cell (the
+ * centres of its 6 faces, the midpoints of its 12 edges and its 8
+ * vertices), central-upwind fluxes at those points, and Newton-Cotes
+ * quadrature of the fluxes over each face.  Declared reading: the value of
+ * cell c at its surface point c + v/2 (v in {-1,0,1}^3, v != 0) is the PPM
+ * face value of the one-dimensional reconstruction along the line of cells
+ * c + m v, i.e. ppm_line on that line (cell c depends on cells m = -2..2
+ * only).  A face normal to axis d has the 9 points v = e_d + o1 e_a + o2 e_b
+ * (o1, o2 in {-1, 0, 1}); at each one the left state is the low cell's value
+ * there (its line along v, upper end) and the right state the high cell's
+ * value there (its line along e_d - o1 e_a - o2 e_b, lower end).  The face
+ * flux is Simpson's rule in both tangential directions,
+ *   Fhat = sum_p c_p Fhat_p / 36,  c_p = (1, 4, 1) x (1, 4, 1),
+ * and the signal speed is the largest over all points. */
+static void ppm_cell_d(const double* W, const ora_geom* g, int f, const int* c, const int* v,
+                       double* qm, double* qp) {
+  double q[7], lm[3], lp[3], work[14];
+  for (int m = -2; m <= 2; m++)
+    q[m + 3] = W[at(g, f, c[0] + m * v[0], c[1] + m * v[1], c[2] + m * v[2])];
+  q[0] = q[1]; /* cells -3 and +3 of the line do not enter cell 0 */
+  q[6] = q[5];
+  ppm_line_d(q, 1, lm, lp, work, work + 7);
+  *qm = lm[1];
+  *qp = lp[1];
+}
+
+static void ppm_cell_f(const double* W, const ora_geom* g, int f, const int* c, const int* v,
+                       float* qm, float* qp) {
+  float q[7], lm[3], lp[3], work[14];
+  for (int m = -2; m <= 2; m++)
+    q[m + 3] = (float)W[at(g, f, c[0] + m * v[0], c[1] + m * v[1], c[2] + m * v[2])];
+  q[0] = q[1];
+  q[6] = q[5];
+  ppm_line_f(q, 1, lm, lp, work, work + 7);
+  *qm = lm[1];
+  *qp = lp[1];
+}
+
+/* Flux through the face between cell cl and cl + e_d (mode as in
+ * ora_rhs_block); returns the largest signal speed of its 9 points. */
+static double quad26_face(const double* W, const ora_geom* g, int nf, int d, const int* cl,
+                          double gamma, int mode, int knp, double* fhat) {
+  const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+  int cr[3] = {cl[0], cl[1], cl[2]};
+  cr[d] += 1;
+  double acc_d[ORA_MAXF] = {0};
+  float acc_f[ORA_MAXF] = {0};
+  double amax = 0.0;
+  float amax_f = 0.0f;
+  for (int o2 = -1; o2 <= 1; o2++)
+    for (int o1 = -1; o1 <= 1; o1++) {
+      int vl[3] = {0, 0, 0}, vr[3] = {0, 0, 0};
+      vl[d] = 1, vl[t1] = o1, vl[t2] = o2;
+      vr[d] = 1, vr[t1] = -o1, vr[t2] = -o2;
+      const int cw = (o1 == 0 ? 4 : 1) * (o2 == 0 ? 4 : 1);
+      if (mode == 0) {
+        double wl[ORA_MAXF], wr[ORA_MAXF], fh[ORA_MAXF], lo, hi;
+        for (int f = 0; f < nf; f++) {
+          ppm_cell_d(W, g, f, cl, vl, &lo, &hi);
+          wl[f] = hi;
+          ppm_cell_d(W, g, f, cr, vr, &lo, &hi);
+          wr[f] = lo;
+        }
+        double sp = knp ? knp_flux_d(wl, wr, nf, d, gamma, fh) : kt_flux_d(wl, wr, nf, d, gamma, fh);
+        if (!(sp <= amax)) amax = sp;
+        for (int f = 0; f < nf; f++) acc_d[f] += cw * fh[f];
+      } else {
+        float wl[ORA_MAXF], wr[ORA_MAXF], fh[ORA_MAXF], lo, hi;
+        for (int f = 0; f < nf; f++) {
+          ppm_cell_f(W, g, f, cl, vl, &lo, &hi);
+          wl[f] = hi;
+          ppm_cell_f(W, g, f, cr, vr, &lo, &hi);
+          wr[f] = lo;
+        }
+        float sp = knp ? knp_flux_f(wl, wr, nf, d, (float)gamma, fh)
+                       : kt_flux_f(wl, wr, nf, d, (float)gamma, fh);
+        if (!(sp <= amax_f)) amax_f = sp;
+        for (int f = 0; f < nf; f++) acc_f[f] += (float)cw * fh[f];
+      }
+    }
+  for (int f = 0; f < nf; f++) fhat[f] = mode == 0 ? acc_d[f] / 36.0 : (double)(acc_f[f] / 36.0f);
+  return mode == 0 ? amax : (double)amax_f;
+}
+
 /* --------------------------------------------------------- steps 1 - 5 --
  * One block (a sub-grid, or any nx*ny*nz box used by the tests).
  *   mode bit 0: 0 all binary64, 1 steps 2-3 in binary32 and step 4 binary64.
  *   mode bit 1: 0 Kurganov-Tadmor flux, 1 Kurganov-Noelle-Petrova flux.
+ *   mode bit 2: 0 face-centre fluxes, 1 the 26-point variant (quad26_face).
  * face_out (optional, may be NULL): receives the face fluxes as doubles,
  *   x faces [nf][nz][ny][nx+1], then y faces [nf][nz][ny+1][nx], then z
  *   faces [nf][nz+1][ny][nx].
@@ -316,10 +415,11 @@ static float knp_flux_f(const float* wl, const float* wr, int nf, int d, float g
 int ora_rhs_block(const double* U, int nx, int ny, int nz, int ghost, int nf, double gamma,
                   double dx, int mode, double* dUdt, double* amax_out, double* face_out) {
   if (nx < 1 || ny < 1 || nz < 1 || nx > ORA_MAXN || ny > ORA_MAXN || nz > ORA_MAXN || ghost < 3 || nf < 6 ||
-      nf > ORA_MAXF || !(gamma > 1.0) || !(dx > 0.0) || mode < 0 || mode > 3)
+      nf > ORA_MAXF || !(gamma > 1.0) || !(dx > 0.0) || mode < 0 || mode > 7)
     return ORA_EINVAL;
   ora_geom g = {nx, ny, nz, ghost, nx + 2 * ghost, ny + 2 * ghost, nz + 2 * ghost, nf};
   const int knp = (mode >> 1) & 1;
+  const int q26 = (mode >> 2) & 1;
   mode &= 1;
   int flags = 0;
   size_t ncell = (size_t)g.gx * g.gy * g.gz;
@@ -329,7 +429,7 @@ int ora_rhs_block(const double* U, int nx, int ny, int nz, int ghost, int nf, do
   for (int k = -3; k < nz + 3; k++)
     for (int j = -3; j < ny + 3; j++)
       for (int i = -3; i < nx + 3; i++) {
-        if (!in_star(&g, i, j, k)) continue;
+        if (!(q26 ? in_read26(&g, i, j, k) : in_star(&g, i, j, k))) continue;
         double u[ORA_MAXF], w[ORA_MAXF];
         for (int f = 0; f < nf; f++) u[f] = U[at(&g, f, i, j, k)];
         flags |= primitives(u, nf, gamma, w) ? ORA_NONPHYS : 0;
@@ -357,8 +457,27 @@ int ora_rhs_block(const double* U, int nx, int ny, int nz, int ghost, int nf, do
   double* work_d = (double*)malloc(2 * L * sizeof(double));
   float* work_f = (float*)malloc(2 * L * sizeof(float));
 
+  /* steps 2-3, 26-point variant: every face of an interior cell */
+  for (int d = 0; q26 && d < 3; d++) {
+    int ext[3] = {n[0] + (d == 0), n[1] + (d == 1), n[2] + (d == 2)};
+    for (int k = 0; k < ext[2]; k++)
+      for (int j = 0; j < ext[1]; j++)
+        for (int i = 0; i < ext[0]; i++) {
+          int cl[3] = {i, j, k};
+          cl[d] -= 1; /* face i-1/2 along d: low cell i-1 */
+          double fh[ORA_MAXF];
+          double sp = quad26_face(W, &g, nf, d, cl, gamma, mode, knp, fh);
+          if (mode == 0 ? !(sp <= amax) : !((float)sp <= amax_f)) {
+            if (mode == 0) amax = sp; else amax_f = (float)sp;
+          }
+          if (!isfinite(sp)) flags |= ORA_NONPHYS;
+          size_t fidx = ((size_t)k * ext[1] + (size_t)j) * ext[0] + (size_t)i;
+          for (int f = 0; f < nf; f++) FH[d][(size_t)f * nface[d] + fidx] = fh[f];
+        }
+  }
+
   /* steps 2-3: for each direction and each interior line along it */
-  for (int d = 0; d < 3; d++) {
+  for (int d = 0; !q26 && d < 3; d++) {
     int nd = n[d];
     int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2; /* tangential axes */
     for (int b = 0; b < n[t2]; b++)
