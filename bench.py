@@ -518,6 +518,18 @@ def run_ours(args, rank, world):
     dom_bytes = batch.n * (synth.star_cells(8) + 512) * batch.nf * 8
     del dom, dout, dtmp
 
+    # ---- the 26-point quadrature variant on the same sub-grids
+    quad = {}
+    if not args.no_quad26:
+        for name, prec in (("fp64_quad26", hydro.FP64), ("mixed_quad26", hydro.FP32_FLUX_FP64_ACC)):
+            pq = hydro.Plan(batch.desc, ghost=3, gamma=GAMMA, prec=prec, autotune=True, stream=stream,
+                            n=batch.n, flags=hydro.PLAN_QUAD26)
+            msq = time_steps(lambda: pq.execute(out, amax, stream), max(1, args.steps // 3), 1, stream)
+            quad[name] = {"value": cells * world / (msq * 1e-3), "ms": msq,
+                          "conservation_drift": conservation_drift(out, batch),
+                          "note": "fluxes at 9 points per face (26 per cell), Simpson weights"}
+            pq.close()
+
     # ---- the Sedov point explosion (the paper's scenario) on the 64^3 cube
     sedov = {}
     if not args.no_sedov:
@@ -616,6 +628,7 @@ def run_ours(args, rank, world):
             "fp64_rk3_step": {"value": 3 * cells * world / (ms_rk64 * 1e-3), "ms": ms_rk64,
                               "note": "three fused SSP-RK3 stages; value = stage cell-updates/s"},
             "mixed_rk3_step": {"value": 3 * cells * world / (ms_rkmx * 1e-3), "ms": ms_rkmx},
+            **quad,
             **sedov,
             "mixed_per_subgrid": {"value": cells * world / (ms_psmx * 1e-3), "ms": ms_psmx,
                                   "streams": args.streams, "launches": batch.n},
@@ -669,6 +682,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-sedov", action="store_true", help="skip the Sedov blast runs")
+    ap.add_argument("--no-quad26", action="store_true", help="skip the 26-point quadrature forms")
     ap.add_argument("--rate", type=float, default=20000.0, help="serving arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--profile", choices=["fp64", "mixed"], default=None,

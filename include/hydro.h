@@ -98,6 +98,11 @@ int hydro_rhs(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t N, in
 #define HYDRO_F_KNP 2u       /* central-upwind flux with one-sided local speeds (Kurganov,
                                 Noelle & Petrova 2001) instead of the single-speed
                                 Kurganov-Tadmor flux; same signal speed for amax */
+#define HYDRO_F_QUAD26 8u         /* the 26-point variant of Sec. IV-B: fluxes at the 9
+                                     points of every face (centre, edge midpoints,
+                                     vertices) from PPM along the lines through them,
+                                     combined with Simpson weights; reads the ghosted
+                                     block except its 3-deep edges beyond 2 cells */
 #define HYDRO_F_REGISTER_LOADS 4u /* mixed form: the kernel that loads the read region
                                      through registers instead of the default pipelined
                                      kernel (asynchronous copies into shared memory,
@@ -129,6 +134,8 @@ typedef struct hydro_plan hydro_plan_t;
 #define HYDRO_PLAN_KNP 4u      /* the flux of HYDRO_F_KNP */
 #define HYDRO_PLAN_PIPELINED 8u       /* mixed form: consider only the pipelined kernel */
 #define HYDRO_PLAN_REGISTER_LOADS 16u /* mixed form: consider only the register-load kernels */
+#define HYDRO_PLAN_QUAD26 32u         /* the flux of HYDRO_F_QUAD26 (one launch shape; the
+                                         autotuner keeps it) */
 
 typedef struct {
   int64_t n_subgrids;

@@ -34,9 +34,11 @@ PLAN_NO_GRAPH = 2
 PLAN_KNP = 4
 PLAN_PIPELINED = 8
 PLAN_REGISTER_LOADS = 16
+PLAN_QUAD26 = 32
 F_NO_STATUS = 1
 F_KNP = 2
 F_REGISTER_LOADS = 4
+F_QUAD26 = 8
 
 
 

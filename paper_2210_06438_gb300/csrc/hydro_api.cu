@@ -261,7 +261,7 @@ int hydro_rhs_ex(const hydro_subgrid_t* sg, int64_t n, int32_t N, int32_t ghost,
   if (multi && (e = cudaMemsetAsync(amax, 0, n * sizeof(double), st)) != cudaSuccess)
     return cuda_fail(e, "cudaMemsetAsync(amax)");
   LaunchCfg cfg = default_cfg(prec, Fmax, c->n_sm, c->smem_optin, (int64_t)tiles.size(),
-                              !(flags & HYDRO_F_REGISTER_LOADS));
+                              !(flags & HYDRO_F_REGISTER_LOADS), (flags & HYDRO_F_QUAD26) != 0);
   if ((e = launch_tiles(cfg, prec, dt, (int)tiles.size(), Fmax, out, amax, c->status, gamma,
                         !(flags & HYDRO_F_NO_STATUS), st, (flags & HYDRO_F_KNP) ? 1 : 0)) != cudaSuccess)
     return cuda_fail(e, "launch");

@@ -35,9 +35,11 @@ int num_variants();
 void variant(int i, int* threads, int* minb);
 bool variant_exists(hydro_precision_t prec, int threads, int minb);
 constexpr int kPipeThreads = 576;
-// pipelined: use the pipelined mixed kernel (ignored for binary64)
+constexpr int kQuadThreads = 192;  // the 26-point quadrature kernels
+// pipelined: use the pipelined mixed kernel (ignored for binary64);
+// quad26: the 26-point quadrature kernel (takes precedence)
 LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin, int64_t n_tiles,
-                      bool pipelined = true);
+                      bool pipelined = true, bool quad26 = false);
 // scheme: 0 Kurganov-Tadmor flux, 1 Kurganov-Noelle-Petrova
 cudaError_t launch_tiles(const LaunchCfg& cfg, hydro_precision_t prec, const hydro_dev::Tile* tiles,
                          int n_tiles, int Fmax, double* out, double* amax, hydro_dev::Status* status,

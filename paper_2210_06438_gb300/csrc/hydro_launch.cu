@@ -1,6 +1,7 @@
 // hydro_launch.cu -- kernel instantiations and launch shapes of libhydro.
 #include "hydro_internal.h"
 #include "hydro_kernels.cuh"
+#include "hydro_quad.cuh"
 
 namespace hydro_host {
 
@@ -14,13 +15,15 @@ struct Variant {
   int threads, minb;
 };
 static const Variant kVariants[] = {{256, 1}, {128, 1}, {512, 1}, {256, 2}, {128, 2}, {256, 3}, {128, 4},
-                                    {kPipeThreads, 1}};
+                                    {kPipeThreads, 1}, {kQuadThreads, 1}};
 static_assert(kPipeThreads == hydro_dev::PNT, "pipelined kernel block size");
+static_assert(kQuadThreads == hydro_dev::QNT, "26-point kernel block size");
 static constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int MODE>
 static void* kfunc(int threads, int minb) {
   if (threads == kPipeThreads) return MODE == 1 ? (void*)&hydro_dev::rhs_tiles_pipe_kernel<kPipeThreads> : nullptr;
+  if (threads == kQuadThreads) return (void*)&hydro_dev::rhs_quad_kernel<MODE>;
   if (threads == 128) {
     if (minb == 4) return (void*)&rhs_tiles_kernel<MODE, 128, 4>;
     return minb == 2 ? (void*)&rhs_tiles_kernel<MODE, 128, 2> : (void*)&rhs_tiles_kernel<MODE, 128, 1>;
@@ -57,6 +60,8 @@ cudaError_t kernels_init(int smem_optin) {
 int smem_bytes(hydro_precision_t prec, int Fmax, int lch, int threads) {
   (void)Fmax;
   if (threads == kPipeThreads && prec != HYDRO_FP64) return (int)hydro_dev::pipe_smem_bytes();
+  if (threads == kQuadThreads)
+    return (int)(prec == HYDRO_FP64 ? hydro_dev::quad_smem_bytes<0>() : hydro_dev::quad_smem_bytes<1>());
   return (int)(prec == HYDRO_FP64 ? hydro_dev::smem_layout_bytes<0>(lch)
                                   : hydro_dev::smem_layout_bytes<1>(lch));
 }
@@ -70,8 +75,20 @@ int occupancy(hydro_precision_t prec, int threads, int minb, int smem) {
 }
 
 LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin,
-                      int64_t n_tiles, bool pipelined) {
+                      int64_t n_tiles, bool pipelined, bool quad26) {
   LaunchCfg c;
+  if (quad26) {
+    c.threads = kQuadThreads;
+    c.minb = 1;
+    c.lch = 64;
+    c.smem = smem_bytes(prec, Fmax, c.lch, c.threads);
+    c.ctas_per_sm = occupancy(prec, c.threads, c.minb, c.smem);
+    if (c.ctas_per_sm < 1) c.ctas_per_sm = 1;
+    int64_t g = (int64_t)c.ctas_per_sm * n_sm;
+    c.grid = (int)(n_tiles < g ? n_tiles : g);
+    if (c.grid < 1) c.grid = 1;
+    return c;
+  }
   if (prec != HYDRO_FP64 && pipelined && smem_bytes(prec, Fmax, 64, kPipeThreads) <= smem_optin) {
     c.threads = kPipeThreads;
     c.minb = 1;

@@ -180,8 +180,9 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
     p->info.interior_cells += N * N * N;
     p->info.alg_bytes += ((N * N * N + 6 * 3 * N * N) + N * N * N) * F * 8 + 8;
   }
+  const bool quad26 = (flags & HYDRO_PLAN_QUAD26) != 0;
   p->cfg = default_cfg(prec, p->Fmax, n_sm, smem_optin, (int64_t)tiles.size(),
-                       !(flags & HYDRO_PLAN_REGISTER_LOADS));
+                       !(flags & HYDRO_PLAN_REGISTER_LOADS), quad26);
   p->a_tiles = p->dev_tiles;
   p->a_n = (int)tiles.size();
   p->a_F = p->Fmax;
@@ -216,6 +217,8 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
         LaunchCfg c;
         variant(vi, &c.threads, &c.minb);
         if (!variant_exists(prec, c.threads, c.minb)) continue;
+        if ((c.threads == kQuadThreads) != quad26) continue;  // one scheme per plan
+        if (quad26 && (li != 2 || pf != 0)) continue;
         const bool pipe = c.threads == kPipeThreads;
         if (pipe && (li != 2 || pf != 0)) continue;  // chunking and prefetch do not apply
         if (pipe && (flags & HYDRO_PLAN_REGISTER_LOADS)) continue;

@@ -1,0 +1,362 @@
+// hydro_quad.cuh -- the 26-point quadrature variant of the hydro RHS.
+//
+// Sec. IV-B: PPM values at 26 points on the surface of every cell (6 face
+// centres, 12 edge midpoints, 8 vertices), central-upwind fluxes at those
+// points and Newton-Cotes quadrature of the fluxes over each face.  The value
+// of a cell at its surface point c + v/2 (v in {-1,0,1}^3) is the PPM face
+// value of the one-dimensional reconstruction along the line of cells
+// c + m v (cells m = -2..2 enter); a face normal to axis d carries the 9
+// points e_d + o1 e_a + o2 e_b, the left state from the low cell's line along
+// that vector (upper end), the right state from the high cell's line along
+// e_d - o1 e_a - o2 e_b (lower end), and the face flux is Simpson's rule in
+// both tangential directions, sum_p c_p Fhat_p / 36, c_p = (1,4,1)x(1,4,1).
+//
+// One CTA per 8^3 tile (persistent over the tile list), QNT threads:
+//   load   hydro primitives and 1/rho of the tile's read region (every cell
+//          with each coordinate in [-3, e+2] and at most one of them at -3 or
+//          e+2) into shared memory; species are read through the read-only
+//          cache and divided by rho on use;
+//   faces  per direction, each thread owns three of the 576 faces and sums the
+//          weighted fluxes of its 9 points in registers, then writes the face
+//          fluxes to shared memory;
+//   A4     each thread owns up to three cells and accumulates x, y, z flux
+//          differences (binary64, or exact binary32 pairs in the mixed form).
+#pragma once
+
+#include "hydro_kernels.cuh"
+
+namespace hydro_dev {
+
+constexpr int QNT = 192;                  // threads per CTA (3 faces per thread per direction)
+constexpr int QBLK = LL * LL * LL;        // 2744 cells of the ghosted 14^3 neighbourhood
+constexpr int QFACES = NLN * NFC;         // 576 faces per direction
+constexpr int QFPT = QFACES / QNT;        // faces per thread: 3
+constexpr int QCPT = (TE * TE * TE + QNT - 1) / QNT;  // cells per thread: 3
+static_assert(QFACES % QNT == 0, "faces divide evenly over the threads");
+
+template <int MODE>
+__host__ __device__ constexpr size_t quad_smem_bytes() {
+  return (MODE == 0 ? 8 : 4) * ((size_t)6 * QBLK + QBLK + (size_t)QFACES * MAXF);
+}
+
+__device__ __forceinline__ int qidx(int x, int y, int z) { return ((z + 3) * LL + (y + 3)) * LL + (x + 3); }
+
+// PPM face values of the middle cell of five line values q[0..4] (cells
+// -2..2), the same steps as ppm_line64 for one cell.
+__device__ __forceinline__ void ppm5_64(const double* q, double& lo, double& hi) {
+  double del[3];
+#pragma unroll
+  for (int c = 1; c <= 3; c++) {
+    double dp = q[c + 1] - q[c], dm = q[c] - q[c - 1];
+    double dbar = dhalf(q[c + 1] - q[c - 1]);
+    double m = dminp(dabs(dbar), dtwice(dminp(dabs(dm), dabs(dp))));
+    del[c - 1] = dsame(dp, dm) ? dcopysign(m, dbar) : 0.0;
+  }
+  const double sixth = 1.0 / 6.0;
+  const double qc = q[2];
+  double l = fma(del[0] - del[1], sixth, dhalf(q[1] + q[2]));
+  double h = fma(del[1] - del[2], sixth, dhalf(q[2] + q[3]));
+  double up = h - qc, dn = qc - l;
+  bool ext = !dsame(up, dn);
+  bool A = dsame(fma(-2.0, up, dn), up);
+  bool B = !A && dsame(-fma(2.0, dn, -up), up);
+  lo = ext ? qc : (A ? fma(-2.0, up, qc) : l);
+  hi = ext ? qc : (B ? fma(2.0, dn, qc) : h);
+}
+
+// The same for binary32, in ppm_line32x2's half-slope and clamp form.
+__device__ __forceinline__ void ppm5_32(const float* q, float& lo, float& hi) {
+  float d0 = q[1] - q[0], d1 = q[2] - q[1], d2 = q[3] - q[2], d3 = q[4] - q[3];
+  float h1 = hslope1(d0, d1, (d0 + d1) * 0.25f, d0 * d1);
+  float h2 = hslope1(d1, d2, (d1 + d2) * 0.25f, d1 * d2);
+  float h3 = hslope1(d2, d3, (d2 + d3) * 0.25f, d2 * d3);
+  const float qc = q[2];
+  float l = fmaf(h1 - h2, 1.0f / 3.0f, (q[1] + q[2]) * 0.5f);
+  float h = fmaf(h2 - h3, 1.0f / 3.0f, (q[2] + q[3]) * 0.5f);
+  float up = h - qc, dn = qc - l;
+  float uu = up + up, du = dn + dn;
+  limit1(qc, l, h, up, dn, up * dn, uu, du, qc - uu, qc + du, lo, hi);
+}
+
+template <int MODE>
+struct QuadPrec;
+template <>
+struct QuadPrec<0> {
+  typedef double R;
+  typedef double Acc;
+};
+template <>
+struct QuadPrec<1> {
+  typedef float R;
+  typedef F2 Acc;  // exact binary32 pair (h + l)
+};
+
+__device__ __forceinline__ void two_diff1(float a, float b, float& s, float& e) {
+  s = a - b;
+  float bb = s - a;
+  e = (a - (s - bb)) - (b + bb);
+}
+
+template <int MODE, class Fetch>
+__device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, double* __restrict__ out,
+                                               double* __restrict__ amax_out, Status* __restrict__ status,
+                                               double gamma_d, int write_status, bool knp) {
+  typedef typename QuadPrec<MODE>::R R;
+  typedef typename QuadPrec<MODE>::Acc Acc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* P = reinterpret_cast<R*>(smem_raw);  // [6][QBLK] hydro primitives
+  R* RR = P + 6 * QBLK;                    // [QBLK] 1/rho
+  R* FF = RR + QBLK;                       // [MAXF][QFACES] face fluxes of one direction
+  __shared__ double red[QNT / 32];
+  const int tid = threadIdx.x;
+  const float gamf = (float)gamma_d, gm1f = (float)(gamma_d - 1.0);
+  const R gamma = R(gamma_d), inv_gm1 = R(1.0 / (gamma_d - 1.0));
+  const bool g53 = gamma_d == 5.0 / 3.0;
+
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const Tile tile = fetch(t);
+    const int F = tile.F, N = tile.N, G = tile.G, gh = (G - N) >> 1, nsp = F - 6;
+    const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
+    const long long plane = (long long)G * G * G;
+    auto off_of = [&](int x, int y, int z) {
+      return ((tile.oz + z + gh) * G + (tile.oy + y + gh)) * G + (tile.ox + x + gh);
+    };
+
+    // ---- A0/A1: hydro primitives of the read region
+    bool bad = false;
+    for (int s = tid; s < QBLK; s += QNT) {
+      const int x = s % LL - 3, y = (s / LL) % LL - 3, z = s / (LL * LL) - 3;
+      const int far = (x == -3 || x == ex + 2) + (y == -3 || y == ey + 2) + (z == -3 || z == ez + 2);
+      if (x > ex + 2 || y > ey + 2 || z > ez + 2 || far > 1) continue;
+      const double* src = tile.U + off_of(x, y, z);
+      double u[6];
+#pragma unroll
+      for (int f = 0; f < 6; f++) u[f] = __ldg(src + f * plane);
+      if constexpr (MODE == 0) {
+        double w[6], r;
+        bad |= prim64(u, gamma_d, g53, w, r);
+#pragma unroll
+        for (int f = 0; f < 6; f++) P[f * QBLK + s] = w[f];
+        RR[s] = r;
+      } else {
+        float w[6], r;
+        bad |= prim_mixed(u, gamma_d, gamf, gm1f, g53, w, r);
+#pragma unroll
+        for (int f = 0; f < 6; f++) P[f * QBLK + s] = w[f];
+        RR[s] = r;
+      }
+      for (int k = 0; k < nsp; k++) bad |= !dfinite(__ldg(src + (6 + k) * plane));
+    }
+    bad = __syncthreads_or(bad);
+    if (bad && tid == 0 && write_status) {
+      atomicOr(&status->flags, 1u);
+      atomicMin(&status->first_bad, (unsigned long long)tile.sub);
+    }
+
+    R amax = R(0);
+    Acc acc[QCPT][MAXF];
+    const int ogl = off_of(0, 0, 0);  // stored-block offset of tile cell (0, 0, 0)
+    for (int d = 0; d < 3; d++) {
+      const int e_d = d == 0 ? ex : (d == 1 ? ey : ez);
+      const int e_a = d == 0 ? ey : ex, e_b = d == 2 ? ey : ez;
+      // index strides along d and the two tangential axes (a: x or y, b: y or z),
+      // in the shared-memory block (LL^axis) and in the stored block (G^axis)
+      const int Sd = d == 0 ? 1 : (d == 1 ? LL : LL * LL);
+      const int Sa = d == 0 ? LL : 1, Sb = d == 2 ? LL : LL * LL;
+      const int Gd = d == 0 ? 1 : (d == 1 ? G : G * G);
+      const int Ga = d == 0 ? G : 1, Gb = d == 2 ? G : G * G;
+      // ---- A2/A3: the faces of this direction, 9 points each
+#pragma unroll 1
+      for (int k = 0; k < QFPT; k++) {
+        const int face = tid + k * QNT, l = face / NFC, i = face - l * NFC;
+        const int ca = l % TE, cb = l / TE;
+        const bool fvalid = ca < e_a && cb < e_b && i <= e_d;
+        // the low cell (i-1 along d) and the high cell (i)
+        const int il = qidx(0, 0, 0) + (i - 1) * Sd + ca * Sa + cb * Sb, ir = il + Sd;
+        const int gl0 = ogl + (i - 1) * Gd + ca * Ga + cb * Gb, gr0 = gl0 + Gd;
+        R fsum[MAXF];
+#pragma unroll
+        for (int f = 0; f < MAXF; f++) fsum[f] = R(0);
+        // faces outside a partial tile are skipped: their stencils may leave
+        // the stored block
+#pragma unroll 1
+        for (int p = 0; p < (fvalid ? 9 : 0); p++) {
+          const int o1 = p % 3 - 1, o2 = p / 3 - 1;
+          // lines e_d + o1 e_a + o2 e_b through the low cell, e_d - o1 e_a - o2 e_b
+          // through the high cell
+          const int sl = Sd + o1 * Sa + o2 * Sb, sr = Sd - o1 * Sa - o2 * Sb;
+          const int gsl = Gd + o1 * Ga + o2 * Gb, gsr = Gd - o1 * Ga - o2 * Gb;
+          R wl[MAXF], wr[MAXF];
+#pragma unroll
+          for (int f = 0; f < 6; f++) {
+            R ql[5], qr[5], lo, hi;
+#pragma unroll
+            for (int m = 0; m < 5; m++) {
+              ql[m] = P[f * QBLK + il + (m - 2) * sl];
+              qr[m] = P[f * QBLK + ir + (m - 2) * sr];
+            }
+            if constexpr (MODE == 0) {
+              ppm5_64(ql, lo, hi);
+              wl[f] = hi;
+              ppm5_64(qr, lo, hi);
+              wr[f] = lo;
+            } else {
+              ppm5_32(ql, lo, hi);
+              wl[f] = hi;
+              ppm5_32(qr, lo, hi);
+              wr[f] = lo;
+            }
+          }
+          // species X_k = rho_k / rho on the stencil cells
+#pragma unroll
+          for (int f = 6; f < MAXF; f++) {
+            if (f - 6 >= nsp) break;
+            const double* base = tile.U + f * plane;
+            R ql[5], qr[5], lo, hi;
+#pragma unroll
+            for (int m = 0; m < 5; m++) {
+              const double ul = __ldg(base + gl0 + (m - 2) * gsl), ur = __ldg(base + gr0 + (m - 2) * gsr);
+              const R rl = RR[il + (m - 2) * sl], rr = RR[ir + (m - 2) * sr];
+              if constexpr (MODE == 0) {
+                ql[m] = ul * rl;
+                qr[m] = ur * rr;
+              } else {
+                ql[m] = d2f_int(ul) * rl;
+                qr[m] = d2f_int(ur) * rr;
+              }
+            }
+            if constexpr (MODE == 0) {
+              ppm5_64(ql, lo, hi);
+              wl[f] = hi;
+              ppm5_64(qr, lo, hi);
+              wr[f] = lo;
+            } else {
+              ppm5_32(ql, lo, hi);
+              wl[f] = hi;
+              ppm5_32(qr, lo, hi);
+              wr[f] = lo;
+            }
+          }
+          // central-upwind flux at the point
+          R fh[MAXF], g_l, g_r, a;
+          if constexpr (MODE == 0) {
+            a = kt_hydro64(wl, wr, d, gamma, inv_gm1, knp, fh, 1, g_l, g_r);
+          } else {
+            float2 pl[3] = {make_float2(wl[0], wl[1]), make_float2(wl[2], wl[3]), make_float2(wl[4], wl[5])};
+            float2 pr[3] = {make_float2(wr[0], wr[1]), make_float2(wr[2], wr[3]), make_float2(wr[4], wr[5])};
+            float2 fo[3];
+            a = kt_hydro32(pl, pr, d, gamma, inv_gm1, knp, fo, 1, g_l, g_r);
+            fh[0] = fo[0].x, fh[1] = fo[0].y, fh[2] = fo[1].x, fh[3] = fo[1].y, fh[4] = fo[2].x, fh[5] = fo[2].y;
+          }
+#pragma unroll
+          for (int f = 6; f < MAXF; f++)
+            if (f - 6 < nsp) {
+              if constexpr (MODE == 0) fh[f] = fma(wl[f], g_l, wr[f] * g_r);
+              else fh[f] = fmaf(wl[f], g_l, wr[f] * g_r);
+            }
+          const R cw = R((o1 == 0 ? 4 : 1) * (o2 == 0 ? 4 : 1));
+#pragma unroll
+          for (int f = 0; f < MAXF; f++)
+            if (f < F) {
+              if constexpr (MODE == 0) fsum[f] = fma(cw, fh[f], fsum[f]);
+              else fsum[f] = fmaf(cw, fh[f], fsum[f]);
+            }
+          if constexpr (MODE == 0) amax = dmaxp(amax, a);
+          else amax = fmaxf(amax, a);
+        }
+#pragma unroll
+        for (int f = 0; f < MAXF; f++)
+          if (f < F) FF[f * QFACES + face] = fsum[f] / R(36);
+      }
+      __syncthreads();
+      // ---- A4: flux differences of the owned cells
+#pragma unroll
+      for (int k = 0; k < QCPT; k++) {
+        const int m = tid + k * QNT;
+        if (m < TE * TE * TE) {
+          const int x = m % TE, y = (m / TE) % TE, z = m / (TE * TE);
+          const int l = d == 0 ? z * TE + y : (d == 1 ? z * TE + x : y * TE + x);
+          const int pos = d == 0 ? x : (d == 1 ? y : z);
+          const R* fl = FF + l * NFC + pos;
+#pragma unroll
+          for (int f = 0; f < MAXF; f++)
+            if (f < F) {
+              const R hi = fl[f * QFACES + 1], lo = fl[f * QFACES];
+              if constexpr (MODE == 0) {
+                acc[k][f] = d == 0 ? hi - lo : acc[k][f] + (hi - lo);
+              } else {
+                float dh, dl;
+                two_diff1(hi, lo, dh, dl);
+                if (d == 0) {
+                  acc[k][f].h = dh;
+                  acc[k][f].l = dl;
+                } else {
+                  F2 s = two_sum(acc[k][f].h, dh);
+                  acc[k][f].h = s.h;
+                  acc[k][f].l = (acc[k][f].l + dl) + s.l;
+                }
+              }
+            }
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- store dU/dt = -(sum of differences)/dx
+    const long long n3 = (long long)N * N * N;
+    const double scale = -tile.inv_dx;
+    const bool pow2 = (tile.flags & 2) != 0;
+    const float sf = pow2 ? d2f_int(scale) : 0.0f;
+#pragma unroll
+    for (int k = 0; k < QCPT; k++) {
+      const int m = tid + k * QNT;
+      if (m < TE * TE * TE) {
+        const int x = m % TE, y = (m / TE) % TE, z = m / (TE * TE);
+        if (x < ex && y < ey && z < ez) {
+          double* o = out + tile.out_off + ((long long)(tile.oz + z) * N + (tile.oy + y)) * N + (tile.ox + x);
+#pragma unroll
+          for (int f = 0; f < MAXF; f++)
+            if (f < F) {
+              double v;
+              if constexpr (MODE == 0) v = acc[k][f] * scale;
+              else v = pair_value(acc[k][f].h, acc[k][f].l, scale, sf, pow2);
+              o[f * n3] = v;
+            }
+        }
+      }
+    }
+
+    // ---- A5: largest signal speed of the tile
+    double am = (double)amax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) am = dmaxp(am, __shfl_xor_sync(0xffffffffu, am, o));
+    if ((tid & 31) == 0) red[tid >> 5] = am;
+    __syncthreads();
+    if (tid == 0) {
+      double mx = red[0];
+      for (int w = 1; w < QNT / 32; w++) mx = dmaxp(mx, red[w]);
+      if (tile.flags & 1)
+        atomicMax(reinterpret_cast<unsigned long long*>(amax_out + tile.amax_off),
+                  (unsigned long long)__double_as_longlong(mx));
+      else
+        amax_out[tile.amax_off] = mx;
+    }
+    __syncthreads();
+  }
+}
+
+// Same arguments as rhs_tiles_kernel; lch and prefetch do not apply.  One
+// CTA per SM in binary64 (up to 255 registers per thread), two in the mixed
+// form (shared memory and registers of a sub-partition allow it).
+template <int MODE>
+__global__ void __launch_bounds__(QNT, MODE == 0 ? 1 : 2)
+rhs_quad_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch, double* __restrict__ out,
+                double* __restrict__ amax_out, Status* __restrict__ status, double gamma_d,
+                int write_status, int prefetch, int scheme) {
+  (void)Fmax;
+  (void)lch;
+  (void)prefetch;
+  tile_loop_quad<MODE>(TileList{tiles}, n_tiles, out, amax_out, status, gamma_d, write_status, scheme == 1);
+}
+
+}  // namespace hydro_dev
