@@ -62,7 +62,10 @@ extern "C" {
 /* One sub-grid task.  The aggregation allocator's per-task chunk of Sec. V-D:
  * each task brings its own input block; the library packs the outputs. */
 typedef struct {
-  const double* U; /* device, [n_fields][N+2g]^3, x fastest */
+  const double* U; /* [n_fields][N+2g]^3, x fastest; memory the GPU can read: device
+                      memory, or pinned host memory (cudaHostAlloc / cudaHostRegister),
+                      which the kernels read in place over the host link -- on GB300
+                      NVLink-C2C -- moving only the cells the scheme reads */
   double dx;       /* cell width > 0 (depends on the octree level) */
   int32_t N;       /* interior cells per edge, 2..HYDRO_MAX_N (8 and 16 are the paper's) */
   int32_t n_fields;
@@ -86,7 +89,8 @@ typedef enum { HYDRO_FP64 = 0, HYDRO_FP32_FLUX_FP64_ACC = 1 } hydro_precision_t;
  *              HYDRO_EINVAL; 0 means per-descriptor values
  *   ghost      ghost layers stored in U, >= 3 (layers beyond 3 are ignored)
  *   gamma      ratio of specific heats, > 1
- *   out_dUdt, out_amax  DEVICE outputs as described above
+ *   out_dUdt, out_amax  outputs as described above, in device memory or in
+ *              pinned host memory (written in place by the kernel)
  * Allocation: the first call on a device (and a call with a larger batch than
  * any before) allocates library workspace; later calls allocate nothing. */
 int hydro_rhs(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t N, int32_t ghost,

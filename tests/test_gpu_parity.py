@@ -262,3 +262,40 @@ def test_polytropes_full_size_sampled():
             gh.check_mixed(got, ref, gam, ram, blocks, [batch.dx] * len(sample))
         p.close()
         del out, amax
+
+
+# ---------------------------------------------- inputs in pinned host memory --
+@pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
+def test_pinned_host_buffers_are_read_in_place(prec):
+    """Descriptors and outputs may point into pinned host memory: the kernels
+    read and write it in place over the host link, with the same bits as
+    device buffers (both mixed kernel families, plans and direct calls)."""
+    leaves = synth.uneven_octree(n_subgrids=24)
+    blocks = [synth.leaf_block(synth.BASE_SEED + 2, l) for l in leaves]
+    dxs = [l[2] for l in leaves]
+    dev = gh.to_dev(blocks)
+    host = [torch.from_numpy(np.ascontiguousarray(b)).pin_memory() for b in blocks]
+    ref, ram = gh.run_gpu(dev, dxs, prec=prec)
+    items = [(h, dx, h.shape[1] - 6, h.shape[0]) for h, dx in zip(host, dxs)]
+    desc = hydro.descriptors(items)
+    n = len(items)
+    out = torch.full((hydro.output_doubles(desc, n),), float("nan"), dtype=torch.float64).pin_memory()
+    amax = torch.full((n,), float("nan"), dtype=torch.float64).pin_memory()
+    flag_sets = [0] if prec == hydro.FP64 else [0, hydro.F_REGISTER_LOADS]
+    for flags in flag_sets:
+        out.fill_(float("nan"))
+        hydro.rhs(desc, out, amax, prec=prec, n=n, flags=flags)
+        torch.cuda.synchronize()
+        off = 0
+        for s, (h, dx, N, F) in enumerate(items):
+            m = F * N ** 3
+            assert np.array_equal(out[off:off + m].numpy().reshape(F, N, N, N), ref[s]), s
+            off += m
+        assert np.array_equal(amax.numpy(), ram)
+    p = hydro.Plan(desc, prec=prec, autotune=True, n=n)
+    out.fill_(float("nan"))
+    p.execute(out, amax)
+    torch.cuda.synchronize()
+    p.close()
+    assert np.array_equal(amax.numpy(), ram)
+    assert np.array_equal(out[:ref[0].size].numpy().reshape(ref[0].shape), ref[0])
