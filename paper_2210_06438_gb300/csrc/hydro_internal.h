@@ -18,8 +18,10 @@ namespace hydro_host {
 
 // Launch shape of the tile kernel.
 struct LaunchCfg {
-  int threads = 256;   // threads per CTA (128, 256 or 512; 576: the pipelined mixed kernel)
+  int threads = 256;   // threads per CTA (128, 256, 384 or 512; 576: the pipelined mixed kernel;
+                       // 192: the 26-point kernels)
   int minb = 1;        // kernel variant: minimum resident CTAs per SM it was compiled for
+  int kc = 4;          // kernel variant: read-region slots per load batch (register-load kernels)
   int lch = 32;        // lines per chunk of the reconstruct/flux phases (16, 32 or 64)
   int grid = 0;        // CTAs (persistent: a multiple of the SM count)
   int ctas_per_sm = 1;
@@ -30,10 +32,10 @@ struct LaunchCfg {
 cudaError_t kernels_init(int smem_optin);
 // threads == kPipeThreads selects the pipelined mixed kernel's layout
 int smem_bytes(hydro_precision_t prec, int Fmax, int lch, int threads = 256);
-int occupancy(hydro_precision_t prec, int threads, int minb, int smem);
+int occupancy(hydro_precision_t prec, int threads, int minb, int smem, int kc);
 int num_variants();
-void variant(int i, int* threads, int* minb);
-bool variant_exists(hydro_precision_t prec, int threads, int minb);
+void variant(int i, int* threads, int* minb, int* kc);
+bool variant_exists(hydro_precision_t prec, int threads, int minb, int kc);
 constexpr int kPipeThreads = 576;
 constexpr int kQuadThreads = 192;  // the 26-point quadrature kernels
 // pipelined: use the pipelined mixed kernel (ignored for binary64);

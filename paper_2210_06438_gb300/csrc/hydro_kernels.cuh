@@ -114,6 +114,27 @@ __device__ __forceinline__ int line_slot(int d, int l, int c) {
   return slot_of(a, b, c - 3);
 }
 
+// Addressing of line l along direction d in the read-region layout: three
+// segments (3 low ghosts, TE interior cells, 3 high ghosts), each with a
+// base slot and a constant stride.
+struct LineAddr {
+  int lo, in, hi, sg, si;
+  __device__ __forceinline__ int at(int c) const {
+    return c < 3 ? lo + c * sg : (c < 3 + TE ? in + (c - 3) * si : hi + (c - 3 - TE) * sg);
+  }
+};
+__device__ __forceinline__ LineAddr line_addr(int d, int l) {
+  int a = l % TE, b = l / TE;
+  if (d == 0) {
+    int base = (b * TE + a) * LL;
+    return {base, base + 3, base + 3 + TE, 1, 1};
+  }
+  if (d == 1)
+    return {XROWS + b * 6 * TE + a, b * TE * LL + a + 3, XROWS + b * 6 * TE + 3 * TE + a, TE, LL};
+  return {XROWS + YSLAB + b * TE + a, b * LL + a + 3, XROWS + YSLAB + 3 * TE * TE + b * TE + a,
+          TE * TE, TE * LL};
+}
+
 // ============================================= binary64 on the integer pipe ==
 // Bit-pattern helpers.  They are exact for zero and for normal numbers of
 // magnitude >= 2^-1021 (far below any value a hydro state produces); the
@@ -136,6 +157,10 @@ __device__ __forceinline__ double dhalf(double x) {  // x/2 (zero stays zero)
 __device__ __forceinline__ bool dsame(double a, double b) {
   int x = hiw(a), y = hiw(b);
   return ((x ^ y) >= 0) && (x & 0x7fffffff) && (y & 0x7fffffff);
+}
+// |a| > |b|, compared exactly on the bit patterns
+__device__ __forceinline__ bool dabs_gt(double a, double b) {
+  return (__double_as_longlong(a) & 0x7fffffffffffffffLL) > (__double_as_longlong(b) & 0x7fffffffffffffffLL);
 }
 // order-preserving integer key of a double (NaN excluded)
 __device__ __forceinline__ long long dkey(double x) {
@@ -228,47 +253,56 @@ __device__ __forceinline__ bool prim64(const double* u, double gamma, bool g53, 
 //   left[i] = q+ of cell i-1,  right[i] = q- of cell i   (shared memory).
 // With up = q+ - q and dn = q - q- (same sign s, else the cell is an
 // extremum and flattened), m = q - (q- + q+)/2 = (dn - up)/2 and D = up + dn,
-// the parabola tests become sign tests:
-//   D m >  D^2/6  <=>  s (dn - 2 up) > 0   ->  q- = q - 2 up  (= 3q - 2q+)
-//   D m < -D^2/6  <=>  s (2 dn - up) < 0   ->  q+ = q + 2 dn  (= 3q - 2q-)
-// The limiter is continuous at both switching surfaces, so evaluating the
-// tests with different rounding than the reference moves results by
-// rounding errors only.
-__device__ __forceinline__ void ppm_line64(const double* q, double* left, double* right) {
-  double dq[LL - 1];
-#pragma unroll
-  for (int c = 0; c < LL - 1; c++) dq[c] = q[c + 1] - q[c];
-  double del[LL];
-#pragma unroll
-  for (int c = 1; c <= LL - 2; c++) {
-    double dp = dq[c], dm = dq[c - 1];
-    double dbar = dhalf(q[c + 1] - q[c - 1]);
-    double m = dminp(dabs(dbar), dtwice(dminp(dabs(dm), dabs(dp))));
-    del[c] = dsame(dp, dm) ? dcopysign(m, dbar) : 0.0;
-  }
+// the parabola tests become comparisons of magnitudes:
+//   D m >  D^2/6  <=>  s (dn - 2 up) > 0  <=>  |dn| > 2|up|  ->  q- = q - 2 up  (= 3q - 2q+)
+//   D m < -D^2/6  <=>  s (2 dn - up) < 0  <=>  |up| > 2|dn|  ->  q+ = q + 2 dn  (= 3q - 2q-)
+// evaluated exactly on the integer pipe; the two cases exclude each other,
+// so one fused multiply-add gives whichever new face value is needed.  The
+// limiter is continuous at both switching surfaces, so evaluating the tests
+// with different rounding than the reference moves results by rounding
+// errors only.
+// One pass along the line keeping a short window of values live (as
+// ppm_line32x2): at step c the slope of cell c, the face c-1/2 and the limited
+// states of cell c-1.  w: the line in shared memory (la addresses it).
+__device__ __forceinline__ void ppm_line64(const double* w, const LineAddr& la, double* left,
+                                           double* right) {
   const double sixth = 1.0 / 6.0;
-  double fc[LL];
+  auto slope = [](double dm, double dp) {
+    double dbar = dhalf(dp + dm);
+    double m = dminp(dabs(dbar), dtwice(dminp(dabs(dm), dabs(dp))));
+    return dsame(dp, dm) ? dcopysign(m, dbar) : 0.0;
+  };
+  double q0 = w[la.at(0)], q1 = w[la.at(1)], q2 = w[la.at(2)];
+  double dm = q2 - q1;
+  double del_prev = slope(q1 - q0, dm);  // cell c = 1
+  double face_prev = 0.0;                // face c - 3/2
+  double qm = q1, qc = q2;               // q[c-1], q[c] for c = 2
 #pragma unroll
-  for (int c = 1; c <= LL - 3; c++) fc[c] = fma(del[c] - del[c + 1], sixth, dhalf(q[c] + q[c + 1]));
-#pragma unroll
-  for (int c = 2; c <= LL - 3; c++) {  // cells -1 .. TE
-    double qc = q[c], lo = fc[c - 1], hi = fc[c];
-    double up = hi - qc, dn = qc - lo;
-    bool ext = !dsame(up, dn);
-    double t1 = fma(-2.0, up, dn);  // dn - 2 up
-    double t2 = fma(2.0, dn, -up);  // 2 dn - up
-    bool A = dsame(t1, up);
-    bool B = !A && dsame(-t2, up);
-    double lo2 = fma(-2.0, up, qc);
-    double hi2 = fma(2.0, dn, qc);
-    lo = ext ? qc : (A ? lo2 : lo);
-    hi = ext ? qc : (B ? hi2 : hi);
-    int j = c - 3;
-    if (j >= 0) right[j] = lo;
-    if (j + 1 <= TE) left[j + 1] = hi;
+  for (int c = 2; c <= LL - 2; c++) {
+    double qp = w[la.at(c + 1)];
+    double dp = qp - qc;
+    double del = slope(dm, dp);  // slope of cell c
+    double face = fma(del_prev - del, sixth, dhalf(qm + qc));  // between cells c-1 and c
+    if (c >= 3) {  // limit cell c-1 with faces face_prev (left) and face (right)
+      double lo = face_prev, hi = face, q = qm;
+      double up = hi - q, dn = q - lo;
+      bool ext = !dsame(up, dn);
+      bool A = dabs_gt(dn, dtwice(up));  // |dn| > 2|up|
+      bool B = dabs_gt(up, dtwice(dn));  // |up| > 2|dn| (excludes A)
+      double nv = fma(A ? -2.0 : 2.0, A ? up : dn, q);  // q - 2 up, or q + 2 dn
+      lo = ext ? q : (A ? nv : lo);
+      hi = ext ? q : (B ? nv : hi);
+      int j = c - 4;  // cell index of c-1
+      if (j >= 0) right[j] = lo;
+      if (j + 1 <= TE) left[j + 1] = hi;
+    }
+    face_prev = face;
+    del_prev = del;
+    dm = dp;
+    qm = qc;
+    qc = qp;
   }
 }
-
 
 // ---------------------------------------------------- step A3, binary64 --
 // Central flux (Kurganov & Tadmor 2000) through a face normal to axis d,
@@ -411,27 +445,6 @@ __device__ __forceinline__ bool prim_mixed(const double* u, double gamma, float 
 #pragma unroll
   for (int f = 0; f < 6; f++) bad |= !dfinite(u[f]);
   return bad;
-}
-
-// Addressing of line l along direction d in the read-region layout: three
-// segments (3 low ghosts, TE interior cells, 3 high ghosts), each with a
-// base slot and a constant stride.
-struct LineAddr {
-  int lo, in, hi, sg, si;
-  __device__ __forceinline__ int at(int c) const {
-    return c < 3 ? lo + c * sg : (c < 3 + TE ? in + (c - 3) * si : hi + (c - 3 - TE) * sg);
-  }
-};
-__device__ __forceinline__ LineAddr line_addr(int d, int l) {
-  int a = l % TE, b = l / TE;
-  if (d == 0) {
-    int base = (b * TE + a) * LL;
-    return {base, base + 3, base + 3 + TE, 1, 1};
-  }
-  if (d == 1)
-    return {XROWS + b * 6 * TE + a, b * TE * LL + a + 3, XROWS + b * 6 * TE + 3 * TE + a, TE, LL};
-  return {XROWS + YSLAB + b * TE + a, b * LL + a + 3, XROWS + YSLAB + 3 * TE * TE + b * TE + a,
-          TE * TE, TE * LL};
 }
 
 // -------------------------------------------- packed binary32 arithmetic --
@@ -699,10 +712,7 @@ __device__ __forceinline__ void group_pass(
         LineAddr la = line_addr(d, l0 + ll);
         const V* w = W + j * STAR;
         if constexpr (MODE == 0) {
-          V q[LL];
-#pragma unroll
-          for (int c = 0; c < LL; c++) q[c] = w[la.at(c)];
-          ppm_line64(q, QS + j * fs + ll * NFC, QR + j * fs + ll * NFC);
+          ppm_line64(w, la, QS + j * fs + ll * NFC, QR + j * fs + ll * NFC);
         } else {
           ppm_line32x2(w, la, QS + j * fs + ll * NFC, QR + j * fs + ll * NFC);
         }
@@ -896,7 +906,7 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
     // ---- A0/A1 (hydro group): rho, s, E, tau -> rho, v, p, phi.  In each
     // batch every load is issued before any result is used.
     bool bad = false;
-#pragma unroll
+#pragma unroll 1
     for (int k0 = 0; k0 < SPT; k0 += KC) {
       double u[KC][6];
       int off[KC];
@@ -946,7 +956,7 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
     // ---- A0/A1 (species): X_k = rho_k / rho into the group slots
     const int nsp = F - 6;
     if (nsp > 0) {
-#pragma unroll
+#pragma unroll 1
       for (int k0 = 0; k0 < SPT; k0 += KC) {
         double v[KC][MAXF - 6];
         int off[KC];
@@ -1018,17 +1028,18 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
   }
 }
 
-template <int MODE, int NT, int MINB>
+// KC: read-region slots per load batch (more loads in flight with more
+// registers per thread; the autotuner picks among compiled variants).
+template <int MODE, int NT, int MINB, int KC = (MINB == 1 ? 4 : 2)>
 __global__ void __launch_bounds__(NT, MINB)
 rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
                  double* __restrict__ out, double* __restrict__ amax_out,
                  Status* __restrict__ status, double gamma_d, int write_status, int prefetch,
                  int scheme) {
   (void)Fmax;  // the shared-memory layout does not depend on the field count
-  // KC: read-region slots per load batch (more loads in flight with more
-  // registers per thread).  scheme: 0 Kurganov-Tadmor, 1 Kurganov-Noelle-Petrova.
-  tile_loop<MODE, NT, MINB == 1 ? 4 : 2>(TileList{tiles}, n_tiles, lch, out, amax_out, status,
-                                         gamma_d, write_status, prefetch, scheme == 1);
+  // scheme: 0 Kurganov-Tadmor, 1 Kurganov-Noelle-Petrova.
+  tile_loop<MODE, NT, KC>(TileList{tiles}, n_tiles, lch, out, amax_out, status, gamma_d, write_status,
+                          prefetch, scheme == 1);
 }
 
 // ================================================ pipelined mixed kernel ==

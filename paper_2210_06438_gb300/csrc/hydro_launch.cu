@@ -7,49 +7,49 @@ namespace hydro_host {
 
 using hydro_dev::rhs_tiles_kernel;
 
-// Kernel variants: (threads per CTA, minimum resident CTAs per SM).  The
-// second number caps registers per thread (65536 / (threads * minb)); the
-// autotuner picks among them per batch.  {576, 1} is the pipelined mixed
-// kernel (no binary64 counterpart).
+// Kernel variants: (threads per CTA, minimum resident CTAs per SM, load
+// batch).  The second number caps registers per thread (65536 / (threads *
+// minb)), the third sets how many read-region slots a thread loads at once;
+// the autotuner picks among them per batch.  {576, 1} is the pipelined mixed
+// kernel (no binary64 counterpart), {192, 1} the 26-point kernel.
 struct Variant {
-  int threads, minb;
+  int threads, minb, kc;
 };
-static const Variant kVariants[] = {{256, 1}, {128, 1}, {512, 1}, {256, 2}, {128, 2}, {256, 3}, {128, 4},
-                                    {kPipeThreads, 1}, {kQuadThreads, 1}};
+static const Variant kVariants[] = {{256, 1, 4}, {128, 1, 4}, {512, 1, 4}, {512, 1, 2}, {384, 1, 4},
+                                    {384, 1, 2}, {256, 2, 2}, {128, 2, 2}, {kPipeThreads, 1, 0},
+                                    {kQuadThreads, 1, 0}};
+static constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 static_assert(kPipeThreads == hydro_dev::PNT, "pipelined kernel block size");
 static_assert(kQuadThreads == hydro_dev::QNT, "26-point kernel block size");
-static constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int MODE>
-static void* kfunc(int threads, int minb) {
+static void* kfunc(int threads, int minb, int kc) {
   if (threads == kPipeThreads) return MODE == 1 ? (void*)&hydro_dev::rhs_tiles_pipe_kernel<kPipeThreads> : nullptr;
   if (threads == kQuadThreads) return (void*)&hydro_dev::rhs_quad_kernel<MODE>;
-  if (threads == 128) {
-    if (minb == 4) return (void*)&rhs_tiles_kernel<MODE, 128, 4>;
-    return minb == 2 ? (void*)&rhs_tiles_kernel<MODE, 128, 2> : (void*)&rhs_tiles_kernel<MODE, 128, 1>;
-  }
-  if (threads == 512) return (void*)&rhs_tiles_kernel<MODE, 512, 1>;
-  if (minb == 3) return (void*)&rhs_tiles_kernel<MODE, 256, 3>;
-  return minb == 2 ? (void*)&rhs_tiles_kernel<MODE, 256, 2> : (void*)&rhs_tiles_kernel<MODE, 256, 1>;
+  if (threads == 128) return minb == 2 ? (void*)&rhs_tiles_kernel<MODE, 128, 2, 2> : (void*)&rhs_tiles_kernel<MODE, 128, 1, 4>;
+  if (threads == 512) return kc == 2 ? (void*)&rhs_tiles_kernel<MODE, 512, 1, 2> : (void*)&rhs_tiles_kernel<MODE, 512, 1, 4>;
+  if (threads == 384) return kc == 2 ? (void*)&rhs_tiles_kernel<MODE, 384, 1, 2> : (void*)&rhs_tiles_kernel<MODE, 384, 1, 4>;
+  return minb == 2 ? (void*)&rhs_tiles_kernel<MODE, 256, 2, 2> : (void*)&rhs_tiles_kernel<MODE, 256, 1, 4>;
 }
 
-static void* pick(hydro_precision_t prec, int threads, int minb) {
-  return prec == HYDRO_FP64 ? kfunc<0>(threads, minb) : kfunc<1>(threads, minb);
+static void* pick(hydro_precision_t prec, int threads, int minb, int kc) {
+  return prec == HYDRO_FP64 ? kfunc<0>(threads, minb, kc) : kfunc<1>(threads, minb, kc);
 }
 
 int num_variants() { return kNumVariants; }
-bool variant_exists(hydro_precision_t prec, int threads, int minb) {
-  return pick(prec, threads, minb) != nullptr;
+bool variant_exists(hydro_precision_t prec, int threads, int minb, int kc) {
+  return pick(prec, threads, minb, kc) != nullptr;
 }
-void variant(int i, int* threads, int* minb) {
+void variant(int i, int* threads, int* minb, int* kc) {
   *threads = kVariants[i].threads;
   *minb = kVariants[i].minb;
+  *kc = kVariants[i].kc;
 }
 
 cudaError_t kernels_init(int smem_optin) {
   for (int m = 0; m < 2; m++)
     for (int i = 0; i < kNumVariants; i++) {
-      void* f = pick((hydro_precision_t)m, kVariants[i].threads, kVariants[i].minb);
+      void* f = pick((hydro_precision_t)m, kVariants[i].threads, kVariants[i].minb, kVariants[i].kc);
       if (!f) continue;
       cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
       if (e != cudaSuccess) return e;
@@ -66,9 +66,9 @@ int smem_bytes(hydro_precision_t prec, int Fmax, int lch, int threads) {
                                   : hydro_dev::smem_layout_bytes<1>(lch));
 }
 
-int occupancy(hydro_precision_t prec, int threads, int minb, int smem) {
+int occupancy(hydro_precision_t prec, int threads, int minb, int smem, int kc) {
   int nb = 0;
-  void* f = pick(prec, threads, minb);
+  void* f = pick(prec, threads, minb, kc);
   if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != cudaSuccess)
     return 0;
   return nb;
@@ -82,7 +82,8 @@ LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin
     c.minb = 1;
     c.lch = 64;
     c.smem = smem_bytes(prec, Fmax, c.lch, c.threads);
-    c.ctas_per_sm = occupancy(prec, c.threads, c.minb, c.smem);
+    c.kc = 0;
+    c.ctas_per_sm = occupancy(prec, c.threads, c.minb, c.smem, c.kc);
     if (c.ctas_per_sm < 1) c.ctas_per_sm = 1;
     int64_t g = (int64_t)c.ctas_per_sm * n_sm;
     c.grid = (int)(n_tiles < g ? n_tiles : g);
@@ -92,6 +93,7 @@ LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin
   if (prec != HYDRO_FP64 && pipelined && smem_bytes(prec, Fmax, 64, kPipeThreads) <= smem_optin) {
     c.threads = kPipeThreads;
     c.minb = 1;
+    c.kc = 0;
     c.lch = 64;
     c.smem = smem_bytes(prec, Fmax, c.lch, c.threads);
     c.ctas_per_sm = 1;
@@ -101,13 +103,14 @@ LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin
   }
   c.threads = 256;
   c.minb = 1;
+  c.kc = 4;
   c.lch = prec == HYDRO_FP64 ? 32 : 64;
   c.smem = smem_bytes(prec, Fmax, c.lch);
   while (c.smem > smem_optin && c.lch > 16) {
     c.lch /= 2;
     c.smem = smem_bytes(prec, Fmax, c.lch);
   }
-  c.ctas_per_sm = occupancy(prec, c.threads, c.minb, c.smem);
+  c.ctas_per_sm = occupancy(prec, c.threads, c.minb, c.smem, c.kc);
   if (c.ctas_per_sm < 1) c.ctas_per_sm = 1;
   int64_t g = (int64_t)c.ctas_per_sm * n_sm;
   c.grid = (int)(n_tiles < g ? n_tiles : g);
@@ -122,12 +125,12 @@ cudaError_t launch_tiles(const LaunchCfg& cfg, hydro_precision_t prec, const hyd
   void* args[] = {(void*)&tiles, (void*)&n_tiles, (void*)&Fmax, (void*)&lch, (void*)&out,
                   (void*)&amax, (void*)&status, (void*)&gamma, (void*)&write_status, (void*)&pf,
                   (void*)&scheme};
-  return cudaLaunchKernel(pick(prec, cfg.threads, cfg.minb), dim3(cfg.grid), dim3(cfg.threads), args,
+  return cudaLaunchKernel(pick(prec, cfg.threads, cfg.minb, cfg.kc), dim3(cfg.grid), dim3(cfg.threads), args,
                           (size_t)cfg.smem, st);
 }
 
 void kernel_node(const LaunchCfg& cfg, hydro_precision_t prec, void** func) {
-  *func = pick(prec, cfg.threads, cfg.minb);
+  *func = pick(prec, cfg.threads, cfg.minb, cfg.kc);
 }
 
 }  // namespace hydro_host

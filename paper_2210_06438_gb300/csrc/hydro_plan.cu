@@ -215,8 +215,8 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
       for (int li = 0; li < 3; li++)
       for (int pf = 0; pf < 3; pf += 2) {
         LaunchCfg c;
-        variant(vi, &c.threads, &c.minb);
-        if (!variant_exists(prec, c.threads, c.minb)) continue;
+        variant(vi, &c.threads, &c.minb, &c.kc);
+        if (!variant_exists(prec, c.threads, c.minb, c.kc)) continue;
         if ((c.threads == kQuadThreads) != quad26) continue;  // one scheme per plan
         if (quad26 && (li != 2 || pf != 0)) continue;
         const bool pipe = c.threads == kPipeThreads;
@@ -227,7 +227,7 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
         c.prefetch = pf;
         c.smem = smem_bytes(prec, p->Fmax, c.lch, c.threads);
         if (c.smem > smem_optin) continue;
-        int occ = occupancy(prec, c.threads, c.minb, c.smem);
+        int occ = occupancy(prec, c.threads, c.minb, c.smem, c.kc);
         if (occ < 1) continue;
         for (int k = 1; k <= occ; k++) {
           c.ctas_per_sm = k;

@@ -58,10 +58,10 @@ __device__ __forceinline__ void ppm5_64(const double* q, double& lo, double& hi)
   double h = fma(del[1] - del[2], sixth, dhalf(q[2] + q[3]));
   double up = h - qc, dn = qc - l;
   bool ext = !dsame(up, dn);
-  bool A = dsame(fma(-2.0, up, dn), up);
-  bool B = !A && dsame(-fma(2.0, dn, -up), up);
-  lo = ext ? qc : (A ? fma(-2.0, up, qc) : l);
-  hi = ext ? qc : (B ? fma(2.0, dn, qc) : h);
+  bool A = dabs_gt(dn, dtwice(up)), B = dabs_gt(up, dtwice(dn));
+  double nv = fma(A ? -2.0 : 2.0, A ? up : dn, qc);
+  lo = ext ? qc : (A ? nv : l);
+  hi = ext ? qc : (B ? nv : h);
 }
 
 // The same for binary32, in ppm_line32x2's half-slope and clamp form.
