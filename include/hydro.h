@@ -156,6 +156,8 @@ typedef struct {
   int32_t lines_per_chunk; /* lines reconstructed per shared-memory chunk */
   int32_t prefetch;        /* L2 prefetch of the next tile: 0 none, 1 per row, 2 per plane */
   int32_t regs_cap;        /* kernel variant: 65536 / (threads * min resident CTAs) */
+  int32_t load_batch;      /* kernel variant: read-region slots a thread loads at once
+                              (0: the pipelined and 26-point kernels) */
 } hydro_plan_info_t;
 
 int hydro_plan_create(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t ghost,

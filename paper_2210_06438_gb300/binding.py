@@ -80,7 +80,8 @@ class PlanInfo(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32), ("tuned_ms", ctypes.c_float),
                 ("n_candidates", ctypes.c_int32), ("lines_per_chunk", ctypes.c_int32),
-                ("prefetch", ctypes.c_int32), ("regs_cap", ctypes.c_int32)]
+                ("prefetch", ctypes.c_int32), ("regs_cap", ctypes.c_int32),
+                ("load_batch", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

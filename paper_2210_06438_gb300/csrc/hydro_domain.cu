@@ -30,11 +30,11 @@ struct Shape {
   int threads, minb, lch;
 };
 // the launch shapes the autotuner picks for the sub-grid batches: binary64
-// 512 threads, mixed the pipelined kernel
-const Shape kShape[2] = {{512, 1, 64}, {hydro_host::kPipeThreads, 1, 64}};
+// 384 threads, mixed the pipelined kernel
+const Shape kShape[2] = {{384, 1, 64}, {hydro_host::kPipeThreads, 1, 64}};
 
 void* domain_func(hydro_precision_t prec) {
-  return prec == HYDRO_FP64 ? (void*)&hydro_dev::rhs_domain_kernel<0, 512, 1>
+  return prec == HYDRO_FP64 ? (void*)&hydro_dev::rhs_domain_kernel<0, 384, 1, 2>
                             : (void*)&hydro_dev::rhs_domain_pipe_kernel<hydro_host::kPipeThreads>;
 }
 

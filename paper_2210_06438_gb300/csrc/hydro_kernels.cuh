@@ -262,8 +262,14 @@ __device__ __forceinline__ bool prim64(const double* u, double gamma, bool g53, 
 // with different rounding than the reference moves results by rounding
 // errors only.
 // One pass along the line keeping a short window of values live (as
-// ppm_line32x2): at step c the slope of cell c, the face c-1/2 and the limited
-// states of cell c-1.  w: the line in shared memory (la addresses it).
+// ppm_line32x2).  The faces enter only through their offsets from the cell
+// values: with dq_c = q_c+1 - q_c,
+//   up_c = q_c+1/2 - q_c = dq_c/2 - (delta_c+1 - delta_c)/6,
+//   dn_c+1 = q_c+1 - q_c+1/2 = dq_c - up_c,
+// and the limited states are q - dn' and q + up' (dn' = 2 up where |dn| > 2|up|,
+// up' = 2 dn where |up| > 2|dn|, both 0 at an extremum).  At step c: the
+// slope of cell c, up of cell c-1, the states of cell c-1, dn of cell c.
+// w: the line in shared memory (la addresses it).
 __device__ __forceinline__ void ppm_line64(const double* w, const LineAddr& la, double* left,
                                            double* right) {
   const double sixth = 1.0 / 6.0;
@@ -273,30 +279,29 @@ __device__ __forceinline__ void ppm_line64(const double* w, const LineAddr& la, 
     return dsame(dp, dm) ? dcopysign(m, dbar) : 0.0;
   };
   double q0 = w[la.at(0)], q1 = w[la.at(1)], q2 = w[la.at(2)];
-  double dm = q2 - q1;
+  double dm = q2 - q1;                   // dq of cell 1
   double del_prev = slope(q1 - q0, dm);  // cell c = 1
-  double face_prev = 0.0;                // face c - 3/2
+  double dn = 0.0;                       // dn of cell c-1
   double qm = q1, qc = q2;               // q[c-1], q[c] for c = 2
 #pragma unroll
   for (int c = 2; c <= LL - 2; c++) {
     double qp = w[la.at(c + 1)];
     double dp = qp - qc;
-    double del = slope(dm, dp);  // slope of cell c
-    double face = fma(del_prev - del, sixth, dhalf(qm + qc));  // between cells c-1 and c
-    if (c >= 3) {  // limit cell c-1 with faces face_prev (left) and face (right)
-      double lo = face_prev, hi = face, q = qm;
-      double up = hi - q, dn = q - lo;
+    double del = slope(dm, dp);                           // slope of cell c
+    double up = fma(del_prev - del, sixth, dhalf(dm));    // up of cell c-1
+    if (c >= 3) {  // states of cell c-1
       bool ext = !dsame(up, dn);
       bool A = dabs_gt(dn, dtwice(up));  // |dn| > 2|up|
       bool B = dabs_gt(up, dtwice(dn));  // |up| > 2|dn| (excludes A)
-      double nv = fma(A ? -2.0 : 2.0, A ? up : dn, q);  // q - 2 up, or q + 2 dn
-      lo = ext ? q : (A ? nv : lo);
-      hi = ext ? q : (B ? nv : hi);
+      double lo = qm - (A ? dtwice(up) : dn);
+      double hi = qm + (B ? dtwice(dn) : up);
+      lo = ext ? qm : lo;
+      hi = ext ? qm : hi;
       int j = c - 4;  // cell index of c-1
       if (j >= 0) right[j] = lo;
       if (j + 1 <= TE) left[j + 1] = hi;
     }
-    face_prev = face;
+    dn = dm - up;  // dn of cell c
     del_prev = del;
     dm = dp;
     qm = qc;
@@ -466,8 +471,8 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // underflows reads as "not the same sign", which changes results by less
 // than those differences).  The parabola limiter in clamp form: with
 // up = q+ - q and dn = q - q- of one sign, q+ = q + 2dn where |up| > 2|dn|
-// and q- = q - 2up where |dn| > 2|up| (CW84 eq. 1.10); faces that are not
-// clamped keep their value exactly; a cell with up dn <= 0 is flattened.
+// and q- = q - 2up where |dn| > 2|up| (CW84 eq. 1.10); a cell with
+// up dn <= 0 is flattened.
 __device__ __forceinline__ float hslope1(float dm, float dp, float s4, float pr) {
   float m = fminf(fminf(fabsf(s4), fabsf(dm)), fabsf(dp));
   return pr > 0.0f ? copysignf(m, s4) : 0.0f;
@@ -483,37 +488,42 @@ __device__ __forceinline__ void limit1(float q, float lo, float hi, float up, fl
   L = ext ? q : (fabsf(dn) > fabsf(uu) ? lc : lo);
   H = ext ? q : (fabsf(up) > fabsf(du) ? hc : hi);
 }
-// One pass along the line keeping a short window of values live: at step c
-// the half slope of cell c, the face c-1/2 and the limited states of cell
-// c-1.  w: the line in shared memory (la addresses it).
+// One pass along the line keeping a short window of values live, in the
+// offset form of ppm_line64 (up = face - q from the half slopes, dn of the next
+// cell = dq - up): at step c the half slope of cell c, up of cell c-1, the
+// states of cell c-1 and dn of cell c.  w: the line in shared memory.
 __device__ __forceinline__ void ppm_line32x2(const float2* w, const LineAddr& la, float2* left,
                                              float2* right) {
   float2 q0 = w[la.at(0)], q1 = w[la.at(1)], q2 = w[la.at(2)];
-  float2 dm = sub2(q2, q1);                  // q2 - q1: the "dm" of cell 2
+  float2 dm = sub2(q2, q1);                      // dq of cell 1
   float2 h_prev = hslope32x2(sub2(q1, q0), dm);  // cell c = 1
-  float2 face_prev = f2(0.0f);               // face c - 3/2
-  float2 qm = q1, qc = q2;                    // q[c-1], q[c] for c = 2
+  float2 dn = f2(0.0f);                          // dn of cell c-1
+  float2 qm = q1, qc = q2;                       // q[c-1], q[c] for c = 2
 #pragma unroll
   for (int c = 2; c <= LL - 2; c++) {
     float2 qp = w[la.at(c + 1)];
     float2 dp = sub2(qp, qc);
     float2 h = hslope32x2(dm, dp);  // half slope of cell c
-    // face between cells c-1 and c
-    float2 face = fma2(sub2(h_prev, h), f2(1.0f / 3.0f), mul2(add2(qm, qc), f2(0.5f)));
-    if (c >= 3) {  // limit cell c-1 with faces face_prev (left) and face (right)
-      float2 lo = face_prev, hi = face, q = qm;
-      float2 up = sub2(hi, q), dn = sub2(q, lo);
+    // up of cell c-1: dq/2 - (h_c - h_c-1)/3
+    float2 up = fma2(sub2(h_prev, h), f2(1.0f / 3.0f), mul2(dm, f2(0.5f)));
+    if (c >= 3) {  // states of cell c-1
       float2 e = mul2(up, dn);
       float2 uu = add2(up, up), du = add2(dn, dn);
-      float2 lc = sub2(q, uu), hc = add2(q, du);
-      float2 L, H;
-      limit1(q.x, lo.x, hi.x, up.x, dn.x, e.x, uu.x, du.x, lc.x, hc.x, L.x, H.x);
-      limit1(q.y, lo.y, hi.y, up.y, dn.y, e.y, uu.y, du.y, lc.y, hc.y, L.y, H.y);
+      float2 a, b;  // the offsets after clamping
+      a.x = fabsf(dn.x) > fabsf(uu.x) ? uu.x : dn.x;
+      a.y = fabsf(dn.y) > fabsf(uu.y) ? uu.y : dn.y;
+      b.x = fabsf(up.x) > fabsf(du.x) ? du.x : up.x;
+      b.y = fabsf(up.y) > fabsf(du.y) ? du.y : up.y;
+      float2 L = sub2(qm, a), H = add2(qm, b);
+      L.x = e.x > 0.0f ? L.x : qm.x;
+      L.y = e.y > 0.0f ? L.y : qm.y;
+      H.x = e.x > 0.0f ? H.x : qm.x;
+      H.y = e.y > 0.0f ? H.y : qm.y;
       int j = c - 4;  // cell index of c-1
       if (j >= 0) right[j] = L;
       if (j + 1 <= TE) left[j + 1] = H;
     }
-    face_prev = face;
+    dn = sub2(dm, up);  // dn of cell c
     h_prev = h;
     dm = dp;
     qm = qc;
@@ -1376,13 +1386,13 @@ struct DomainTiles {
   }
 };
 
-template <int MODE, int NT, int MINB>
+template <int MODE, int NT, int MINB, int KC = (MINB == 1 ? 4 : 2)>
 __global__ void __launch_bounds__(NT, MINB)
 rhs_domain_kernel(DomainTiles dom, int n_tiles, int lch, double* __restrict__ out,
                   double* __restrict__ amax_out, Status* __restrict__ status, double gamma_d,
                   int write_status, int scheme, StageArgs stage) {
-  tile_loop<MODE, NT, MINB == 1 ? 4 : 2, DomainTiles, true>(dom, n_tiles, lch, out, amax_out, status,
-                                                            gamma_d, write_status, 0, scheme == 1, stage);
+  tile_loop<MODE, NT, KC, DomainTiles, true>(dom, n_tiles, lch, out, amax_out, status, gamma_d, write_status,
+                                             0, scheme == 1, stage);
 }
 
 template <int NT>

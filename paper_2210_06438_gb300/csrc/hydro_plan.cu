@@ -260,6 +260,7 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
   p->info.lines_per_chunk = p->cfg.lch;
   p->info.prefetch = p->cfg.prefetch;
   p->info.regs_cap = 65536 / (p->cfg.threads * p->cfg.minb);
+  p->info.load_batch = p->cfg.kc;
   kernel_node(p->cfg, prec, &p->func);
   p->use_graph = !(flags & HYDRO_PLAN_NO_GRAPH);
   *out_plan = p;
