@@ -582,10 +582,13 @@ def run_ours(args, rank, world):
     # ---- serving: Poisson task stream, continuous batching vs one launch per task
     serving = None
     if not args.no_serving:
+        serving_run(args.rate, 0.3, per_task=False)  # warm-up (first use of the pools), not reported
         serving = {
             "aggregated": serving_run(args.rate, args.serve_seconds, per_task=False),
             "per_task": serving_run(args.rate, args.serve_seconds, per_task=True),
+            # at four times the rate the one-launch-per-task form runs out of capacity
             "stress_x4_aggregated": serving_run(4 * args.rate, args.serve_seconds / 2, per_task=False),
+            "stress_x4_per_task": serving_run(4 * args.rate, args.serve_seconds / 2, per_task=True),
         }
 
     # ---- max over ranks
