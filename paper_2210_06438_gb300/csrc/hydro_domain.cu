@@ -59,7 +59,8 @@ int domain_setup(DomDev** out) {
       return hydro_host::cuda_fail(e, "cudaDeviceGetAttribute");
     for (int m = 0; m < 2; m++) {
       hydro_precision_t prec = (hydro_precision_t)m;
-      int smem = hydro_host::smem_bytes(prec, HYDRO_MAX_FIELDS, kShape[m].lch, kShape[m].threads);
+      int smem = hydro_host::smem_bytes(prec, HYDRO_MAX_FIELDS, kShape[m].lch,
+                                        m == 0 ? hydro_host::kKindTiles : hydro_host::kKindPipe);
       if ((e = cudaFuncSetAttribute(domain_func(prec), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     optin - 1024)) != cudaSuccess)
         return hydro_host::cuda_fail(e, "cudaFuncSetAttribute");
@@ -113,7 +114,8 @@ int domain_launch(const double* U, const double* U0, double alpha, double beta, 
   int nt = (int)n_tiles, lch = sh.lch, ws = 1, scheme = (flags & HYDRO_F_KNP) ? 1 : 0;
   long long g64 = (long long)D->occ[prec == HYDRO_FP64 ? 0 : 1] * D->n_sm;
   int grid = (int)(n_tiles < g64 ? n_tiles : g64);
-  size_t smem = (size_t)hydro_host::smem_bytes(prec, F, lch, sh.threads);
+  size_t smem = (size_t)hydro_host::smem_bytes(prec, F, lch,
+                                               prec == HYDRO_FP64 ? hydro_host::kKindTiles : hydro_host::kKindPipe);
   void* args[] = {(void*)&dom, (void*)&nt, (void*)&lch, (void*)&out, (void*)&amax, (void*)&status,
                   (void*)&gamma, (void*)&ws, (void*)&scheme, (void*)&sa};
   if ((e = cudaLaunchKernel(domain_func(prec), dim3(grid), dim3(sh.threads), args, smem, st)) != cudaSuccess)

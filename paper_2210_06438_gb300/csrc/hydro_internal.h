@@ -16,10 +16,16 @@ struct Status;
 
 namespace hydro_host {
 
+// Kernel families: the register-load tile kernels, the pipelined mixed
+// kernel, the 26-point quadrature kernels.
+constexpr int kKindTiles = 0, kKindPipe = 1, kKindQuad = 2;
+constexpr int kPipeThreads = 576;  // threads of the pipelined mixed kernel
+constexpr int kQuadThreads = 192;  // threads of the 26-point quadrature kernels
+
 // Launch shape of the tile kernel.
 struct LaunchCfg {
-  int threads = 256;   // threads per CTA (128, 256, 384 or 512; 576: the pipelined mixed kernel;
-                       // 192: the 26-point kernels)
+  int kind = kKindTiles;
+  int threads = 256;   // threads per CTA
   int minb = 1;        // kernel variant: minimum resident CTAs per SM it was compiled for
   int kc = 4;          // kernel variant: read-region slots per load batch (register-load kernels)
   int lch = 32;        // lines per chunk of the reconstruct/flux phases (16, 32 or 64)
@@ -30,14 +36,11 @@ struct LaunchCfg {
 };
 
 cudaError_t kernels_init(int smem_optin);
-// threads == kPipeThreads selects the pipelined mixed kernel's layout
-int smem_bytes(hydro_precision_t prec, int Fmax, int lch, int threads = 256);
-int occupancy(hydro_precision_t prec, int threads, int minb, int smem, int kc);
+int smem_bytes(hydro_precision_t prec, int Fmax, int lch, int kind = kKindTiles);
+int occupancy(hydro_precision_t prec, const LaunchCfg& c);  // c.smem must be set
 int num_variants();
-void variant(int i, int* threads, int* minb, int* kc);
-bool variant_exists(hydro_precision_t prec, int threads, int minb, int kc);
-constexpr int kPipeThreads = 576;
-constexpr int kQuadThreads = 192;  // the 26-point quadrature kernels
+void variant(int i, LaunchCfg* c);  // sets kind, threads, minb, kc
+bool variant_exists(hydro_precision_t prec, const LaunchCfg& c);
 // pipelined: use the pipelined mixed kernel (ignored for binary64);
 // quad26: the 26-point quadrature kernel (takes precedence)
 LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin, int64_t n_tiles,

@@ -215,19 +215,19 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
       for (int li = 0; li < 3; li++)
       for (int pf = 0; pf < 3; pf += 2) {
         LaunchCfg c;
-        variant(vi, &c.threads, &c.minb, &c.kc);
-        if (!variant_exists(prec, c.threads, c.minb, c.kc)) continue;
-        if ((c.threads == kQuadThreads) != quad26) continue;  // one scheme per plan
+        variant(vi, &c);
+        if (!variant_exists(prec, c)) continue;
+        if ((c.kind == kKindQuad) != quad26) continue;  // one scheme per plan
         if (quad26 && (li != 2 || pf != 0)) continue;
-        const bool pipe = c.threads == kPipeThreads;
+        const bool pipe = c.kind == kKindPipe;
         if (pipe && (li != 2 || pf != 0)) continue;  // chunking and prefetch do not apply
         if (pipe && (flags & HYDRO_PLAN_REGISTER_LOADS)) continue;
         if (!pipe && prec != HYDRO_FP64 && (flags & HYDRO_PLAN_PIPELINED)) continue;
         c.lch = lc[li];
         c.prefetch = pf;
-        c.smem = smem_bytes(prec, p->Fmax, c.lch, c.threads);
+        c.smem = smem_bytes(prec, p->Fmax, c.lch, c.kind);
         if (c.smem > smem_optin) continue;
-        int occ = occupancy(prec, c.threads, c.minb, c.smem, c.kc);
+        int occ = occupancy(prec, c);
         if (occ < 1) continue;
         for (int k = 1; k <= occ; k++) {
           c.ctas_per_sm = k;
