@@ -17,17 +17,22 @@
  *   - Fields, in order: 0 rho, 1-3 momentum (x, y, z), 4 total energy E,
  *     5 entropy tracer tau = (rho e)^(1/gamma), 6.. species densities rho_k.
  *     n_fields = 6 + species, 6 <= n_fields <= HYDRO_MAX_FIELDS.
- *   - Input U of a sub-grid: DEVICE memory, binary64, [n_fields][G][G][G]
- *     with G = N + 2*ghost and x fastest; 8-byte aligned.  Only the 3
- *     innermost ghost layers are read, and of those only the cells with at
- *     most one coordinate outside the interior.  U is never written.
- *   - Output dU/dt: DEVICE memory, binary64, packed in descriptor order:
- *     sub-grid s occupies n_fields_s * N_s^3 doubles ([f][z][y][x]) starting at
- *     sum_{t<s} n_fields_t * N_t^3.  Output amax: DEVICE, one double per
- *     sub-grid.  Both are owned by the caller and fully overwritten.
+ *   - Input U of a sub-grid: binary64, [n_fields][G][G][G] with G = N + 2*ghost
+ *     and x fastest; 8-byte aligned; in memory the GPU can read (device
+ *     memory, or pinned host memory, which the kernels read in place over the
+ *     host link).  Only the 3 innermost ghost layers are read, and of those
+ *     only the cells with at most one coordinate outside the interior (the
+ *     26-point variant, HYDRO_F_QUAD26, also reads cells two deep in a second
+ *     coordinate).  U is never written.
+ *   - Output dU/dt: binary64, packed in descriptor order: sub-grid s occupies
+ *     n_fields_s * N_s^3 doubles ([f][z][y][x]) starting at
+ *     sum_{t<s} n_fields_t * N_t^3.  Output amax: one double per sub-grid.
+ *     Both in device memory or pinned host memory, owned by the caller and
+ *     fully overwritten.
  *   - Streams are cudaStream_t passed as void*; NULL means the legacy default
  *     stream.  Every launch entry point is asynchronous with respect to the
- *     host.  Pointers are plain device pointers (e.g. from torch tensors).
+ *     host.  Pointers are plain addresses in CUDA's unified address space
+ *     (device pointers, e.g. from torch tensors, or pinned host pointers).
  *   - Return value: HYDRO_OK (0) or a negative status below.  No entry point
  *     aborts the process or traps the GPU; device-side problems are recorded
  *     in a per-device status word read back by hydro_status().
