@@ -349,13 +349,13 @@ def sedov_gpu_run(n=64, prec=0, cfl=0.3, t_end=None, dts=None, gamma=5.0 / 3.0, 
     return {"U": U, "t": t, "dts": used, "steps": k, "ms": ev0.elapsed_time(ev1), "n": n, "dx": dx}
 
 
-def sedov_form(n, prec):
+def sedov_form(n, prec, flags=0):
     """One Sedov run at n^3 with its measures against the similarity solution."""
     from tests.sedov_exact import Sedov
     from tests.sedov_run import from_domain, shock_measures
 
     ex = Sedov(5.0 / 3.0)
-    r = sedov_gpu_run(n=n, prec=prec, t_end=ex.time_for_radius(0.35))
+    r = sedov_gpu_run(n=n, prec=prec, t_end=ex.time_for_radius(0.35), flags=flags)
     rho = from_domain(r["U"].cpu().numpy(), n)[0]
     Rp, L1 = shock_measures(rho, r["dx"], ex, r["t"])
     return {"value": 3 * n ** 3 * r["steps"] / (r["ms"] * 1e-3), "unit": "stage cell-updates/s",
@@ -534,7 +534,9 @@ def run_ours(args, rank, world):
     sedov = {}
     if not args.no_sedov:
         sedov = {"sedov_fp64_64": sedov_form(64, hydro.FP64),
-                 "sedov_mixed_64": sedov_form(64, hydro.FP32_FLUX_FP64_ACC)}
+                 "sedov_mixed_64": sedov_form(64, hydro.FP32_FLUX_FP64_ACC),
+                 "sedov_fp64_quad26_64": sedov_form(64, hydro.FP64, hydro.F_QUAD26),
+                 "sedov_mixed_quad26_64": sedov_form(64, hydro.FP32_FLUX_FP64_ACC, hydro.F_QUAD26)}
 
     # ---- end to end through the C ABI with host buffers.  Inputs and outputs
     # live in pinned host memory; the plan's descriptors point there and the
@@ -589,6 +591,9 @@ def run_ours(args, rank, world):
             # at four times the rate the one-launch-per-task form runs out of capacity
             "stress_x4_aggregated": serving_run(4 * args.rate, args.serve_seconds / 2, per_task=False),
             "stress_x4_per_task": serving_run(4 * args.rate, args.serve_seconds / 2, per_task=True),
+            # the mixed precision form at the same rate
+            "aggregated_mixed": serving_run(args.rate, args.serve_seconds, per_task=False, prec=1),
+            "per_task_mixed": serving_run(args.rate, args.serve_seconds, per_task=True, prec=1),
         }
 
     # ---- max over ranks

@@ -267,7 +267,8 @@ int64_t hydro_now_ns(void);
  * (SSP-RK3 of Shu & Osher: (alpha, beta) = (0,1), (3/4,1/4), (1/3,2/3) with
  * U0 the state at the start of the step; the paper's time step has three
  * hydro iterations, Sec. VI-A).  U_out must not alias U; U0 may alias U or
- * U_out.  flags: HYDRO_F_KNP or 0.  Both launch asynchronously on `stream`,
+ * U_out.  flags: HYDRO_F_KNP, HYDRO_F_QUAD26 (the 26-point variant), or 0.
+ * Both launch asynchronously on `stream`,
  * allocate nothing, and record nonphysical input in the hydro_status word. */
 int hydro_domain_rhs(const double* U, int32_t nb, int32_t N, int32_t n_fields, double dx,
                      double gamma, double* out_dUdt, double* out_amax, hydro_precision_t prec,

@@ -19,6 +19,7 @@
 #include "hydro.h"
 #include "hydro_internal.h"
 #include "hydro_kernels.cuh"
+#include "hydro_quad.cuh"
 
 namespace hydro_host {
 int ctx_status_ptr(hydro_dev::Status** st, int* n_sm, int* smem_optin);
@@ -29,18 +30,30 @@ namespace {
 struct Shape {
   int threads, minb, lch;
 };
-// the launch shapes the autotuner picks for the sub-grid batches: binary64
-// 384 threads, mixed the pipelined kernel
-const Shape kShape[2] = {{384, 1, 64}, {hydro_host::kPipeThreads, 1, 64}};
+// the launch shapes the autotuner picks for the sub-grid batches (binary64
+// 384 threads, mixed the pipelined kernel), then the 26-point kernels
+const Shape kShape[4] = {{384, 1, 64},
+                         {hydro_host::kPipeThreads, 1, 64},
+                         {hydro_host::kQuadThreads, 1, 64},
+                         {hydro_host::kQuadThreads, 1, 64}};
+const int kKind[4] = {hydro_host::kKindTiles, hydro_host::kKindPipe, hydro_host::kKindQuad,
+                      hydro_host::kKindQuad};
 
-void* domain_func(hydro_precision_t prec) {
-  return prec == HYDRO_FP64 ? (void*)&hydro_dev::rhs_domain_kernel<0, 384, 1, 2>
-                            : (void*)&hydro_dev::rhs_domain_pipe_kernel<hydro_host::kPipeThreads>;
+// shape index: precision, plus 2 for the 26-point variant
+int shape_of(hydro_precision_t prec, bool quad26) { return (prec == HYDRO_FP64 ? 0 : 1) + (quad26 ? 2 : 0); }
+
+void* domain_func(int k) {
+  switch (k) {
+    case 0: return (void*)&hydro_dev::rhs_domain_kernel<0, 384, 1, 2>;
+    case 1: return (void*)&hydro_dev::rhs_domain_pipe_kernel<hydro_host::kPipeThreads>;
+    case 2: return (void*)&hydro_dev::rhs_domain_quad_kernel<0>;
+    default: return (void*)&hydro_dev::rhs_domain_quad_kernel<1>;
+  }
 }
 
 struct DomDev {
   bool ready = false;
-  int n_sm = 0, occ[2] = {0, 0};
+  int n_sm = 0, occ[4] = {0, 0, 0, 0};
 };
 DomDev g_dom[64];
 std::mutex g_dmu;
@@ -57,17 +70,16 @@ int domain_setup(DomDev** out) {
     if ((e = cudaDeviceGetAttribute(&D.n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
       return hydro_host::cuda_fail(e, "cudaDeviceGetAttribute");
-    for (int m = 0; m < 2; m++) {
-      hydro_precision_t prec = (hydro_precision_t)m;
-      int smem = hydro_host::smem_bytes(prec, HYDRO_MAX_FIELDS, kShape[m].lch,
-                                        m == 0 ? hydro_host::kKindTiles : hydro_host::kKindPipe);
-      if ((e = cudaFuncSetAttribute(domain_func(prec), cudaFuncAttributeMaxDynamicSharedMemorySize,
+    for (int k = 0; k < 4; k++) {
+      hydro_precision_t prec = (k % 2 == 0) ? HYDRO_FP64 : HYDRO_FP32_FLUX_FP64_ACC;
+      int smem = hydro_host::smem_bytes(prec, HYDRO_MAX_FIELDS, kShape[k].lch, kKind[k]);
+      if ((e = cudaFuncSetAttribute(domain_func(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     optin - 1024)) != cudaSuccess)
         return hydro_host::cuda_fail(e, "cudaFuncSetAttribute");
-      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&D.occ[m], domain_func(prec),
-                                                             kShape[m].threads, smem)) != cudaSuccess)
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&D.occ[k], domain_func(k), kShape[k].threads,
+                                                             smem)) != cudaSuccess)
         return hydro_host::cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-      if (D.occ[m] < 1) D.occ[m] = 1;
+      if (D.occ[k] < 1) D.occ[k] = 1;
     }
     D.ready = true;
   }
@@ -110,15 +122,15 @@ int domain_launch(const double* U, const double* U0, double alpha, double beta, 
   bool pow2 = std::frexp(dx, &ex2) == 0.5 && ex2 > -120 && ex2 < 120;
   hydro_dev::DomainTiles dom{U, nb, N, F, tpe, 1.0 / dx, (short)(pow2 ? 2 : 0)};
   hydro_dev::StageArgs sa{U, stage ? U0 : U, alpha, beta, dt, stage};
-  const Shape& sh = kShape[prec == HYDRO_FP64 ? 0 : 1];
+  const int k = shape_of(prec, (flags & HYDRO_F_QUAD26) != 0);
+  const Shape& sh = kShape[k];
   int nt = (int)n_tiles, lch = sh.lch, ws = 1, scheme = (flags & HYDRO_F_KNP) ? 1 : 0;
-  long long g64 = (long long)D->occ[prec == HYDRO_FP64 ? 0 : 1] * D->n_sm;
+  long long g64 = (long long)D->occ[k] * D->n_sm;
   int grid = (int)(n_tiles < g64 ? n_tiles : g64);
-  size_t smem = (size_t)hydro_host::smem_bytes(prec, F, lch,
-                                               prec == HYDRO_FP64 ? hydro_host::kKindTiles : hydro_host::kKindPipe);
+  size_t smem = (size_t)hydro_host::smem_bytes(prec, F, lch, kKind[k]);
   void* args[] = {(void*)&dom, (void*)&nt, (void*)&lch, (void*)&out, (void*)&amax, (void*)&status,
                   (void*)&gamma, (void*)&ws, (void*)&scheme, (void*)&sa};
-  if ((e = cudaLaunchKernel(domain_func(prec), dim3(grid), dim3(sh.threads), args, smem, st)) != cudaSuccess)
+  if ((e = cudaLaunchKernel(domain_func(k), dim3(grid), dim3(sh.threads), args, smem, st)) != cudaSuccess)
     return hydro_host::cuda_fail(e, "launch");
   return HYDRO_OK;
 }

@@ -97,10 +97,15 @@ __device__ __forceinline__ void two_diff1(float a, float b, float& s, float& e) 
   e = (a - (s - bb)) - (b + bb);
 }
 
-template <int MODE, class Fetch>
+// DOMAIN: the tiles belong to a periodic cube of pad[0]^3 sub-grids stored
+// without ghosts (as in tile_loop); `stage` may turn the output into an
+// explicit stage update.
+template <int MODE, class Fetch, bool DOMAIN = false>
 __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, double* __restrict__ out,
                                                double* __restrict__ amax_out, Status* __restrict__ status,
-                                               double gamma_d, int write_status, bool knp) {
+                                               double gamma_d, int write_status, bool knp,
+                                               const StageArgs& stage = StageArgs{nullptr, nullptr, 0.0, 0.0,
+                                                                                  0.0, 0}) {
   typedef typename QuadPrec<MODE>::R R;
   typedef typename QuadPrec<MODE>::Acc Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -117,9 +122,20 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
     const Tile tile = fetch(t);
     const int F = tile.F, N = tile.N, G = tile.G, gh = (G - N) >> 1, nsp = F - 6;
     const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
-    const long long plane = (long long)G * G * G;
+    const long long plane = DOMAIN ? (long long)N * N * N : (long long)G * G * G;  // field stride
+    // offset (within one field) of tile cell (x, y, z); in a domain the cell is
+    // located by its periodic global coordinates
     auto off_of = [&](int x, int y, int z) {
-      return ((tile.oz + z + gh) * G + (tile.oy + y + gh)) * G + (tile.ox + x + gh);
+      if constexpr (DOMAIN) {
+        const int nb = tile.pad[0], L = nb * N, sb = tile.sub;
+        const int gx = ((sb % nb) * N + tile.ox + x + L) % L;
+        const int gy = (((sb / nb) % nb) * N + tile.oy + y + L) % L;
+        const int gz = ((sb / (nb * nb)) * N + tile.oz + z + L) % L;
+        const int blk = ((gz / N) * nb + gy / N) * nb + gx / N;
+        return blk * F * N * N * N + ((gz % N) * N + gy % N) * N + gx % N;
+      } else {
+        return ((tile.oz + z + gh) * G + (tile.oy + y + gh)) * G + (tile.ox + x + gh);
+      }
     };
 
     // ---- A0/A1: hydro primitives of the read region
@@ -215,7 +231,23 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
             R ql[5], qr[5], lo, hi;
 #pragma unroll
             for (int m = 0; m < 5; m++) {
-              const double ul = __ldg(base + gl0 + (m - 2) * gsl), ur = __ldg(base + gr0 + (m - 2) * gsr);
+              int ol, orr;
+              if constexpr (DOMAIN) {
+                // tile coordinates of the stencil cells (axis d, then a, b)
+                const int cd = i - 1, vd = 1;
+                const int lx = d == 0 ? cd + (m - 2) * vd : ca + (m - 2) * o1;
+                const int ly = d == 1 ? cd + (m - 2) * vd : (d == 0 ? ca + (m - 2) * o1 : cb + (m - 2) * o2);
+                const int lz = d == 2 ? cd + (m - 2) * vd : cb + (m - 2) * o2;
+                const int rx = d == 0 ? cd + 1 + (m - 2) * vd : ca - (m - 2) * o1;
+                const int ry = d == 1 ? cd + 1 + (m - 2) * vd : (d == 0 ? ca - (m - 2) * o1 : cb - (m - 2) * o2);
+                const int rz = d == 2 ? cd + 1 + (m - 2) * vd : cb - (m - 2) * o2;
+                ol = off_of(lx, ly, lz);
+                orr = off_of(rx, ry, rz);
+              } else {
+                ol = gl0 + (m - 2) * gsl;
+                orr = gr0 + (m - 2) * gsr;
+              }
+              const double ul = __ldg(base + ol), ur = __ldg(base + orr);
               const R rl = RR[il + (m - 2) * sl], rr = RR[ir + (m - 2) * sr];
               if constexpr (MODE == 0) {
                 ql[m] = ul * rl;
@@ -320,6 +352,12 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
               double v;
               if constexpr (MODE == 0) v = acc[k][f] * scale;
               else v = pair_value(acc[k][f].h, acc[k][f].l, scale, sf, pow2);
+              if constexpr (DOMAIN) {
+                if (stage.on) {
+                  long long e = (o - out) + f * n3;  // same index in U, U0 and out
+                  v = fma(stage.alpha, __ldg(stage.U0 + e), stage.beta * fma(stage.dt, v, __ldg(stage.U + e)));
+                }
+              }
               o[f * n3] = v;
             }
         }
@@ -357,6 +395,17 @@ rhs_quad_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch, 
   (void)lch;
   (void)prefetch;
   tile_loop_quad<MODE>(TileList{tiles}, n_tiles, out, amax_out, status, gamma_d, write_status, scheme == 1);
+}
+
+// The 26-point variant of the domain form (rhs_domain_kernel's arguments).
+template <int MODE>
+__global__ void __launch_bounds__(QNT, MODE == 0 ? 1 : 2)
+rhs_domain_quad_kernel(DomainTiles dom, int n_tiles, int lch, double* __restrict__ out,
+                       double* __restrict__ amax_out, Status* __restrict__ status, double gamma_d,
+                       int write_status, int scheme, StageArgs stage) {
+  (void)lch;
+  tile_loop_quad<MODE, DomainTiles, true>(dom, n_tiles, out, amax_out, status, gamma_d, write_status,
+                                          scheme == 1, stage);
 }
 
 }  // namespace hydro_dev

@@ -116,3 +116,53 @@ def test_domain_argument_checks():
         hydro.domain_rhs(U, 2, 8, 6, 0.1, U, am)  # output aliases input
     with pytest.raises(hydro.HydroError):
         hydro.domain_rhs(U, 2, 8, 5, 0.1, torch.empty_like(U), am)
+
+
+@pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
+def test_domain_with_the_one_sided_flux(prec):
+    """HYDRO_F_KNP in the domain form against the oracle's KNP mode on the
+    gathered sub-grids."""
+    n, N = 16, 8
+    glob = synth.plain_domain(seed=29, n=n, nf=11)
+    dom, nb = domain_layout(glob, N)
+    dx = 1.0 / n
+    U = torch.from_numpy(dom).cuda()
+    out = torch.empty_like(U)
+    am = torch.empty(nb ** 3, dtype=torch.float64, device="cuda")
+    hydro.domain_rhs(U, nb, N, 11, dx, out, am, prec=prec, flags=hydro.F_KNP)
+    torch.cuda.synchronize()
+    blocks = list(synth.gather_blocks(glob, N))
+    mode = oracle.FLUX_KNP + (0 if prec == hydro.FP64 else 1)
+    ref, ram, _ = gh.oracle_ref(blocks, [dx] * len(blocks), mode=mode)
+    got = [o for o in out.cpu().numpy()]
+    if prec == hydro.FP64:
+        gh.check_fp64(got, ref, am.cpu().numpy(), ram, blocks, [dx] * len(blocks))
+    else:
+        gh.check_mixed(got, ref, am.cpu().numpy(), ram, blocks, [dx] * len(blocks))
+
+
+@pytest.mark.parametrize("N,n", [(8, 16), (12, 24)])
+@pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
+def test_domain_with_the_26_point_variant(N, n, prec):
+    """HYDRO_F_QUAD26 in the domain form gives the bits of the ghosted entry
+    point on the gathered sub-grids (which the oracle pins separately); the
+    fused stage applies on top of it."""
+    glob = synth.plain_domain(seed=31, n=n, nf=9)
+    dom, nb = domain_layout(glob, N)
+    dx = 1.0 / n
+    U = torch.from_numpy(dom).cuda()
+    out = torch.empty_like(U)
+    am = torch.empty(nb ** 3, dtype=torch.float64, device="cuda")
+    hydro.domain_rhs(U, nb, N, 9, dx, out, am, prec=prec, flags=hydro.F_QUAD26)
+    torch.cuda.synchronize()
+    blocks = list(synth.gather_blocks(glob, N))
+    g, gam = gh.run_gpu(gh.to_dev(blocks), [dx] * len(blocks), prec=prec, flags=hydro.F_QUAD26)
+    for a, b in zip(out.cpu().numpy(), g):
+        assert np.array_equal(a, b)
+    assert np.array_equal(am.cpu().numpy(), gam)
+    st = torch.empty_like(U)
+    hydro.domain_stage(U, U, 0.0, 1.0, 1e-3, nb, N, 9, dx, st, am, prec=prec, flags=hydro.F_QUAD26)
+    torch.cuda.synchronize()
+    ref = U + 1e-3 * out
+    err = (st - ref).abs().amax(dim=(0, 2, 3, 4)) / ref.abs().amax(dim=(0, 2, 3, 4))
+    assert float(err.max()) <= 4e-16

@@ -60,3 +60,21 @@ def test_sedov_converges_to_the_similarity_solution(exact):
         assert abs(Rp - exact.shock_radius(r["t"])) <= 1.0 / n, (n, Rp)
         assert rho.min() > 0
     assert L1[64] < 0.8 * L1[32] and L1[128] < 0.8 * L1[64], L1
+
+
+def test_sedov_with_the_26_point_variant(exact):
+    """The paper's scheme on the paper's scenario: the binary64 26-point run
+    follows the oracle's QUAD26 trajectory at 16^3 and puts the shock within a
+    cell of R(t) at 32^3, spherically symmetric."""
+    import oracle
+
+    t_end = exact.time_for_radius(0.35)
+    U_ora, t, dts = oracle_run(16, t_end, mode=oracle.QUAD26)
+    r = sedov_gpu_run(n=16, prec=hydro.FP64, dts=dts, flags=hydro.F_QUAD26)
+    U = from_domain(r["U"].cpu().numpy(), 16)
+    assert _normwise(U, U_ora) < 1e-9
+    r = sedov_gpu_run(n=32, prec=hydro.FP64, t_end=t_end, flags=hydro.F_QUAD26)
+    rho = from_domain(r["U"].cpu().numpy(), 32)[0]
+    Rp, L1 = shock_measures(rho, 1.0 / 32, exact, r["t"])
+    assert abs(Rp - exact.shock_radius(r["t"])) <= 1.0 / 32
+    assert np.abs(rho - rho.transpose(1, 2, 0)).max() < 1e-10 * rho.max()
