@@ -132,13 +132,22 @@ def test_mixed_kernel_families_agree_bitwise():
         assert np.array_equal(oam, aam)
 
 
-def test_wider_ghost_layer_is_ignored_beyond_three():
+@pytest.mark.parametrize("prec,flags", [(hydro.FP64, 0), (hydro.FP64, hydro.F_QUAD26),
+                                        (hydro.FP32_FLUX_FP64_ACC, 0),
+                                        (hydro.FP32_FLUX_FP64_ACC, hydro.F_REGISTER_LOADS)])
+def test_wider_ghost_layer_is_ignored_beyond_three(prec, flags):
     U4 = synth.iid_block(synth.rng_for(8, 0), 8, 7, ghost=4)
     U4[:, 0, :, :] = np.nan  # the 4th layer is never read
+    U4[:, :, -1, :] = np.nan
     dev = gh.to_dev([U4])
-    got, gam = gh.run_gpu(dev, [0.1], ghost=4)
-    ref, ram, _ = oracle.rhs_batch([U4[:, 1:-1, 1:-1, 1:-1].copy()], G53, 0.1, 0)
-    gh.check_fp64(got, ref, gam, ram, [U4[:, 1:-1, 1:-1, 1:-1]], [0.1])
+    got, gam = gh.run_gpu(dev, [0.1], ghost=4, prec=prec, flags=flags)
+    U3 = U4[:, 1:-1, 1:-1, 1:-1].copy()
+    mode = (0 if prec == hydro.FP64 else oracle.MODE_MIXED) + (oracle.QUAD26 if flags & hydro.F_QUAD26 else 0)
+    ref, ram, _ = oracle.rhs_batch([U3], G53, 0.1, mode)
+    if prec == hydro.FP64:
+        gh.check_fp64(got, ref, gam, ram, [U3], [0.1])
+    else:
+        gh.check_mixed(got, ref, gam, ram, [U3], [0.1])
 
 
 def test_every_field_count():
