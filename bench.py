@@ -208,15 +208,27 @@ def max_over_ranks(values, world, device="cuda"):
     return [float(x) for x in t.cpu()]
 
 
+def kernel_source_digest(path):
+    """sha256 of a CUDA source with // comments and blank lines removed (so
+    that the record follows code changes, not comment edits)."""
+    import hashlib
+    import re
+
+    lines = []
+    for line in open(path, encoding="utf-8"):
+        line = re.sub(r"//.*", "", line).rstrip()
+        if line:
+            lines.append(line)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def recorded_traffic(form, n_tiles):
     """DRAM bytes of one launch from the committed ncu record, scaled to
-    n_tiles; None unless the kernel source still matches the record."""
-    import hashlib
-
+    n_tiles; None unless the kernel source's code still matches the record."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
         src = os.path.join(ROOT, "paper_2210_06438_gb300", "csrc", "hydro_kernels.cuh")
-        if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["kernel_source_sha256"]:
+        if kernel_source_digest(src) != rec["kernel_code_sha256"]:
             return None
         return rec["forms"][form]["bytes_per_tile"] * n_tiles
     except Exception:

@@ -9,7 +9,7 @@
 // turned around: the GPU always sees 8^3 work items, whatever the sub-grid
 // size, and many of them per launch (the aggregated kernel of Sec. V-D).
 //
-// Per tile, one CTA:
+// Per tile, one CTA (the register-load kernels, tile_loop):
 //   1. stage the tile's read region (interior rows with their x ghosts, plus
 //      the y and z ghost slabs: 1664 cells) from HBM, converting to primitive
 //      variables on the way into shared memory                    (steps A0-A1)
@@ -20,6 +20,9 @@
 //      x, then y, then z in registers (step A4); the result is scaled by
 //      -1/dx and stored.  The largest signal speed is reduced with warp
 //      shuffles and one atomic per tile (step A5).
+// The pipelined mixed kernel (tile_loop_pipe, further down) moves the read
+// region by asynchronous copies one field group ahead and reconstructs the
+// three directions together; the 26-point variant lives in hydro_quad.cuh.
 //
 // MODE 0 runs every step in binary64.  On this GPU the binary64 pipe issues
 // about 2 operations per SM per clock (1/64 of binary32), so the binary64 form
