@@ -31,8 +31,8 @@ struct Shape {
   int threads, minb, lch;
 };
 // the launch shapes the autotuner picks for the sub-grid batches (binary64
-// 384 threads, mixed the pipelined kernel), then the 26-point kernels
-const Shape kShape[4] = {{384, 1, 64},
+// 576 threads, mixed the pipelined kernel), then the 26-point kernels
+const Shape kShape[4] = {{576, 1, 64},
                          {hydro_host::kPipeThreads, 1, 64},
                          {hydro_host::kQuadThreads, 1, 64},
                          {hydro_host::kQuadThreads, 1, 64}};
@@ -44,7 +44,7 @@ int shape_of(hydro_precision_t prec, bool quad26) { return (prec == HYDRO_FP64 ?
 
 void* domain_func(int k) {
   switch (k) {
-    case 0: return (void*)&hydro_dev::rhs_domain_kernel<0, 384, 1, 2>;
+    case 0: return (void*)&hydro_dev::rhs_domain_kernel<0, 576, 1, 1>;
     case 1: return (void*)&hydro_dev::rhs_domain_pipe_kernel<hydro_host::kPipeThreads>;
     case 2: return (void*)&hydro_dev::rhs_domain_quad_kernel<0>;
     default: return (void*)&hydro_dev::rhs_domain_quad_kernel<1>;

@@ -18,7 +18,8 @@ struct Variant {
 static const Variant kVariants[] = {
     {kKindTiles, 256, 1, 4}, {kKindTiles, 128, 1, 4}, {kKindTiles, 512, 1, 4}, {kKindTiles, 512, 1, 2},
     {kKindTiles, 384, 1, 4}, {kKindTiles, 384, 1, 2}, {kKindTiles, 192, 1, 4}, {kKindTiles, 256, 2, 2},
-    {kKindTiles, 128, 2, 2}, {kKindPipe, kPipeThreads, 1, 0}, {kKindQuad, kQuadThreads, 1, 0}};
+    {kKindTiles, 128, 2, 2}, {kKindTiles, 448, 1, 2}, {kKindTiles, 576, 1, 1},
+    {kKindPipe, kPipeThreads, 1, 0}, {kKindQuad, kQuadThreads, 1, 0}};
 static constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 static_assert(kPipeThreads == hydro_dev::PNT, "pipelined kernel block size");
 static_assert(kQuadThreads == hydro_dev::QNT, "26-point kernel block size");
@@ -34,8 +35,12 @@ static void* kfunc(const LaunchCfg& c) {
       return (void*)&rhs_tiles_kernel<MODE, 192, 1, 4>;
     case 384:
       return c.kc == 2 ? (void*)&rhs_tiles_kernel<MODE, 384, 1, 2> : (void*)&rhs_tiles_kernel<MODE, 384, 1, 4>;
+    case 448:
+      return (void*)&rhs_tiles_kernel<MODE, 448, 1, 2>;
     case 512:
       return c.kc == 2 ? (void*)&rhs_tiles_kernel<MODE, 512, 1, 2> : (void*)&rhs_tiles_kernel<MODE, 512, 1, 4>;
+    case 576:
+      return (void*)&rhs_tiles_kernel<MODE, 576, 1, 1>;
     default:
       return c.minb == 2 ? (void*)&rhs_tiles_kernel<MODE, 256, 2, 2> : (void*)&rhs_tiles_kernel<MODE, 256, 1, 4>;
   }
