@@ -34,6 +34,7 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 GAMMA = 5.0 / 3.0
+METRIC = "cell-updates/s (aggregated FP64 hydro RHS: PPM + Kurganov-Tadmor)"
 WORKLOAD = "polytropes: 32768 sub-grids of 8^3 + 3 ghost layers (256^3 cells), 11 FP64 fields"
 
 
@@ -405,25 +406,27 @@ def run_reference(args, rank, world):
 
     oracle.build()
     n_sample = args.ref_sample
-    glob = synth.polytropes(n=128, nf=11)  # same recipe, smaller domain for the sample
-    idx = np.linspace(0, (128 // 8) ** 3 - 1, n_sample).astype(int)
-    nb = 128 // 8
+    n = args.domain
+    glob = synth.polytropes(n=n, nf=11)  # the workload itself; a sample of its sub-grids per step
+    nb = n // 8
+    idx = np.linspace(0, nb ** 3 - 1, n_sample).astype(int)
     blocks = list(synth.gather_blocks(glob, 8, blocks=[(i % nb, (i // nb) % nb, i // (nb * nb)) for i in idx]))
+    del glob
     threads = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle.rhs_batch(blocks, GAMMA, 2.0 / 128, 0, threads=threads)
+        oracle.rhs_batch(blocks, GAMMA, 2.0 / n, 0, threads=threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.rhs_batch(blocks, GAMMA, 2.0 / 128, 0, threads=threads)
+        oracle.rhs_batch(blocks, GAMMA, 2.0 / n, 0, threads=threads)
     el = time.perf_counter() - t0
     cells = n_sample * 512
     value = cells * args.steps / el
     line = {
-        "impl": "reference", "metric": "cell-updates/s (FP64 hydro RHS)", "value": value,
+        "impl": "reference", "metric": METRIC, "value": value,
         "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "%d sub-grids of the polytrope recipe per step"
+        "config": {"workload": WORKLOAD, "sample": "%d evenly spaced sub-grids of the workload per step"
                    % n_sample},
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads,
                          "kind": "oracle",
@@ -648,7 +651,7 @@ def run_ours(args, rank, world):
 
     value = cells * world / (ms64 * 1e-3)
     line = {
-        "metric": "cell-updates/s (aggregated FP64 hydro RHS: PPM + Kurganov-Tadmor)",
+        "metric": METRIC,
         "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
