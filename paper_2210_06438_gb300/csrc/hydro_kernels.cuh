@@ -138,6 +138,49 @@ __device__ __forceinline__ LineAddr line_addr(int d, int l) {
           TE * TE, TE * LL};
 }
 
+// --------------------------------------------------- periodic domains --
+// Position of a domain tile's sub-grid in a periodic cube of nb^3 sub-grids
+// of N^3 cells stored without ghosts ([s][f][N^3], s = bx + nb (by + nb bz)),
+// computed once per tile.  off() locates a cell given by coordinates within
+// the sub-grid that may lie outside [0, N): a read-region cell is at most 3
+// cells outside its tile, so for N >= 3 it lies in the sub-grid or in a direct
+// neighbour (one compare and step per axis, wrapping around the cube); for
+// N < 3 the periodic global coordinates are reduced with divisions.
+struct DomainPos {
+  int bx, by, bz, nb, N, bsz;  // bsz: doubles per stored sub-grid (F N^3)
+  __device__ __forceinline__ void init(int sub, int nb_, int N_, int F) {
+    nb = nb_;
+    N = N_;
+    bsz = F * N * N * N;
+    bx = sub % nb;
+    by = (sub / nb) % nb;
+    bz = sub / (nb * nb);
+  }
+  __device__ __forceinline__ void step(int& c, int& b) const {
+    if (c < 0) {
+      c += N;
+      b = b == 0 ? nb - 1 : b - 1;
+    } else if (c >= N) {
+      c -= N;
+      b = b == nb - 1 ? 0 : b + 1;
+    }
+  }
+  __device__ __forceinline__ int off(int cx, int cy, int cz) const {
+    int ax = bx, ay = by, az = bz;
+    if (N >= 3) {
+      step(cx, ax);
+      step(cy, ay);
+      step(cz, az);
+    } else {
+      const int L = nb * N;
+      const int gx = (bx * N + cx + L) % L, gy = (by * N + cy + L) % L, gz = (bz * N + cz + L) % L;
+      ax = gx / N, ay = gy / N, az = gz / N;
+      cx = gx % N, cy = gy % N, cz = gz % N;
+    }
+    return ((az * nb + ay) * nb + ax) * bsz + (cz * N + cy) * N + cx;
+  }
+};
+
 // ============================================= binary64 on the integer pipe ==
 // Bit-pattern helpers.  They are exact for zero and for normal numbers of
 // magnitude >= 2^-1021 (far below any value a hydro state produces); the
@@ -892,7 +935,8 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
     const int F = tile.F, G = tile.G, N = tile.N, gh = (tile.G - tile.N) >> 1;
     const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
     const long long plane = DOMAIN ? (long long)N * N * N : (long long)G * G * G;  // field stride
-    const int nb = DOMAIN ? tile.pad[0] : 0;
+    DomainPos dp;
+    if constexpr (DOMAIN) dp.init(tile.sub, tile.pad[0], N, F);
 
     // offset of read-region slot s within a field of the stored block; -1 if
     // the slot is outside the (possibly partial) tile's read region: at most
@@ -905,12 +949,7 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
       bool valid = s < STAR && outside <= 1 && x < ex + 3 && y < ey + 3 && z < ez + 3;
       if (!valid) return -1;
       if constexpr (DOMAIN) {
-        const int L = nb * N, sb = tile.sub;
-        int gx = ((sb % nb) * N + tile.ox + x + L) % L;
-        int gy = (((sb / nb) % nb) * N + tile.oy + y + L) % L;
-        int gz = ((sb / (nb * nb)) * N + tile.oz + z + L) % L;
-        int blk = ((gz / N) * nb + gy / N) * nb + gx / N;
-        return blk * F * N * N * N + ((gz % N) * N + gy % N) * N + gx % N;
+        return dp.off(tile.ox + x, tile.oy + y, tile.oz + z);
       } else {
         return ((tile.oz + z + gh) * G + (tile.oy + y + gh)) * G + (tile.ox + x + gh);
       }
@@ -1109,16 +1148,12 @@ __device__ __forceinline__ bool pipe_valid(int x, int y, int z, int ex, int ey, 
   return outside <= 1 && x < ex + 3 && y < ey + 3 && z < ez + 3;
 }
 template <bool DOMAIN>
-__device__ __forceinline__ int pipe_offset(const Tile& tile, int x, int y, int z, int ex, int ey, int ez) {
+__device__ __forceinline__ int pipe_offset(const Tile& tile, const DomainPos& dp, int x, int y, int z, int ex,
+                                           int ey, int ez) {
   if (!pipe_valid(x, y, z, ex, ey, ez)) return -1;
   const int N = tile.N;
   if constexpr (DOMAIN) {
-    const int nb = tile.pad[0], L = nb * N, sb = tile.sub;
-    int gx = ((sb % nb) * N + tile.ox + x + L) % L;
-    int gy = (((sb / nb) % nb) * N + tile.oy + y + L) % L;
-    int gz = ((sb / (nb * nb)) * N + tile.oz + z + L) % L;
-    int blk = ((gz / N) * nb + gy / N) * nb + gx / N;
-    return blk * tile.F * N * N * N + ((gz % N) * N + gy % N) * N + gx % N;
+    return dp.off(tile.ox + x, tile.oy + y, tile.oz + z);
   } else {
     const int G = tile.G, gh = (G - N) >> 1;
     return ((tile.oz + z + gh) * G + (tile.oy + y + gh)) * G + (tile.ox + x + gh);
@@ -1131,6 +1166,8 @@ __device__ __forceinline__ void pipe_issue(const Tile& tile, const SlotXYZ& sx, 
   const int N = tile.N;
   const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
   const long long plane = DOMAIN ? (long long)N * N * N : (long long)tile.G * tile.G * tile.G;
+  DomainPos dp;
+  if constexpr (DOMAIN) dp.init(tile.sub, tile.pad[0], N, tile.F);
   const int tid = threadIdx.x;
 #pragma unroll
   for (int k = 0; k < PSPT; k++) {
@@ -1138,7 +1175,7 @@ __device__ __forceinline__ void pipe_issue(const Tile& tile, const SlotXYZ& sx, 
     if (s >= STAR) continue;
     int x, y, z;
     sx.get(k, x, y, z);
-    int off = pipe_offset<DOMAIN>(tile, x, y, z, ex, ey, ez);
+    int off = pipe_offset<DOMAIN>(tile, dp, x, y, z, ex, ey, ez);
     if (off < 0) continue;
     const double* src = tile.U + (long long)f0 * plane + off;
 #pragma unroll

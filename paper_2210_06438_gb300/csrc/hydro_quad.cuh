@@ -125,14 +125,11 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
     const long long plane = DOMAIN ? (long long)N * N * N : (long long)G * G * G;  // field stride
     // offset (within one field) of tile cell (x, y, z); in a domain the cell is
     // located by its periodic global coordinates
+    DomainPos dp;
+    if constexpr (DOMAIN) dp.init(tile.sub, tile.pad[0], N, F);
     auto off_of = [&](int x, int y, int z) {
       if constexpr (DOMAIN) {
-        const int nb = tile.pad[0], L = nb * N, sb = tile.sub;
-        const int gx = ((sb % nb) * N + tile.ox + x + L) % L;
-        const int gy = (((sb / nb) % nb) * N + tile.oy + y + L) % L;
-        const int gz = ((sb / (nb * nb)) * N + tile.oz + z + L) % L;
-        const int blk = ((gz / N) * nb + gy / N) * nb + gx / N;
-        return blk * F * N * N * N + ((gz % N) * N + gy % N) * N + gx % N;
+        return dp.off(tile.ox + x, tile.oy + y, tile.oz + z);
       } else {
         return ((tile.oz + z + gh) * G + (tile.oy + y + gh)) * G + (tile.ox + x + gh);
       }

@@ -30,7 +30,7 @@ def from_domain(arr, nb, N):
     return np.ascontiguousarray(a.reshape(nf, nb * N, nb * N, nb * N))
 
 
-@pytest.mark.parametrize("N,n", [(8, 32), (16, 32), (12, 24)])
+@pytest.mark.parametrize("N,n", [(8, 32), (16, 32), (12, 24), (3, 9), (2, 6), (8, 8)])
 @pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
 def test_domain_rhs_matches_the_ghosted_subgrids(N, n, prec):
     glob = synth.plain_domain(seed=17, n=n, nf=11)
