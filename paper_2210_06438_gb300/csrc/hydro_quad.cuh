@@ -42,26 +42,29 @@ __host__ __device__ constexpr size_t quad_smem_bytes() {
 __device__ __forceinline__ int qidx(int x, int y, int z) { return ((z + 3) * LL + (y + 3)) * LL + (x + 3); }
 
 // PPM face values of the middle cell of five line values q[0..4] (cells
-// -2..2), the same steps as ppm_line64 for one cell.
+// -2..2), in the offset form of ppm_line64: up = dq_0/2 - (delta_1 -
+// delta_0)/6 and dn = dq_-1 - up_-1 (subscripts relative to the middle cell).
 __device__ __forceinline__ void ppm5_64(const double* q, double& lo, double& hi) {
+  const double sixth = 1.0 / 6.0;
+  double dq[4];
+#pragma unroll
+  for (int c = 0; c < 4; c++) dq[c] = q[c + 1] - q[c];
   double del[3];
 #pragma unroll
-  for (int c = 1; c <= 3; c++) {
-    double dp = q[c + 1] - q[c], dm = q[c] - q[c - 1];
-    double dbar = dhalf(q[c + 1] - q[c - 1]);
+  for (int c = 0; c < 3; c++) {  // cells -1, 0, 1
+    const double dm = dq[c], dp = dq[c + 1];
+    double dbar = dhalf(dp + dm);
     double m = dminp(dabs(dbar), dtwice(dminp(dabs(dm), dabs(dp))));
-    del[c - 1] = dsame(dp, dm) ? dcopysign(m, dbar) : 0.0;
+    del[c] = dsame(dp, dm) ? dcopysign(m, dbar) : 0.0;
   }
-  const double sixth = 1.0 / 6.0;
   const double qc = q[2];
-  double l = fma(del[0] - del[1], sixth, dhalf(q[1] + q[2]));
-  double h = fma(del[1] - del[2], sixth, dhalf(q[2] + q[3]));
-  double up = h - qc, dn = qc - l;
+  const double upm = fma(del[0] - del[1], sixth, dhalf(dq[1]));  // up of cell -1
+  const double up = fma(del[1] - del[2], sixth, dhalf(dq[2]));   // up of the middle cell
+  const double dn = dq[1] - upm;
   bool ext = !dsame(up, dn);
   bool A = dabs_gt(dn, dtwice(up)), B = dabs_gt(up, dtwice(dn));
-  double nv = fma(A ? -2.0 : 2.0, A ? up : dn, qc);
-  lo = ext ? qc : (A ? nv : l);
-  hi = ext ? qc : (B ? nv : h);
+  lo = ext ? qc : qc - (A ? dtwice(up) : dn);
+  hi = ext ? qc : qc + (B ? dtwice(dn) : up);
 }
 
 // The same for binary32, in ppm_line32x2's half-slope and clamp form.
