@@ -489,23 +489,38 @@ def run_ours(args, rank, world):
     # ---- per-sub-grid launch form (strategy-2 analogue), 128-stream pool
     pool = [torch.cuda.Stream(device=dev) for _ in range(args.streams)]
 
-    def per_sub(prec):
-        hydro.rhs_per_subgrid(batch.desc, out, amax, pool, ghost=3, gamma=GAMMA, prec=prec,
+    def per_sub(prec, streams):
+        hydro.rhs_per_subgrid(batch.desc, out, amax, streams, ghost=3, gamma=GAMMA, prec=prec,
                               n=batch.n)
 
-    def timed_pool(prec, steps):
+    def timed_pool(prec, steps, streams=pool):
         for _ in range(1):
-            per_sub(prec)
+            per_sub(prec, streams)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(steps):
-            per_sub(prec)
+            per_sub(prec, streams)
         torch.cuda.synchronize()
         return (time.perf_counter() - t0) / steps * 1e3
 
     ps_steps = max(1, min(args.steps, 3))
     ms_ps64 = timed_pool(hydro.FP64, ps_steps)
     ms_psmx = timed_pool(hydro.FP32_FLUX_FP64_ACC, ps_steps)
+    # the stream-pool sweep of the per-sub-grid form (binary64)
+    ps_sweep = {str(k): timed_pool(hydro.FP64, 1, pool[:k]) for k in (1, 4, 16) if k <= len(pool)}
+    ps_sweep[str(len(pool))] = ms_ps64
+
+    # ---- per-replay distribution of the headline plan (CUDA events around each replay)
+    reps = []
+    for _ in range(30):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan64.execute(out, amax, stream)
+        e1.record(stream)
+        e1.synchronize()
+        reps.append(e0.elapsed_time(e1))
+    rep_pct = {"p10": float(np.percentile(reps, 10)), "p50": float(np.percentile(reps, 50)),
+               "p90": float(np.percentile(reps, 90)), "replays": len(reps)}
 
     # ---- domain form: the same cells stored without ghosts, ghost shells
     # gathered in the kernel; and one SSP-RK3 step of three fused stages
@@ -669,12 +684,14 @@ def run_ours(args, rank, world):
         "gpu_launches": args.steps,
         "roofline": roof,
         "forms": {
-            "fp64_aggregated": {"value": value, "ms": ms64, "conservation_drift": drift64},
+            "fp64_aggregated": {"value": value, "ms": ms64, "conservation_drift": drift64,
+                                "replay_ms": rep_pct},
             "mixed_aggregated": {"value": cells * world / (msmx * 1e-3), "ms": msmx,
                                  "roofline": mixed_roof, "max_rel_err_vs_fp64": mixed_err,
                                  "conservation_drift": drift},
             "fp64_per_subgrid": {"value": cells * world / (ms_ps64 * 1e-3), "ms": ms_ps64,
-                                 "streams": args.streams, "launches": batch.n},
+                                 "streams": args.streams, "launches": batch.n,
+                                 "ms_by_streams": ps_sweep},
             "fp64_domain": {"value": cells * world / (ms_dom64 * 1e-3), "ms": ms_dom64,
                             "note": "ghost shells gathered in the kernel from ghost-free storage"},
             "mixed_domain": {"value": cells * world / (ms_dommx * 1e-3), "ms": ms_dommx,
