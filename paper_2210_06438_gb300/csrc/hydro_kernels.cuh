@@ -519,6 +519,12 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // up = q+ - q and dn = q - q- of one sign, q+ = q + 2dn where |up| > 2|dn|
 // and q- = q - 2up where |dn| > 2|up| (CW84 eq. 1.10); a cell with
 // up dn <= 0 is flattened.
+// min(|a|, |b|) with the sign of a (min.xorsign.abs with |b|)
+__device__ __forceinline__ float min_signed(float a, float b) {
+  float r;
+  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(fabsf(b)));
+  return r;
+}
 __device__ __forceinline__ float hslope1(float dm, float dp, float s4, float pr) {
   float m = fminf(fminf(fabsf(s4), fabsf(dm)), fabsf(dp));
   return pr > 0.0f ? copysignf(m, s4) : 0.0f;
@@ -555,11 +561,14 @@ __device__ __forceinline__ void ppm_line32x2(const float2* w, const LineAddr& la
     if (c >= 3) {  // states of cell c-1
       float2 e = mul2(up, dn);
       float2 uu = add2(up, up), du = add2(dn, dn);
-      float2 a, b;  // the offsets after clamping
-      a.x = fabsf(dn.x) > fabsf(uu.x) ? uu.x : dn.x;
-      a.y = fabsf(dn.y) > fabsf(uu.y) ? uu.y : dn.y;
-      b.x = fabsf(up.x) > fabsf(du.x) ? du.x : up.x;
-      b.y = fabsf(up.y) > fabsf(du.y) ? du.y : up.y;
+      // the offsets after clamping: with up, dn of one sign, the smaller of
+      // |dn| and 2|up| with the sign of dn, the smaller of |up| and 2|dn| with
+      // the sign of up (one instruction each)
+      float2 a, b;
+      a.x = min_signed(dn.x, uu.x);
+      a.y = min_signed(dn.y, uu.y);
+      b.x = min_signed(up.x, du.x);
+      b.y = min_signed(up.y, du.y);
       float2 L = sub2(qm, a), H = add2(qm, b);
       L.x = e.x > 0.0f ? L.x : qm.x;
       L.y = e.y > 0.0f ? L.y : qm.y;
