@@ -399,7 +399,7 @@ def oracle_sample_rate(blocks_host, dx, seconds=10.0, threads=None, mode=0):
 
 # ------------------------------------------------------------ reference --
 def run_reference(args, rank, world):
-    """The oracle timed on the host cores: the reference arm of this build."""
+    """The reference arm: the oracle timed on the host cores."""
     if rank != 0:
         return
     import oracle
