@@ -772,6 +772,10 @@ def main():
         if args.impl == "ours":
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group(backend)
+    if world > 1:
+        # replicas: the scaling run times the headline and the forms beside it;
+        # the serving, Sedov and 26-point runs stay single-GPU extras
+        args.no_serving = args.no_sedov = args.no_quad26 = True
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
