@@ -17,6 +17,8 @@ Functions
 rhs_block(U, ghost, gamma, dx, mode)        any nx*ny*nz block, returns (dUdt, amax, flags)
 rhs_block_faces(...)                        also returns the face fluxes per direction
 rhs_batch(Us, gamma, dx, mode, threads)     list of cubic sub-grids, OpenMP over sub-grids
+forest.rhs / forest.stage                   multi-level forests of sub-grids: ghost cells
+                                            across levels and the flux correction
 """
 from __future__ import annotations
 

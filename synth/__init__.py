@@ -23,6 +23,9 @@ with the shapes of the paper's workloads:
   sedov_domain     the point explosion itself: a periodic cube of gas at rest
                    with the blast energy put into the 8 cells at its centre
                    (the scenario of Sec. VI-A, here with 5 passive species)
+  forest_leaves    leaves of a 2:1 balanced octree forest over a periodic
+                   cube (random or around-a-point refinement), and
+  smooth_forest_state  smooth random fields sampled at the forest's cells
 """
 from __future__ import annotations
 
@@ -280,3 +283,140 @@ def cell_radii(n):
     """Distance of every cell centre of sedov_domain's cube from its centre."""
     x = (np.arange(n) + 0.5) / n - 0.5
     return np.sqrt(x[None, None, :] ** 2 + x[None, :, None] ** 2 + x[:, None, None] ** 2)
+
+
+# --------------------------------------------------------------- forests --
+def _leaf_hash(seed, level, bx, by, bz):
+    """Uniform number in [0, 1) fixed by the seed and the block (order-free)."""
+    h = splitmix64((seed ^ (level << 60) ^ (bx << 40) ^ (by << 20) ^ bz) & MASK64)
+    return (h >> 11) / float(1 << 53)
+
+
+def forest_leaves(nb0, max_level, refine, seed=BASE_SEED, shuffle=True):
+    """Leaves of a 2:1 face-balanced octree forest over the periodic unit cube
+    cut into nb0^3 root blocks.
+
+    refine(level, corner (x, y, z), width) -> bool says whether a block (unit-
+    cube coordinates) is split; blocks at max_level are never split.  After
+    that, any leaf with a face neighbour two or more levels finer is split
+    until none is left (periodic neighbours included), so face neighbours
+    differ by at most one level.  Returns an int32 array [n][4] of
+    (level, bx, by, bz), block coordinates at the leaf's level in
+    [0, nb0 2^level); shuffled by the seed unless shuffle is False (then
+    sorted by level, bz, by, bx)."""
+    leaves = set()
+    stack = [(0, bx, by, bz) for bz in range(nb0) for by in range(nb0) for bx in range(nb0)]
+    while stack:
+        L, bx, by, bz = stack.pop()
+        w = 1.0 / (nb0 << L)
+        if L < max_level and refine(L, (bx * w, by * w, bz * w), w):
+            stack.extend((L + 1, 2 * bx + i, 2 * by + j, 2 * bz + k)
+                         for k in (0, 1) for j in (0, 1) for i in (0, 1))
+        else:
+            leaves.add((L, bx, by, bz))
+
+    def covering(L, b):
+        for l in range(L, -1, -1):
+            key = (l,) + tuple(c >> (L - l) for c in b)
+            if key in leaves:
+                return key
+        return None
+
+    changed = True
+    while changed:
+        changed = False
+        for leaf in sorted(leaves):
+            if leaf not in leaves:
+                continue
+            L, b = leaf[0], leaf[1:]
+            m = nb0 << L
+            for d in range(3):
+                for step in (-1, 1):
+                    q = list(b)
+                    q[d] = (q[d] + step) % m
+                    c = covering(L, q)
+                    if c is not None and c[0] < L - 1:
+                        leaves.discard(c)
+                        cl, cb = c[0], c[1:]
+                        for k in (0, 1):
+                            for j in (0, 1):
+                                for i in (0, 1):
+                                    leaves.add((cl + 1, 2 * cb[0] + i, 2 * cb[1] + j, 2 * cb[2] + k))
+                        changed = True
+    out = np.array(sorted(leaves, key=lambda t: (t[0], t[3], t[2], t[1])), dtype=np.int32).reshape(-1, 4)
+    if shuffle:
+        out = out[rng_for(seed, 0xF0CE57).permutation(len(out))]
+    return out
+
+
+def random_refine(seed, prob):
+    """refine() predicate for forest_leaves: split a block with probability
+    `prob`, decided by a hash of the seed and the block."""
+    def f(level, corner, width):
+        b = tuple(int(round(c / width)) for c in corner)
+        return _leaf_hash(seed, level, *b) < prob
+    return f
+
+
+def sphere_refine(centre, radii):
+    """refine() predicate: split a level-L block if it reaches within radii[L]
+    of `centre` (periodic unit cube); refinement around a point, as a
+    simulation refines around a blast or a star."""
+    def f(level, corner, width):
+        if level >= len(radii):
+            return False
+        d2 = 0.0
+        for c, x0 in zip(corner, centre):
+            # distance from the centre to the block along one axis, periodic
+            lo = (c - x0) % 1.0
+            hi = (x0 - c - width) % 1.0
+            d = 0.0 if lo + width >= 1.0 or hi + width >= 1.0 else min(lo, hi)
+            d2 += d * d
+        return d2 < radii[level] ** 2
+    return f
+
+
+def forest_cell_centres(leaves, nb0, N):
+    """Cell centres (unit-cube coordinates) of every leaf: array [n][3][N][N][N]
+    (x, y, z) in the storage order [z][y][x]."""
+    leaves = np.asarray(leaves).reshape(-1, 4)
+    out = np.empty((len(leaves), 3, N, N, N))
+    r = np.arange(N) + 0.5
+    for s, (L, bx, by, bz) in enumerate(leaves):
+        w = 1.0 / ((nb0 << int(L)) * N)
+        out[s, 0] = ((bx * N + r) * w)[None, None, :]
+        out[s, 1] = ((by * N + r) * w)[None, :, None]
+        out[s, 2] = ((bz * N + r) * w)[:, None, None]
+    return out
+
+
+def smooth_forest_state(leaves, nb0, N, nf=11, seed=BASE_SEED, gamma=GAMMA):
+    """Smooth periodic random fields sampled at the cell centres of a forest:
+    rho and p = 1.25 + 0.75 f with f a sum of 6 Fourier modes (wave numbers
+    1-3) normalised to |f| <= 1, so rho, p in [0.5, 2]; each velocity
+    component 0.1 g (g likewise in [-1, 1]); species Dirichlet(1) per cell.
+    Returns U [n_leaves][nf][N][N][N] (no ghost layers) and the root-level
+    cell width dx0 = 1 / (nb0 N)."""
+    rng = rng_for(seed, 0xF0E57)
+    xyz = forest_cell_centres(leaves, nb0, N)
+
+    def field():
+        f = np.zeros(xyz.shape[:1] + xyz.shape[2:])
+        amps = rng.normal(size=6)
+        amps /= np.abs(amps).sum()
+        for a in amps:
+            k = rng.integers(-3, 4, 3)
+            if not k.any():
+                k[0] = 1
+            ph = rng.uniform(0, 2 * np.pi)
+            f += a * np.cos(2 * np.pi * (k[0] * xyz[:, 0] + k[1] * xyz[:, 1] + k[2] * xyz[:, 2]) + ph)
+        return f
+
+    rho = 1.25 + 0.75 * field()
+    v = [0.1 * field() for _ in range(3)]
+    p = 1.25 + 0.75 * field()
+    X = None
+    if nf > 6:
+        X = np.moveaxis(rng.dirichlet(np.ones(nf - 6), size=rho.shape), -1, 0)
+    U = conserved_from_states(rho, v[0], v[1], v[2], p, X, gamma)  # [nf][n][N][N][N]
+    return np.ascontiguousarray(np.moveaxis(U, 0, 1)), 1.0 / (nb0 * N)
