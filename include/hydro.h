@@ -279,6 +279,85 @@ int hydro_domain_stage(const double* U, const double* U0, double alpha, double b
                        uint32_t flags);
 
 /* ---------------------------------------------------------------------------
+ * Forests: the adaptive mesh of the paper's application (Cartesian adaptive
+ * mesh refinement of an octree of sub-grids, Sec. III), as the leaves of an
+ * octree over a periodic cube of nb0^3 root blocks.  Every leaf holds N^3
+ * cells of width dx0 / 2^level and is stored without ghost layers,
+ * U[s][f][z][y][x] (DEVICE, binary64) for the leaves in the order given at
+ * creation.  Face neighbours must differ by at most one level (2:1 balance).
+ *
+ * The ghost shells are built on the device before every RHS: a face
+ * neighbour of the same level is read in place (as in hydro_domain_rhs);
+ * for a neighbour of another level the slab is first transferred into a
+ * library-owned auxiliary block:
+ *   - coarser neighbour: each ghost cell takes the value of the coarse cell
+ *     that contains it (piecewise-constant prolongation);
+ *   - finer neighbours (four leaves): each ghost cell takes the mean of the
+ *     eight fine cells it covers, summed in the order i + 2j + 4k of their
+ *     offsets, times 1/8 (restriction).
+ * Then the tile kernel runs on every leaf (face-centre scheme) and records
+ * the fluxes through faces towards other levels; last, every coarse cell
+ * next to finer leaves has the flux through that face replaced by the mean
+ * of the four fine fluxes (summed (0,0), (1,0), (0,1), (1,1) over the two
+ * tangential offsets, times 1/4; x, then y, then z faces), so that the RHS
+ * conserves every field to rounding, as the paper's application does.
+ * The paper states no level-transfer formulas: these are readings.
+ */
+typedef struct {
+  int32_t level;      /* 0 = root blocks; at most HYDRO_FOREST_MAX_LEVEL */
+  int32_t bx, by, bz; /* block coordinates at that level, in [0, nb0 << level) */
+} hydro_leaf_t;
+
+#define HYDRO_FOREST_MAX_LEVEL 15
+typedef struct hydro_forest hydro_forest_t;
+
+typedef struct {
+  int32_t n_leaves;
+  int32_t N, n_fields, nb0;
+  int32_t max_level;
+  int32_t n_level_faces;    /* leaf faces towards another level (auxiliary blocks) */
+  int32_t n_reflux_leaves;  /* leaves with at least one finer face neighbour */
+  int32_t pad;
+  int64_t device_bytes;     /* tables, auxiliary blocks and flux registers */
+} hydro_forest_info_t;
+
+/* Face neighbours of a forest's leaves, computed on the host (no GPU call):
+ * for leaf s and face k = 2 d + side (d = x, y, z; side 1 the high face),
+ * kind[6 s + k] = 0 same level, -1 coarser, +1 finer, and nbr[6 s + k] =
+ * the neighbour leaf (same level or coarser), or for finer neighbours the
+ * leaf of the four that touches the face at its lowest tangential corner.
+ * kind and nbr may be NULL.  HYDRO_EINVAL if the leaves are not a 2:1
+ * balanced exact cover of the cube (duplicates, overlaps, gaps, levels or
+ * coordinates out of range), or N is odd, < 6 or > HYDRO_MAX_N (a ghost
+ * slab of three cells must lie in one finer leaf), or nb0 < 1. */
+int hydro_forest_links(const hydro_leaf_t* leaves, int32_t n_leaves, int32_t nb0, int32_t N,
+                       int32_t* kind, int32_t* nbr);
+
+/* Validate the forest (as hydro_forest_links, plus 6 <= n_fields <=
+ * HYDRO_MAX_FIELDS), build its tables and allocate its device memory (on
+ * the current device).  The forest is then used on that device only. */
+int hydro_forest_create(const hydro_leaf_t* leaves, int32_t n_leaves, int32_t nb0, int32_t N,
+                        int32_t n_fields, hydro_forest_t** out);
+int hydro_forest_info(const hydro_forest_t* forest, hydro_forest_info_t* info);
+
+/* dU/dt (packed like U) and amax per leaf, with dx0 the cell width of
+ * level 0.  hydro_forest_stage: U_out = alpha U0 + beta (U + dt dU/dt) in
+ * the same launches (as hydro_domain_stage; U_out must not alias U, U0 may
+ * alias U or U_out).  flags: HYDRO_F_KNP or 0 (the 26-point variant reads
+ * edge ghosts and is refused on forests: HYDRO_EINVAL).  Three launches on
+ * `stream` (level transfer, tiles, flux correction); nothing is allocated.
+ * The auxiliary blocks and flux registers belong to the forest, so calls on
+ * one forest must be ordered (one stream, or synchronised). */
+int hydro_forest_rhs(hydro_forest_t* forest, const double* U, double dx0, double gamma,
+                     double* out_dUdt, double* out_amax, hydro_precision_t prec, void* stream,
+                     uint32_t flags);
+int hydro_forest_stage(hydro_forest_t* forest, const double* U, const double* U0, double alpha,
+                       double beta, double dt, double dx0, double gamma, double* U_out,
+                       double* out_amax, hydro_precision_t prec, void* stream, uint32_t flags);
+/* Free the forest's device memory (synchronises its device). */
+int hydro_forest_destroy(hydro_forest_t* forest);
+
+/* ---------------------------------------------------------------------------
  * hydro_rhs_noalloc -- hydro_rhs_ex for callers that cannot allocate memory.
  * The paper has no counterpart: this is a service of the library.
  *

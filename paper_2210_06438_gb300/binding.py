@@ -39,6 +39,7 @@ F_NO_STATUS = 1
 F_KNP = 2
 F_REGISTER_LOADS = 4
 F_QUAD26 = 8
+FOREST_MAX_LEVEL = 15
 
 
 
@@ -71,6 +72,21 @@ class ServerStats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Leaf(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("bx", ctypes.c_int32), ("by", ctypes.c_int32),
+                ("bz", ctypes.c_int32)]
+
+
+class ForestInfo(ctypes.Structure):
+    _fields_ = [("n_leaves", ctypes.c_int32), ("N", ctypes.c_int32), ("n_fields", ctypes.c_int32),
+                ("nb0", ctypes.c_int32), ("max_level", ctypes.c_int32),
+                ("n_level_faces", ctypes.c_int32), ("n_reflux_leaves", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class PlanInfo(ctypes.Structure):
@@ -136,6 +152,14 @@ def load(build_if_missing: bool = False):
         "hydro_domain_rhs": (ctypes.c_int, [P, i32, i32, i32, dbl, dbl, P, P, ctypes.c_int, P, u32]),
         "hydro_domain_stage": (ctypes.c_int, [P, P, dbl, dbl, dbl, i32, i32, i32, dbl, dbl, P, P,
                                               ctypes.c_int, P, u32]),
+        "hydro_forest_links": (ctypes.c_int, [ctypes.POINTER(Leaf), i32, i32, i32, P, P]),
+        "hydro_forest_create": (ctypes.c_int, [ctypes.POINTER(Leaf), i32, i32, i32, i32,
+                                               ctypes.POINTER(P)]),
+        "hydro_forest_info": (ctypes.c_int, [P, ctypes.POINTER(ForestInfo)]),
+        "hydro_forest_rhs": (ctypes.c_int, [P, P, dbl, dbl, P, P, ctypes.c_int, P, u32]),
+        "hydro_forest_stage": (ctypes.c_int, [P, P, P, dbl, dbl, dbl, dbl, dbl, P, P, ctypes.c_int,
+                                              P, u32]),
+        "hydro_forest_destroy": (ctypes.c_int, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -226,6 +250,64 @@ def domain_stage(U, U0, alpha, beta, dt, nb, N, n_fields, dx, U_out, amax, gamma
                                      int(nb), int(N), int(n_fields), float(dx), float(gamma),
                                      _ptr(U_out), _ptr(amax), int(prec), _stream(stream),
                                      int(flags)), "hydro_domain_stage")
+
+
+def _leaves(leaves):
+    """(level, bx, by, bz) rows -> a ctypes array of hydro_leaf_t."""
+    rows = [tuple(int(v) for v in r) for r in leaves]
+    return (Leaf * max(len(rows), 1))(*[Leaf(*r) for r in rows]), len(rows)
+
+
+def forest_links(leaves, nb0, N):
+    """hydro_forest_links (host only): (kind, nbr) as lists of 6 per leaf;
+    kind -1 coarser, 0 same level, +1 finer."""
+    arr, n = _leaves(leaves)
+    kind = (ctypes.c_int32 * (6 * max(n, 1)))()
+    nbr = (ctypes.c_int32 * (6 * max(n, 1)))()
+    _check(load().hydro_forest_links(arr, n, int(nb0), int(N), ctypes.addressof(kind),
+                                     ctypes.addressof(nbr)), "hydro_forest_links")
+    return ([list(kind[6 * s:6 * s + 6]) for s in range(n)],
+            [list(nbr[6 * s:6 * s + 6]) for s in range(n)])
+
+
+class Forest:
+    """hydro_forest_*: a multi-level forest of N^3 leaves (ghost slabs across
+    levels and the flux correction on the device)."""
+
+    def __init__(self, leaves, nb0, N, n_fields):
+        arr, n = _leaves(leaves)
+        h = ctypes.c_void_p()
+        _check(load().hydro_forest_create(arr, n, int(nb0), int(N), int(n_fields), ctypes.byref(h)),
+               "hydro_forest_create")
+        self._h = h
+
+    def rhs(self, U, dx0, out, amax, gamma=5.0 / 3.0, prec=FP64, stream=None, flags=0):
+        _check(load().hydro_forest_rhs(self._h, _ptr(U), float(dx0), float(gamma), _ptr(out),
+                                       _ptr(amax), int(prec), _stream(stream), int(flags)),
+               "hydro_forest_rhs")
+
+    def stage(self, U, U0, alpha, beta, dt, dx0, U_out, amax, gamma=5.0 / 3.0, prec=FP64,
+              stream=None, flags=0):
+        _check(load().hydro_forest_stage(self._h, _ptr(U), _ptr(U0), float(alpha), float(beta),
+                                         float(dt), float(dx0), float(gamma), _ptr(U_out),
+                                         _ptr(amax), int(prec), _stream(stream), int(flags)),
+               "hydro_forest_stage")
+
+    def info(self) -> dict:
+        fi = ForestInfo()
+        _check(load().hydro_forest_info(self._h, ctypes.byref(fi)), "hydro_forest_info")
+        return fi.as_dict()
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().hydro_forest_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def rhs_per_subgrid(desc, out, amax, streams: Iterable, ghost=3, gamma=5.0 / 3.0, prec=FP64,

@@ -746,18 +746,144 @@ __host__ __device__ constexpr size_t smem_layout_bytes(int lch) {
          ((size_t)NGRP * STAR + STAR + 3 * NLN * NFC * 2 + 2 * (size_t)NGRP * lch * NFC);
 }
 
+// ------------------------------------------------------------ forests --
+// Leaves of an octree forest of several refinement levels, N^3 cells each,
+// stored without ghosts ([s][f][N^3]).  links[8 s + k], k < 6 (face k = 2 d +
+// side, side 1 the high face): the face neighbour, a leaf of the same level
+// (< nl) or nl + j for auxiliary block j, which holds that face's ghost slab
+// transferred from a coarser or finer level (in the layout of a same-level
+// neighbour, [j][f][N^3]); links[8 s + 6]: the leaf's level.
+//
+// ForestLoc locates a read-region cell given by leaf-local coordinates, at
+// most one of which lies outside [0, N).
+struct ForestLoc {
+  const double* U;
+  const double* aux;
+  const int* row;  // links of the leaf
+  int s, nl, N;
+  long long bsz;   // doubles per stored block (F N^3)
+  __device__ __forceinline__ const double* ptr(int cx, int cy, int cz) const {
+    int face = -1;
+    if (cx < 0) {
+      face = 0;
+      cx += N;
+    } else if (cx >= N) {
+      face = 1;
+      cx -= N;
+    } else if (cy < 0) {
+      face = 2;
+      cy += N;
+    } else if (cy >= N) {
+      face = 3;
+      cy -= N;
+    } else if (cz < 0) {
+      face = 4;
+      cz += N;
+    } else if (cz >= N) {
+      face = 5;
+      cz -= N;
+    }
+    const int blk = face < 0 ? s : __ldg(row + face);
+    const double* base = blk < nl ? U + blk * bsz : aux + (blk - nl) * bsz;
+    return base + (cz * N + cy) * N + cx;
+  }
+};
+
+// Flux registers: for auxiliary block j (a leaf face towards another level),
+// reg[(j F + f) N^2 + b N + a] receives the flux of field f through the
+// face's cell column (a, b); the tangential axes of a face normal to d are
+// (y, z), (x, z), (x, y) for d = x, y, z.
+struct ForestCapture {
+  double* reg;
+  const int* row;
+  int nl, N, F, ox, oy, oz, f0;
+  // Record the fluxes of the lines [l0, l0 + lch) of direction d, just
+  // computed in QS (slot j = field f0 + j, or the field pair f0 + 2j, +1),
+  // through the faces that lie on the leaf's boundary towards another level.
+  template <int MODE, int NT>
+  __device__ __forceinline__ void faces(const typename Prec<MODE>::V* QS, int fs, int lch, int l0, int ng,
+                                        int d, int ex, int ey, int ez) const {
+    const int e_d = d == 0 ? ex : (d == 1 ? ey : ez);
+    const int e_a = d == 0 ? ey : ex, e_b = d == 2 ? ey : ez;
+    const int o_d = d == 0 ? ox : (d == 1 ? oy : oz);
+    const int o_a = d == 0 ? oy : ox, o_b = d == 2 ? oy : oz;
+    const int lo = o_d == 0 ? __ldg(row + 2 * d) : -1;
+    const int hi = o_d + e_d == N ? __ldg(row + 2 * d + 1) : -1;
+    if (lo < nl && hi < nl) return;
+    const long long nn = (long long)N * N;
+    for (int task = threadIdx.x; task < 2 * lch * ng; task += NT) {
+      const int ll = task % lch, r = task / lch, side = r & 1, j = r >> 1;
+      const int blk = side ? hi : lo;
+      const int l = l0 + ll, a = l % TE, b = l / TE;
+      if (blk < nl || a >= e_a || b >= e_b) continue;
+      const auto v = QS[j * fs + ll * NFC + (side ? e_d : 0)];
+      double* dst = reg + (long long)(blk - nl) * F * nn + (long long)(o_b + b) * N + (o_a + a);
+      if constexpr (MODE == 0) {
+        dst[(f0 + j) * nn] = v;
+      } else {
+        const int f = f0 + 2 * j;
+        dst[f * nn] = (double)v.x;
+        if (f + 1 < F) dst[(f + 1) * nn] = (double)v.y;
+      }
+    }
+  }
+};
+
+// Source of forest tiles: leaf s = t / tpe^3, cell width dx0 / 2^level.
+struct ForestTiles {
+  const double* __restrict__ U;
+  const double* __restrict__ aux;
+  const int* __restrict__ links;
+  double* __restrict__ reg;
+  int nl, N, F, tpe;
+  double inv_dx0;
+  short flags;  // bit 1: dx0 a power of two
+  __device__ __forceinline__ Tile operator()(int t) const {
+    const int tps = tpe * tpe * tpe;
+    const int s = t / tps, k = t - s * tps;
+    Tile tile;
+    tile.U = U;
+    tile.out_off = (long long)s * F * N * N * N;
+    tile.amax_off = s;
+    tile.inv_dx = inv_dx0 * (double)(1u << __ldg(links + 8 * s + 6));
+    tile.sub = s;
+    tile.N = N;
+    tile.F = F;
+    tile.G = N;
+    tile.ox = (short)((k % tpe) * TE);
+    tile.oy = (short)(((k / tpe) % tpe) * TE);
+    tile.oz = (short)((k / (tpe * tpe)) * TE);
+    tile.flags = (short)((tps > 1 ? 1 : 0) | (flags & 2));
+    tile.pad[0] = 0;
+    tile.pad[1] = 0;
+    return tile;
+  }
+  __device__ __forceinline__ ForestLoc loc(const Tile& tile) const {
+    return ForestLoc{U, aux, links + 8 * tile.sub, tile.sub, nl, N, (long long)F * N * N * N};
+  }
+  __device__ __forceinline__ ForestCapture capture(const Tile& tile, int f0) const {
+    return ForestCapture{reg, links + 8 * tile.sub, nl, N, F, tile.ox, tile.oy, tile.oz, f0};
+  }
+};
+
+struct NoCapture {
+  template <int MODE, int NT>
+  __device__ __forceinline__ void faces(const typename Prec<MODE>::V*, int, int, int, int, int, int, int,
+                                        int) const {}
+};
+
 // One pass of steps A2-A4 over a group of `ng` field slots (V elements) for
 // all three directions.  HYD: the hydro group (Kurganov-Tadmor flux, records
 // g_l, g_r and the signal speed); else the species (flux from g_l, g_r).
 // acc[k][j] receives, for the thread's owned cells k, the sum of the flux
-// differences x, then y, then z of slot j.
-template <int MODE, int NT, bool HYD>
+// differences x, then y, then z of slot j.  `cap` may record face fluxes.
+template <int MODE, int NT, bool HYD, class Cap = NoCapture>
 __device__ __forceinline__ void group_pass(
     const typename Prec<MODE>::V* W, typename Prec<MODE>::R* GG, typename Prec<MODE>::V* QS,
     int lch, int ng, int ex, int ey, int ez, typename Prec<MODE>::R gamma,
     typename Prec<MODE>::R inv_gm1, bool knp,
     typename Prec<MODE>::Acc (&acc)[(TE * TE * TE + NT - 1) / NT][NGRP / Prec<MODE>::PACK],
-    typename Prec<MODE>::R& amax) {
+    typename Prec<MODE>::R& amax, const Cap& cap = Cap{}) {
   typedef typename Prec<MODE>::R R;
   typedef typename Prec<MODE>::V V;
   constexpr int CPT = (TE * TE * TE + NT - 1) / NT;
@@ -819,6 +945,7 @@ __device__ __forceinline__ void group_pass(
         }
       }
       __syncthreads();
+      cap.template faces<MODE, NT>(QS, fs, lch, l0, ng, d, ex, ey, ez);
       // ---- A4: flux differences into the owned cells, x then y then z
 #pragma unroll
       for (int k = 0; k < CPT; k++) {
@@ -909,12 +1036,19 @@ __device__ __forceinline__ void store_group(
 }
 
 // The persistent tile loop; `fetch(t)` returns tile t's descriptor; KC read-
-// region slots of a thread are loaded per batch.
-// DOMAIN: the tiles belong to a periodic cube of pad[0]^3 sub-grids stored
-// without ghosts ([s][f][N^3], s = bx + nb (by + nb bz)); each tile's read
-// region is gathered from the neighbouring sub-grids' interiors, and `stage`
-// may turn the output into an explicit stage update.
-template <int MODE, int NT, int KC, class Fetch, bool DOMAIN = false>
+// region slots of a thread are loaded per batch.  DOM says where a tile's
+// read region lives:
+//   0  its sub-grid's ghosted block;
+//   1  a periodic cube of pad[0]^3 sub-grids stored without ghosts ([s][f][N^3],
+//      s = bx + nb (by + nb bz)): the ghost slabs are read from the
+//      neighbouring sub-grids' interiors;
+//   2  a forest of leaves of several refinement levels stored without ghosts:
+//      a ghost slab is read from the face neighbour of the same level or from
+//      an auxiliary block holding the slab transferred from another level
+//      (`fetch.loc`), and the fluxes through faces towards other levels are
+//      recorded for the flux correction (`fetch.capture`).
+// With DOM != 0, `stage` may turn the output into an explicit stage update.
+template <int MODE, int NT, int KC, class Fetch, int DOM = 0>
 __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int lch,
                                           double* __restrict__ out, double* __restrict__ amax_out,
                                           Status* __restrict__ status, double gamma_d,
@@ -943,9 +1077,11 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
     const Tile tile = fetch(t);
     const int F = tile.F, G = tile.G, N = tile.N, gh = (tile.G - tile.N) >> 1;
     const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
-    const long long plane = DOMAIN ? (long long)N * N * N : (long long)G * G * G;  // field stride
+    const long long plane = DOM ? (long long)N * N * N : (long long)G * G * G;  // field stride
     DomainPos dp;
-    if constexpr (DOMAIN) dp.init(tile.sub, tile.pad[0], N, F);
+    if constexpr (DOM == 1) dp.init(tile.sub, tile.pad[0], N, F);
+    ForestLoc fl;
+    if constexpr (DOM == 2) fl = fetch.loc(tile);
 
     // offset of read-region slot s within a field of the stored block; -1 if
     // the slot is outside the (possibly partial) tile's read region: at most
@@ -957,11 +1093,19 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
       int outside = (x < 0 || x >= ex) + (y < 0 || y >= ey) + (z < 0 || z >= ez);
       bool valid = s < STAR && outside <= 1 && x < ex + 3 && y < ey + 3 && z < ez + 3;
       if (!valid) return -1;
-      if constexpr (DOMAIN) {
+      if constexpr (DOM == 1) {
         return dp.off(tile.ox + x, tile.oy + y, tile.oz + z);
       } else {
         return ((tile.oz + z + gh) * G + (tile.oy + y + gh)) * G + (tile.ox + x + gh);
       }
+    };
+    // forests: the address of slot s's cell in field 0, or null if not read
+    auto slot_src = [&](int s) -> const double* {
+      int x, y, z;
+      cell_of(s < STAR ? s : 0, x, y, z);
+      int outside = (x < 0 || x >= ex) + (y < 0 || y >= ey) + (z < 0 || z >= ez);
+      bool valid = s < STAR && outside <= 1 && x < ex + 3 && y < ey + 3 && z < ez + 3;
+      return valid ? fl.ptr(tile.ox + x, tile.oy + y, tile.oz + z) : nullptr;
     };
 
     // ---- A0/A1 (hydro group): rho, s, E, tau -> rho, v, p, phi.  In each
@@ -971,12 +1115,21 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
     for (int k0 = 0; k0 < SPT; k0 += KC) {
       double u[KC][6];
       int off[KC];
+      const double* src[KC];
 #pragma unroll
       for (int kk = 0; kk < KC; kk++) {
-        off[kk] = slot_offset(tid + (k0 + kk) * NT);
+        if constexpr (DOM == 2) {
+          src[kk] = slot_src(tid + (k0 + kk) * NT);
+          off[kk] = src[kk] ? 0 : -1;
+        } else {
+          off[kk] = slot_offset(tid + (k0 + kk) * NT);
+        }
 #pragma unroll
         for (int f = 0; f < 6; f++)
-          if (k0 + kk < SPT && off[kk] >= 0) u[kk][f] = __ldg(tile.U + f * plane + off[kk]);
+          if (k0 + kk < SPT && off[kk] >= 0) {
+            if constexpr (DOM == 2) u[kk][f] = __ldg(src[kk] + f * plane);
+            else u[kk][f] = __ldg(tile.U + f * plane + off[kk]);
+          }
       }
 #pragma unroll
       for (int kk = 0; kk < KC; kk++) {
@@ -1003,15 +1156,19 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
       }
     }
     bad = __syncthreads_or(bad);
-    if (!DOMAIN && prefetch && t + (int)gridDim.x < n_tiles)
+    if (!DOM && prefetch && t + (int)gridDim.x < n_tiles)
       prefetch_tile_l2(fetch(t + gridDim.x), tid, NT, prefetch);
 
     // ---- hydro group: rho, momentum, E, tau
     R amax = R(0);
     {
       Acc acc[CPT][NS];
-      group_pass<MODE, NT, true>(W, GG, QS, lch, NS, ex, ey, ez, gamma, inv_gm1, knp, acc, amax);
-      store_group<MODE, NT, DOMAIN>(out, tile, ex, ey, ez, 0, 6, acc, stage);
+      if constexpr (DOM == 2)
+        group_pass<MODE, NT, true>(W, GG, QS, lch, NS, ex, ey, ez, gamma, inv_gm1, knp, acc, amax,
+                                   fetch.capture(tile, 0));
+      else
+        group_pass<MODE, NT, true>(W, GG, QS, lch, NS, ex, ey, ez, gamma, inv_gm1, knp, acc, amax);
+      store_group<MODE, NT, (DOM != 0)>(out, tile, ex, ey, ez, 0, 6, acc, stage);
     }
 
     // ---- A0/A1 (species): X_k = rho_k / rho into the group slots
@@ -1021,13 +1178,21 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
       for (int k0 = 0; k0 < SPT; k0 += KC) {
         double v[KC][MAXF - 6];
         int off[KC];
+        const double* src[KC];
 #pragma unroll
         for (int kk = 0; kk < KC; kk++) {
-          off[kk] = slot_offset(tid + (k0 + kk) * NT);
+          if constexpr (DOM == 2) {
+            src[kk] = slot_src(tid + (k0 + kk) * NT);
+            off[kk] = src[kk] ? 0 : -1;
+          } else {
+            off[kk] = slot_offset(tid + (k0 + kk) * NT);
+          }
 #pragma unroll
           for (int f = 0; f < MAXF - 6; f++)
-            if (k0 + kk < SPT && off[kk] >= 0 && f < nsp)
-              v[kk][f] = __ldg(tile.U + (6 + f) * plane + off[kk]);
+            if (k0 + kk < SPT && off[kk] >= 0 && f < nsp) {
+              if constexpr (DOM == 2) v[kk][f] = __ldg(src[kk] + (6 + f) * plane);
+              else v[kk][f] = __ldg(tile.U + (6 + f) * plane + off[kk]);
+            }
         }
 #pragma unroll
         for (int kk = 0; kk < KC; kk++) {
@@ -1065,9 +1230,13 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
     // ---- species group
     if (nsp > 0) {
       Acc acc[CPT][NS];
-      group_pass<MODE, NT, false>(W, GG, QS, lch, (nsp + PK - 1) / PK, ex, ey, ez, gamma, inv_gm1,
-                                  knp, acc, amax);
-      store_group<MODE, NT, DOMAIN>(out, tile, ex, ey, ez, 6, nsp, acc, stage);
+      if constexpr (DOM == 2)
+        group_pass<MODE, NT, false>(W, GG, QS, lch, (nsp + PK - 1) / PK, ex, ey, ez, gamma, inv_gm1,
+                                    knp, acc, amax, fetch.capture(tile, 6));
+      else
+        group_pass<MODE, NT, false>(W, GG, QS, lch, (nsp + PK - 1) / PK, ex, ey, ez, gamma, inv_gm1,
+                                    knp, acc, amax);
+      store_group<MODE, NT, (DOM != 0)>(out, tile, ex, ey, ez, 6, nsp, acc, stage);
     }
 
     // ---- A5: largest signal speed of the tile
@@ -1440,8 +1609,18 @@ __global__ void __launch_bounds__(NT, MINB)
 rhs_domain_kernel(DomainTiles dom, int n_tiles, int lch, double* __restrict__ out,
                   double* __restrict__ amax_out, Status* __restrict__ status, double gamma_d,
                   int write_status, int scheme, StageArgs stage) {
-  tile_loop<MODE, NT, KC, DomainTiles, true>(dom, n_tiles, lch, out, amax_out, status, gamma_d, write_status,
+  tile_loop<MODE, NT, KC, DomainTiles, 1>(dom, n_tiles, lch, out, amax_out, status, gamma_d, write_status,
                                              0, scheme == 1, stage);
+}
+
+// Forest tiles (register-load kernel; see ForestTiles).
+template <int MODE, int NT, int MINB, int KC = (MINB == 1 ? 4 : 2)>
+__global__ void __launch_bounds__(NT, MINB)
+rhs_forest_kernel(ForestTiles ft, int n_tiles, int lch, double* __restrict__ out,
+                  double* __restrict__ amax_out, Status* __restrict__ status, double gamma_d,
+                  int write_status, int scheme, StageArgs stage) {
+  tile_loop<MODE, NT, KC, ForestTiles, 2>(ft, n_tiles, lch, out, amax_out, status, gamma_d, write_status, 0,
+                                          scheme == 1, stage);
 }
 
 template <int NT>

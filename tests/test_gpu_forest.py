@@ -1,0 +1,159 @@
+"""GPU parity of the forest entry points (multi-level ghost slabs, fused tile
+kernel, flux correction) against the forest oracle, in both precision
+forms, with both fluxes, the fused stage, 8^3 and 16^3 leaves; plus the
+one-level forest against the periodic domain kernel bit for bit, exact
+zeros on constant states and conservation across levels."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2210_06438_gb300 as hydro
+import synth
+from oracle import forest as of
+from tests import gpu_helpers as gh
+
+pytestmark = pytest.mark.gpu
+MX = hydro.FP32_FLUX_FP64_ACC
+
+
+def _forest(nb0=2, seed=7, prob=0.25, max_level=2):
+    return synth.forest_leaves(nb0, max_level, synth.random_refine(seed, prob), seed=seed)
+
+
+def _run(lv, nb0, U, dx0, prec, flags=0, stage=None):
+    n, nf, N = U.shape[0], U.shape[1], U.shape[-1]
+    fo = hydro.Forest(lv, nb0, N, nf)
+    Ud = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+    out = torch.full_like(Ud, float("nan"))
+    am = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    if stage is None:
+        fo.rhs(Ud, dx0, out, am, prec=prec, flags=flags)
+    else:
+        U0, a, b, dt = stage
+        fo.stage(Ud, torch.from_numpy(U0).cuda(), a, b, dt, dx0, out, am, prec=prec, flags=flags)
+    torch.cuda.synchronize()
+    info = fo.info()
+    fo.close()
+    return list(out.cpu().numpy()), am.cpu().numpy(), info
+
+
+def _dxs(lv, dx0):
+    return [dx0 / (1 << int(L)) for L in lv[:, 0]]
+
+
+def _check(prec, got, gam, ref, ram, U, dxs):
+    if prec == hydro.FP64:
+        return gh.check_fp64(got, ref, gam, ram, list(U), dxs)
+    return gh.check_mixed(got, ref, gam, ram, list(U), dxs)
+
+
+@pytest.mark.parametrize("prec", [hydro.FP64, MX])
+@pytest.mark.parametrize("N,nb0,seed,prob,nf", [(8, 2, 7, 0.25, 11), (8, 2, 4, 0.25, 6), (16, 1, 3, 0.6, 7)])
+def test_forest_rhs_matches_oracle(prec, N, nb0, seed, prob, nf):
+    lv = _forest(nb0, seed, prob)
+    assert len(set(lv[:, 0])) >= 2
+    U, dx0 = synth.smooth_forest_state(lv, nb0, N, nf=nf, seed=31 + seed)
+    got, gam, info = _run(lv, nb0, U, dx0, prec)
+    ref, ram = of.rhs(lv, nb0, list(U), dx0, mode=0 if prec == hydro.FP64 else oracle.MODE_MIXED)
+    _check(prec, got, gam, ref, ram, U, _dxs(lv, dx0))
+    kind, _ = hydro.forest_links(lv, nb0, N)
+    assert info["n_level_faces"] == sum(k != 0 for row in kind for k in row) > 0
+    assert info["n_reflux_leaves"] == sum(any(k == 1 for k in row) for row in kind) > 0
+
+
+def test_forest_one_sided_flux():
+    lv = _forest()
+    U, dx0 = synth.smooth_forest_state(lv, 2, 8, nf=9, seed=41)
+    got, gam, _ = _run(lv, 2, U, dx0, hydro.FP64, flags=hydro.F_KNP)
+    ref, ram = of.rhs(lv, 2, list(U), dx0, mode=oracle.FLUX_KNP)
+    gh.check_fp64(got, ref, gam, ram, list(U), _dxs(lv, dx0))
+
+
+@pytest.mark.parametrize("prec", [hydro.FP64, MX])
+def test_forest_stage_matches_oracle(prec):
+    lv = _forest(2, 4, 0.25)
+    U, dx0 = synth.smooth_forest_state(lv, 2, 8, nf=8, seed=42)
+    U0, _ = synth.smooth_forest_state(lv, 2, 8, nf=8, seed=43)
+    a, b, dt = 0.75, 0.25, 2e-3
+    got, gam, _ = _run(lv, 2, U, dx0, prec, stage=(U0, a, b, dt))
+    mode = 0 if prec == hydro.FP64 else oracle.MODE_MIXED
+    ref, ram = of.stage(lv, 2, list(U), list(U0), a, b, dt, dx0, mode=mode)
+    dU, _ = of.rhs(lv, 2, list(U), dx0, mode=mode)
+    dxs = _dxs(lv, dx0)
+    for s in range(len(lv)):
+        Umax = np.abs(U[s]).reshape(U.shape[1], -1).max(axis=1)
+        for f in range(U.shape[1]):
+            # the state's rounding plus beta dt times the RHS gate of the form
+            if mode == 0:
+                rt = 1e-12 * max(np.abs(dU[s][f]).max(), ram[s] * Umax[f] / dxs[s])
+            else:
+                rt = 64 * 2.0 ** -24 * 2 * ram[s] * (Umax[f] + (Umax[4] if 1 <= f <= 4 else 0)) / dxs[s]
+            tol = 4e-16 * np.abs(ref[s][f]).max() + b * dt * rt
+            assert np.abs(got[s][f] - ref[s][f]).max() <= tol, (s, f)
+    assert np.allclose(gam, ram, rtol=1e-14 if mode == 0 else 1e-6, atol=0)
+
+
+@pytest.mark.parametrize("prec", [hydro.FP64, MX])
+def test_one_level_forest_equals_domain_kernel(prec):
+    nb0, N = 3, 8
+    lv = synth.forest_leaves(nb0, 0, lambda *a: False, seed=6)
+    glob = synth.plain_domain(seed=44, n=nb0 * N, nf=11)
+    blocks = synth.gather_blocks(glob, N, blocks=[tuple(l[1:]) for l in lv])
+    U = np.ascontiguousarray(blocks[:, :, 3:-3, 3:-3, 3:-3])
+    dx0 = 1.0 / (nb0 * N)
+    got, gam, info = _run(lv, nb0, U, dx0, prec)
+    assert info["n_level_faces"] == 0 and info["n_reflux_leaves"] == 0
+    # the domain kernel on the cube in its own order s = bx + nb (by + nb bz)
+    order = [int(x + nb0 * (y + nb0 * z)) for _, x, y, z in lv]
+    dom = np.empty_like(U)
+    dom[order] = U
+    Ud = torch.from_numpy(dom).cuda()
+    out = torch.empty_like(Ud)
+    am = torch.empty(len(lv), dtype=torch.float64, device="cuda")
+    hydro.domain_rhs(Ud, nb0, N, 11, dx0, out, am, prec=prec)
+    torch.cuda.synchronize()
+    o, a = out.cpu().numpy(), am.cpu().numpy()
+    for s in range(len(lv)):
+        assert np.array_equal(got[s], o[order[s]])
+        assert gam[s] == a[order[s]]
+
+
+@pytest.mark.parametrize("prec", [hydro.FP64, MX])
+def test_constant_state_exact_zero(prec):
+    lv = _forest(2, 4, 0.25)
+    n, N = len(lv), 8
+    shp = (n, N, N, N)
+    X = np.full((2,) + shp, 0.5)
+    Uc = synth.conserved_from_states(np.full(shp, 0.8), np.full(shp, -0.3), np.full(shp, 0.1),
+                                     np.full(shp, 0.2), np.full(shp, 1.7), X)
+    U = np.ascontiguousarray(np.moveaxis(Uc, 0, 1))
+    got, gam, _ = _run(lv, 2, U, 1.0 / 16, prec)
+    for o in got:
+        assert np.all(o == 0.0)
+
+
+@pytest.mark.parametrize("prec", [hydro.FP64, MX])
+def test_conservation_across_levels(prec):
+    lv = _forest(2, 7, 0.25)
+    U, dx0 = synth.smooth_forest_state(lv, 2, 8, nf=11, seed=45)
+    got, _, _ = _run(lv, 2, U, dx0, prec)
+    vol = np.array(_dxs(lv, dx0)) ** 3
+    tot = sum(got[s].sum(axis=(1, 2, 3)) * vol[s] for s in range(len(lv)))
+    mag = sum(np.abs(got[s]).sum(axis=(1, 2, 3)) * vol[s] for s in range(len(lv)))
+    assert np.all(np.abs(tot) <= (1e-14 if prec == hydro.FP64 else 1e-12) * mag), tot / mag
+
+
+def test_forest_argument_checks():
+    lv = _forest(2, 4, 0.25)
+    U, dx0 = synth.smooth_forest_state(lv, 2, 8, nf=6)
+    fo = hydro.Forest(lv, 2, 8, 6)
+    Ud = torch.from_numpy(U).cuda()
+    out = torch.empty_like(Ud)
+    am = torch.empty(len(lv), dtype=torch.float64, device="cuda")
+    for kw in (dict(flags=hydro.F_QUAD26), dict(dx0=-1.0), dict(gamma=1.0), dict(out=Ud)):
+        with pytest.raises(hydro.HydroError) as ei:
+            fo.rhs(Ud, kw.get("dx0", dx0), kw.get("out", out), am, gamma=kw.get("gamma", 5.0 / 3.0),
+                   flags=kw.get("flags", 0))
+        assert ei.value.code == hydro.HYDRO_EINVAL
+    fo.close()
