@@ -362,6 +362,103 @@ def sedov_gpu_run(n=64, prec=0, cfl=0.3, t_end=None, dts=None, gamma=5.0 / 3.0, 
     return {"U": U, "t": t, "dts": used, "steps": k, "ms": ev0.elapsed_time(ev1), "n": n, "dx": dx}
 
 
+def sedov_forest_run(nb0=2, N=8, radii=(0.45, 0.25), prec=0, cfl=0.3, t_end=None, dts=None,
+                     gamma=5.0 / 3.0, flags=0, stream=None):
+    """The point explosion on a forest refined around the centre
+    (synth.sedov_forest, 11 fields), integrated with SSP-RK3 steps of three
+    forest stages (ghost slabs across levels, fused tiles, flux correction),
+    to t_end or along `dts`.  One global step for all levels: dt = cfl min
+    over leaves of dx_leaf / a_leaf, a_leaf the leaf's largest signal speed
+    over the previous step's stages.  Returns a dict with the final state
+    (device, [n][nf][N^3]), the leaves, t, the steps' dt and the wall time."""
+    import torch
+
+    import paper_2210_06438_gb300 as hydro
+
+    leaves, U0, dx0 = synth.sedov_forest(nb0=nb0, N=N, radii=radii, gamma=gamma)
+    nf = U0.shape[1]
+    fo = hydro.Forest(leaves, nb0, N, nf)
+    U = torch.from_numpy(U0).cuda()
+    W1, W2 = torch.empty_like(U), torch.empty_like(U)
+    n = len(leaves)
+    am = torch.empty((3, n), dtype=torch.float64, device="cuda")
+    dxs = torch.tensor([dx0 / (1 << int(L)) for L in leaves[:, 0]], dtype=torch.float64, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    kw = dict(gamma=gamma, prec=prec, stream=st, flags=flags)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(st)
+    fo.rhs(U, dx0, W1, am[0], **kw)
+    a_leaf = am[0].clone()
+    t, used, k = 0.0, [], 0
+    while (dts is not None and k < len(dts)) or (dts is None and t < t_end):
+        dt = dts[k] if dts is not None else min(cfl * float((dxs / a_leaf).min()), t_end - t)
+        fo.stage(U, U, 0.0, 1.0, dt, dx0, W1, am[0], **kw)
+        fo.stage(W1, U, 0.75, 0.25, dt, dx0, W2, am[1], **kw)
+        fo.stage(W2, U, 1.0 / 3.0, 2.0 / 3.0, dt, dx0, W1, am[2], **kw)
+        U, W1 = W1, U
+        a_leaf = am.max(dim=0).values
+        t += dt
+        used.append(dt)
+        k += 1
+    ev1.record(st)
+    torch.cuda.synchronize()
+    info = fo.info()
+    fo.close()
+    return {"U": U, "leaves": leaves, "t": t, "dts": used, "steps": k, "ms": ev0.elapsed_time(ev1),
+            "nb0": nb0, "dx0": dx0, "info": info}
+
+
+def forest_forms(steps, warmup, stream, nb0=16, radii=(0.35, 0.2), N=8, nf=11, gamma=5.0 / 3.0):
+    """The RHS of an adaptive forest: leaves of three levels refined around
+    the cube's centre (synth.sphere_refine; 128^3 cells' resolution at level
+    0, 512^3 at the centre), smooth random fields (synth.smooth_forest_state),
+    11 fields.  Each RHS is three launches: ghost slabs across levels, the
+    fused tile kernel, the flux correction.  Also one SSP-RK3 step of three
+    forest stages.  Value: leaf cell-updates/s."""
+    import torch
+
+    import paper_2210_06438_gb300 as hydro
+
+    leaves = synth.forest_leaves(nb0, len(radii), synth.sphere_refine((0.5, 0.5, 0.5), radii))
+    U_h, dx0 = synth.smooth_forest_state(leaves, nb0, N, nf=nf)
+    U = torch.from_numpy(U_h).cuda()
+    del U_h
+    out, tmp = torch.empty_like(U), torch.empty_like(U)
+    n = len(leaves)
+    am = torch.empty(n, dtype=torch.float64, device="cuda")
+    vol = torch.tensor([(dx0 / (1 << int(L))) ** 3 for L in leaves[:, 0]], dtype=torch.float64,
+                       device="cuda")
+    fo = hydro.Forest(leaves, nb0, N, nf)
+    cells = n * N ** 3
+    res = {}
+    for name, prec in (("fp64_forest", hydro.FP64), ("mixed_forest", hydro.FP32_FLUX_FP64_ACC)):
+        ms = time_steps(lambda: fo.rhs(U, dx0, out, am, gamma=gamma, prec=prec, stream=stream), steps,
+                        warmup, stream)
+        w = (out * vol[:, None, None, None, None]).sum(dim=(0, 2, 3, 4))
+        a = (out.abs() * vol[:, None, None, None, None]).sum(dim=(0, 2, 3, 4))
+        res[name] = {"value": cells / (ms * 1e-3), "ms": ms,
+                     "conservation_drift": float((w / a.clamp_min(1e-300)).abs().max())}
+
+    def rk3(prec):
+        dt = 1e-5
+        fo.stage(U, U, 0.0, 1.0, dt, dx0, out, am, gamma=gamma, prec=prec, stream=stream)
+        fo.stage(out, U, 0.75, 0.25, dt, dx0, tmp, am, gamma=gamma, prec=prec, stream=stream)
+        fo.stage(tmp, U, 1.0 / 3.0, 2.0 / 3.0, dt, dx0, out, am, gamma=gamma, prec=prec, stream=stream)
+
+    ms = time_steps(lambda: rk3(hydro.FP64), max(1, steps // 2), 1, stream)
+    res["fp64_forest_rk3_step"] = {"value": 3 * cells / (ms * 1e-3), "ms": ms,
+                                   "note": "three forest stages; value = stage cell-updates/s"}
+    info = fo.info()
+    fo.close()
+    levels = np.bincount(leaves[:, 0]).tolist()
+    res["fp64_forest"]["workload"] = {
+        "leaves": n, "leaves_by_level": levels, "cells": cells, "N": N, "fields": nf, "nb0": nb0,
+        "refine_radii": list(radii), "level_faces": info["n_level_faces"],
+        "reflux_leaves": info["n_reflux_leaves"], "forest_device_bytes": info["device_bytes"],
+        "note": "sphere refinement around the centre, 2:1 balanced, periodic; smooth random fields"}
+    return res
+
+
 def sedov_form(n, prec, flags=0):
     """One Sedov run at n^3 with its measures against the similarity solution."""
     from tests.sedov_exact import Sedov
@@ -560,6 +657,11 @@ def run_ours(args, rank, world):
                           "note": "fluxes at 9 points per face (26 per cell), Simpson weights"}
             pq.close()
 
+    # ---- an adaptive forest of three refinement levels
+    forest = {}
+    if not args.no_forest:
+        forest = forest_forms(args.steps, args.warmup, stream)
+
     # ---- the Sedov point explosion (the paper's scenario) on the 64^3 cube
     sedov = {}
     if not args.no_sedov:
@@ -700,6 +802,7 @@ def run_ours(args, rank, world):
                               "note": "three fused SSP-RK3 stages; value = stage cell-updates/s"},
             "mixed_rk3_step": {"value": 3 * cells * world / (ms_rkmx * 1e-3), "ms": ms_rkmx},
             **quad,
+            **forest,
             **sedov,
             "mixed_per_subgrid": {"value": cells * world / (ms_psmx * 1e-3), "ms": ms_psmx,
                                   "streams": args.streams, "launches": batch.n},
@@ -753,6 +856,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-sedov", action="store_true", help="skip the Sedov blast runs")
+    ap.add_argument("--no-forest", action="store_true", help="skip the adaptive-forest forms")
     ap.add_argument("--no-quad26", action="store_true", help="skip the 26-point quadrature forms")
     ap.add_argument("--rate", type=float, default=20000.0, help="serving arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
@@ -775,7 +879,7 @@ def main():
     if world > 1:
         # replicas: the scaling run times the headline and the forms beside it;
         # the serving, Sedov and 26-point runs stay single-GPU extras
-        args.no_serving = args.no_sedov = args.no_quad26 = True
+        args.no_serving = args.no_sedov = args.no_quad26 = args.no_forest = True
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

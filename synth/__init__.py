@@ -420,3 +420,31 @@ def smooth_forest_state(leaves, nb0, N, nf=11, seed=BASE_SEED, gamma=GAMMA):
         X = np.moveaxis(rng.dirichlet(np.ones(nf - 6), size=rho.shape), -1, 0)
     U = conserved_from_states(rho, v[0], v[1], v[2], p, X, gamma)  # [nf][n][N][N][N]
     return np.ascontiguousarray(np.moveaxis(U, 0, 1)), 1.0 / (nb0 * N)
+
+
+def sedov_forest(nb0=2, N=8, radii=(0.45, 0.25), nf=11, gamma=GAMMA, E=1.0, rho0=1.0, p0=1e-5,
+                 seed=BASE_SEED):
+    """The point explosion of sedov_domain on a forest refined around the
+    centre of the periodic unit cube (sphere_refine with the given radii, so
+    len(radii) levels of refinement at the centre): gas at rest, rho0, p0,
+    and the energy E added as internal energy, evenly, to the 8 finest cells
+    that touch the centre.  Returns (leaves, U [n][nf][N][N][N], dx0)."""
+    leaves = forest_leaves(nb0, len(radii), sphere_refine((0.5, 0.5, 0.5), radii), seed=seed)
+    xyz = forest_cell_centres(leaves, nb0, N)
+    n = len(leaves)
+    shp = (n, N, N, N)
+    rho = np.full(shp, rho0)
+    p = np.full(shp, p0)
+    lmax = int(leaves[:, 0].max())
+    dxf = 1.0 / ((nb0 << lmax) * N)
+    near = np.all(np.abs(xyz - 0.5) < 0.75 * dxf, axis=1) & (leaves[:, 0] == lmax)[:, None, None, None]
+    if near.sum() != 8:
+        raise ValueError("the centre is not refined to the finest level")
+    p[near] += (gamma - 1.0) * E / (8.0 * dxf ** 3)
+    X = None
+    if nf > 6:
+        x = rng_for(seed, 0xB1A57).dirichlet(np.ones(nf - 6))
+        X = np.broadcast_to(x[:, None, None, None, None], (nf - 6,) + shp).copy()
+    zero = np.zeros(shp)
+    U = conserved_from_states(rho, zero, zero, zero, p, X, gamma)
+    return leaves, np.ascontiguousarray(np.moveaxis(U, 0, 1)), 1.0 / (nb0 * N)

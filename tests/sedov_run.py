@@ -82,3 +82,36 @@ def oracle_run(n, t_end, gamma=5.0 / 3.0, cfl=0.3, mode=0, nf=11, threads=8, dts
         used.append(dt)
         k += 1
     return U, t, used
+
+
+# ------------------------------------------------------------------ forests --
+def forest_shock_measures(leaves, nb0, rho, exact, t):
+    """(R_peak, L1(rho)) of the density of a forest (rho [n][N][N][N], the
+    leaves of synth.sedov_forest): cells binned by the radius of their centre
+    from the cube's centre, averaged with volume weights; L1 volume-weighted."""
+    N = rho.shape[-1]
+    xyz = synth.forest_cell_centres(leaves, nb0, N)
+    r = np.sqrt(((xyz - 0.5) ** 2).sum(axis=1))
+    vol = (1.0 / ((nb0 << leaves[:, 0].astype(np.int64)) * N)) ** 3
+    w = np.broadcast_to(vol[:, None, None, None], r.shape)
+    rho_ex, _, _ = exact.profile(r, t)
+    dxf = 1.0 / ((nb0 << int(leaves[:, 0].max())) * N)
+    bins = np.arange(0.0, 0.5, dxf)
+    idx = np.digitize(r.ravel(), bins)
+    cnt = np.bincount(idx, w.ravel(), minlength=len(bins) + 1)
+    prof = np.bincount(idx, (rho * w).ravel(), minlength=len(bins) + 1) / np.maximum(cnt, 1e-300)
+    rb = (np.arange(len(prof)) - 0.5) * dxf
+    L1 = float((np.abs(rho - rho_ex) * w).sum() / w.sum())
+    return float(rb[np.argmax(prof)]), L1
+
+
+def oracle_forest_steps(leaves, nb0, U, dx0, dts, gamma=5.0 / 3.0, mode=0):
+    """SSP-RK3 steps of the forest oracle along the given dt sequence."""
+    from oracle import forest as of
+
+    U = [np.asarray(u, dtype=np.float64) for u in U]
+    for dt in dts:
+        U1, _ = of.stage(leaves, nb0, U, U, 0.0, 1.0, dt, dx0, gamma, mode)
+        U2, _ = of.stage(leaves, nb0, U1, U, 0.75, 0.25, dt, dx0, gamma, mode)
+        U, _ = of.stage(leaves, nb0, U2, U, 1.0 / 3.0, 2.0 / 3.0, dt, dx0, gamma, mode)
+    return U

@@ -157,3 +157,46 @@ def test_forest_argument_checks():
                    flags=kw.get("flags", 0))
         assert ei.value.code == hydro.HYDRO_EINVAL
     fo.close()
+
+
+# ------------------------------------------------------- Sedov on a forest --
+def test_sedov_on_a_forest():
+    """The point explosion on a forest refined around the centre (levels 1
+    and 2, 64^3 cells' resolution at the centre): two steps follow the
+    forest oracle's; the run to R = 0.35 conserves mass and energy to
+    rounding across the level boundaries the shock crosses, keeps the mirror
+    symmetry, and puts the density peak within a cell of the similarity
+    solution's shock radius."""
+    from bench import sedov_forest_run
+    from tests.sedov_exact import Sedov
+    from tests.sedov_run import forest_shock_measures, oracle_forest_steps
+
+    ex = Sedov(5.0 / 3.0)
+    r2 = sedov_forest_run(prec=hydro.FP64, dts=[2e-5, 2e-5])
+    leaves, U0, dx0 = synth.sedov_forest()
+    ref = oracle_forest_steps(leaves, 2, list(U0), dx0, r2["dts"])
+    got = r2["U"].cpu().numpy()
+    for s in range(len(leaves)):
+        for f in range(U0.shape[1]):
+            assert np.abs(got[s][f] - ref[s][f]).max() <= 1e-11 * np.abs(ref[s][f]).max() + 1e-300
+    r = sedov_forest_run(prec=hydro.FP64, t_end=ex.time_for_radius(0.35))
+    U = r["U"].cpu().numpy()
+    lv = r["leaves"]
+    vol = (dx0 / (1 << lv[:, 0].astype(np.int64))) ** 3
+    tot0 = (U0.sum(axis=(2, 3, 4)) * vol[:, None]).sum(axis=0)
+    tot = (U.sum(axis=(2, 3, 4)) * vol[:, None]).sum(axis=0)
+    mag = (np.abs(U).sum(axis=(2, 3, 4)) * vol[:, None]).sum(axis=0)
+    for f in (0, 4, 5, 6, 10):
+        assert abs(tot[f] - tot0[f]) <= 1e-12 * mag[f], (f, tot[f] - tot0[f])
+    for f in (1, 2, 3):
+        assert abs(tot[f]) <= 1e-12 * mag[0]
+    # mirror x -> 1 - x maps the forest onto itself
+    key = {tuple(int(v) for v in l): s for s, l in enumerate(lv)}
+    worst = 0.0
+    for s, (L, bx, by, bz) in enumerate(lv):
+        m = key[(int(L), int((2 << int(L)) - 1 - bx), int(by), int(bz))]
+        worst = max(worst, np.abs(U[s, 0] - U[m, 0, :, :, ::-1]).max())
+    assert worst <= 1e-9 * U[:, 0].max()
+    Rp, L1 = forest_shock_measures(lv, 2, U[:, 0], ex, r["t"])
+    assert abs(Rp - ex.shock_radius(r["t"])) <= 1.0 / 32, (Rp, ex.shock_radius(r["t"]))
+    assert U[:, 0].min() > 0 and L1 < 0.5
