@@ -343,8 +343,10 @@ int hydro_forest_info(const hydro_forest_t* forest, hydro_forest_info_t* info);
 /* dU/dt (packed like U) and amax per leaf, with dx0 the cell width of
  * level 0.  hydro_forest_stage: U_out = alpha U0 + beta (U + dt dU/dt) in
  * the same launches (as hydro_domain_stage; U_out must not alias U, U0 may
- * alias U or U_out).  flags: HYDRO_F_KNP or 0 (the 26-point variant reads
- * edge ghosts and is refused on forests: HYDRO_EINVAL).  Three launches on
+ * alias U or U_out).  flags: HYDRO_F_KNP, HYDRO_F_REGISTER_LOADS (mixed form:
+ * the register-load kernel instead of the pipelined one; same results) or 0
+ * (the 26-point variant reads edge ghosts and is refused on forests:
+ * HYDRO_EINVAL).  Three launches on
  * `stream` (level transfer, tiles, flux correction); nothing is allocated.
  * The auxiliary blocks and flux registers belong to the forest, so calls on
  * one forest must be ordered (one stream, or synchronised). */

@@ -190,19 +190,24 @@ struct hydro_forest {
 
 namespace {
 
-// Launch shapes of the forest tile kernel: binary64 576 threads (the shape
-// the autotuner picks for sub-grid batches); mixed the register-load kernel
-// of 256 threads.
-constexpr int kF64Threads = 576, kMixThreads = 256, kLch = 64;
+// Forest tile kernels (the shapes the autotuner picks for sub-grid batches):
+// 0 binary64, register loads, 576 threads; 1 mixed, pipelined (576 threads);
+// 2 mixed, register loads, 256 threads (HYDRO_F_REGISTER_LOADS).
+constexpr int kLch = 64;
+constexpr int kThreads[3] = {576, hydro_host::kPipeThreads, 256};
+constexpr int kKinds[3] = {hydro_host::kKindTiles, hydro_host::kKindPipe, hydro_host::kKindTiles};
 
-void* forest_func(hydro_precision_t prec) {
-  return prec == HYDRO_FP64 ? (void*)&hydro_dev::rhs_forest_kernel<0, kF64Threads, 1, 1>
-                            : (void*)&hydro_dev::rhs_forest_kernel<1, kMixThreads, 1, 4>;
+void* forest_func(int k) {
+  switch (k) {
+    case 0: return (void*)&hydro_dev::rhs_forest_kernel<0, 576, 1, 1>;
+    case 1: return (void*)&hydro_dev::rhs_forest_pipe_kernel<hydro_host::kPipeThreads>;
+    default: return (void*)&hydro_dev::rhs_forest_kernel<1, 256, 1, 4>;
+  }
 }
 
 struct ForestDev {
   bool ready = false;
-  int n_sm = 0, occ[2] = {0, 0};
+  int n_sm = 0, occ[3] = {0, 0, 0};
 };
 ForestDev g_fdev[64];
 std::mutex g_fmu;
@@ -217,14 +222,13 @@ int forest_setup(int dev, ForestDev** out) {
     if ((e = cudaDeviceGetAttribute(&D.n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
       return hydro_host::cuda_fail(e, "cudaDeviceGetAttribute");
-    for (int m = 0; m < 2; m++) {
+    for (int m = 0; m < 3; m++) {
       hydro_precision_t prec = m == 0 ? HYDRO_FP64 : HYDRO_FP32_FLUX_FP64_ACC;
-      int smem = hydro_host::smem_bytes(prec, HYDRO_MAX_FIELDS, kLch, hydro_host::kKindTiles);
-      if ((e = cudaFuncSetAttribute(forest_func(prec), cudaFuncAttributeMaxDynamicSharedMemorySize,
+      int smem = hydro_host::smem_bytes(prec, HYDRO_MAX_FIELDS, kLch, kKinds[m]);
+      if ((e = cudaFuncSetAttribute(forest_func(m), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     optin - 1024)) != cudaSuccess)
         return hydro_host::cuda_fail(e, "cudaFuncSetAttribute");
-      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&D.occ[m], forest_func(prec),
-                                                             m == 0 ? kF64Threads : kMixThreads, smem)) !=
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&D.occ[m], forest_func(m), kThreads[m], smem)) !=
           cudaSuccess)
         return hydro_host::cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
       if (D.occ[m] < 1) D.occ[m] = 1;
@@ -366,7 +370,7 @@ int forest_launch(hydro_forest* fo, const double* U, const double* U0, double al
                   int stage, double dx0, double gamma, double* out, double* amax, hydro_precision_t prec,
                   void* stream, uint32_t flags) {
   if (!fo || !U || !out || !amax || (stage && !U0)) return HYDRO_EINVAL;
-  if (flags & ~(uint32_t)HYDRO_F_KNP) return HYDRO_EINVAL;
+  if (flags & ~(uint32_t)(HYDRO_F_KNP | HYDRO_F_REGISTER_LOADS)) return HYDRO_EINVAL;
   if (!(dx0 > 0.0) || !std::isfinite(dx0) || !(gamma > 1.0) || !std::isfinite(gamma)) return HYDRO_EINVAL;
   if (prec != HYDRO_FP64 && prec != HYDRO_FP32_FLUX_FP64_ACC) return HYDRO_EINVAL;
   if (stage && (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(dt))) return HYDRO_EINVAL;
@@ -406,15 +410,15 @@ int forest_launch(hydro_forest* fo, const double* U, const double* U0, double al
   const bool pow2 = std::frexp(dx0, &ex2) == 0.5 && ex2 > -120 && ex2 < 120;
   hydro_dev::ForestTiles ft{U, fo->aux, fo->links, fo->reg, fo->nl, N, F, tpe, 1.0 / dx0, (short)(pow2 ? 2 : 0)};
   hydro_dev::StageArgs sa{U, stage ? U0 : U, alpha, beta, dt, stage};
-  const int m = prec == HYDRO_FP64 ? 0 : 1;
-  const int threads = m == 0 ? kF64Threads : kMixThreads;
+  const int m = prec == HYDRO_FP64 ? 0 : ((flags & HYDRO_F_REGISTER_LOADS) ? 2 : 1);
+  const int threads = kThreads[m];
   int nt = (int)n_tiles, lch = kLch, ws = 1, scheme = (flags & HYDRO_F_KNP) ? 1 : 0;
   const long long g64 = (long long)D->occ[m] * D->n_sm;
   const int grid = (int)(n_tiles < g64 ? n_tiles : g64);
-  size_t smem = (size_t)hydro_host::smem_bytes(prec, F, lch, hydro_host::kKindTiles);
+  size_t smem = (size_t)hydro_host::smem_bytes(prec, F, lch, kKinds[m]);
   void* args[] = {(void*)&ft, (void*)&nt, (void*)&lch, (void*)&out, (void*)&amax, (void*)&status,
                   (void*)&gamma, (void*)&ws, (void*)&scheme, (void*)&sa};
-  if ((e = cudaLaunchKernel(forest_func(prec), dim3(grid), dim3(threads), args, smem, st)) != cudaSuccess)
+  if ((e = cudaLaunchKernel(forest_func(m), dim3(grid), dim3(threads), args, smem, st)) != cudaSuccess)
     return hydro_host::cuda_fail(e, "forest tile launch");
   // 3. flux correction
   if (fo->n_rf > 0) {

@@ -1338,14 +1338,18 @@ __device__ __forceinline__ int pipe_offset(const Tile& tile, const DomainPos& dp
   }
 }
 
-// Issue the copies of fields f0 .. f0+nf-1 of the tile's read region into S.
-template <bool DOMAIN>
-__device__ __forceinline__ void pipe_issue(const Tile& tile, const SlotXYZ& sx, double* S, int f0, int nf) {
+// Issue the copies of fields f0 .. f0+nf-1 of the tile's read region into S
+// (DOM as in tile_loop; a forest locates cells through fetch.loc).
+template <int DOM, class Fetch>
+__device__ __forceinline__ void pipe_issue(const Fetch& fetch, const Tile& tile, const SlotXYZ& sx, double* S,
+                                           int f0, int nf) {
   const int N = tile.N;
   const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
-  const long long plane = DOMAIN ? (long long)N * N * N : (long long)tile.G * tile.G * tile.G;
+  const long long plane = DOM ? (long long)N * N * N : (long long)tile.G * tile.G * tile.G;
   DomainPos dp;
-  if constexpr (DOMAIN) dp.init(tile.sub, tile.pad[0], N, tile.F);
+  if constexpr (DOM == 1) dp.init(tile.sub, tile.pad[0], N, tile.F);
+  ForestLoc fl;
+  if constexpr (DOM == 2) fl = fetch.loc(tile);
   const int tid = threadIdx.x;
 #pragma unroll
   for (int k = 0; k < PSPT; k++) {
@@ -1353,9 +1357,15 @@ __device__ __forceinline__ void pipe_issue(const Tile& tile, const SlotXYZ& sx, 
     if (s >= STAR) continue;
     int x, y, z;
     sx.get(k, x, y, z);
-    int off = pipe_offset<DOMAIN>(tile, dp, x, y, z, ex, ey, ez);
-    if (off < 0) continue;
-    const double* src = tile.U + (long long)f0 * plane + off;
+    const double* src;
+    if constexpr (DOM == 2) {
+      if (!pipe_valid(x, y, z, ex, ey, ez)) continue;
+      src = fl.ptr(tile.ox + x, tile.oy + y, tile.oz + z) + (long long)f0 * plane;
+    } else {
+      int off = pipe_offset<DOM == 1>(tile, dp, x, y, z, ex, ey, ez);
+      if (off < 0) continue;
+      src = tile.U + (long long)f0 * plane + off;
+    }
 #pragma unroll
     for (int f = 0; f < 6; f++)
       if (f < nf) cp_async8(S + f * STAR + s, src + f * plane);
@@ -1363,7 +1373,7 @@ __device__ __forceinline__ void pipe_issue(const Tile& tile, const SlotXYZ& sx, 
   cp_async_commit();
 }
 
-template <class Fetch, bool DOMAIN>
+template <class Fetch, int DOM>
 __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, double* __restrict__ out,
                                                double* __restrict__ amax_out, Status* __restrict__ status,
                                                double gamma_d, int write_status, bool knp,
@@ -1388,7 +1398,7 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
   sx.init(tid);
 
   int t = blockIdx.x;
-  if (t < n_tiles) pipe_issue<DOMAIN>(fetch(t), sx, S, 0, 6);
+  if (t < n_tiles) pipe_issue<DOM>(fetch, fetch(t), sx, S, 0, 6);
   for (; t < n_tiles; t += gridDim.x) {
     const Tile tile = fetch(t);
     const int F = tile.F, N = tile.N, nsp = F - 6;
@@ -1424,8 +1434,8 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
     }
     bad = __syncthreads_or(bad);
     // the staging buffer is free: species of this tile, or the next tile
-    if (nsp > 0) pipe_issue<DOMAIN>(tile, sx, S, 6, nsp);
-    else if (tn < n_tiles) pipe_issue<DOMAIN>(fetch(tn), sx, S, 0, 6);
+    if (nsp > 0) pipe_issue<DOM>(fetch, tile, sx, S, 6, nsp);
+    else if (tn < n_tiles) pipe_issue<DOM>(fetch, fetch(tn), sx, S, 0, 6);
 
     float amax = 0.0f;
     Acc acc[1][3];
@@ -1476,8 +1486,13 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
         }
       }
     };
+    if constexpr (DOM == 2) {
+      const ForestCapture cap = fetch.capture(tile, 0);
+#pragma unroll 1
+      for (int d = 0; d < 3; d++) cap.template faces<1, PNT>(qs(d, 0, 0), FS, NLN, 0, 3, d, ex, ey, ez);
+    }
     diff_pass(3);
-    store_group<1, PNT, DOMAIN>(out, tile, ex, ey, ez, 0, 6, acc, stage);
+    store_group<1, PNT, (DOM != 0)>(out, tile, ex, ey, ez, 0, 6, acc, stage);
 
     if (nsp > 0) {
       const int npair = (nsp + 1) / 2;
@@ -1507,7 +1522,7 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
           if (j < npair) W[j * STAR + s] = make_float2(xs[2 * j], xs[2 * j + 1]);
       }
       bad = __syncthreads_or(bad);
-      if (tn < n_tiles) pipe_issue<DOMAIN>(fetch(tn), sx, S, 0, 6);
+      if (tn < n_tiles) pipe_issue<DOM>(fetch, fetch(tn), sx, S, 0, 6);
       // ---- A2 species
       {
         const int d = tid / (3 * NLN), rem = tid - d * 3 * NLN, j = rem / NLN, l = rem - j * NLN;
@@ -1532,8 +1547,13 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
         }
       }
       __syncthreads();
+      if constexpr (DOM == 2) {
+        const ForestCapture cap = fetch.capture(tile, 6);
+#pragma unroll 1
+        for (int d = 0; d < 3; d++) cap.template faces<1, PNT>(qs(d, 0, 0), FS, NLN, 0, npair, d, ex, ey, ez);
+      }
       diff_pass(npair);
-      store_group<1, PNT, DOMAIN>(out, tile, ex, ey, ez, 6, nsp, acc, stage);
+      store_group<1, PNT, (DOM != 0)>(out, tile, ex, ey, ez, 6, nsp, acc, stage);
     }
     if (bad && tid == 0 && write_status) {
       atomicOr(&status->flags, 1u);
@@ -1571,7 +1591,7 @@ rhs_tiles_pipe_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int
   (void)Fmax;
   (void)lch;
   (void)prefetch;
-  tile_loop_pipe<TileList, false>(TileList{tiles}, n_tiles, out, amax_out, status, gamma_d, write_status,
+  tile_loop_pipe<TileList, 0>(TileList{tiles}, n_tiles, out, amax_out, status, gamma_d, write_status,
                                   scheme == 1, StageArgs{nullptr, nullptr, 0.0, 0.0, 0.0, 0});
 }
 
@@ -1630,8 +1650,19 @@ rhs_domain_pipe_kernel(DomainTiles dom, int n_tiles, int lch, double* __restrict
                        int write_status, int scheme, StageArgs stage) {
   static_assert(NT == PNT, "the pipelined kernel runs PNT threads");
   (void)lch;
-  tile_loop_pipe<DomainTiles, true>(dom, n_tiles, out, amax_out, status, gamma_d, write_status, scheme == 1,
+  tile_loop_pipe<DomainTiles, 1>(dom, n_tiles, out, amax_out, status, gamma_d, write_status, scheme == 1,
                                     stage);
+}
+
+// Forest tiles, pipelined mixed kernel.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1)
+rhs_forest_pipe_kernel(ForestTiles ft, int n_tiles, int lch, double* __restrict__ out,
+                       double* __restrict__ amax_out, Status* __restrict__ status, double gamma_d,
+                       int write_status, int scheme, StageArgs stage) {
+  static_assert(NT == PNT, "the pipelined kernel runs PNT threads");
+  (void)lch;
+  tile_loop_pipe<ForestTiles, 2>(ft, n_tiles, out, amax_out, status, gamma_d, write_status, scheme == 1, stage);
 }
 
 }  // namespace hydro_dev

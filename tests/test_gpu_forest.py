@@ -49,7 +49,8 @@ def _check(prec, got, gam, ref, ram, U, dxs):
 
 
 @pytest.mark.parametrize("prec", [hydro.FP64, MX])
-@pytest.mark.parametrize("N,nb0,seed,prob,nf", [(8, 2, 7, 0.25, 11), (8, 2, 4, 0.25, 6), (16, 1, 3, 0.6, 7)])
+@pytest.mark.parametrize("N,nb0,seed,prob,nf", [(8, 2, 7, 0.25, 11), (8, 2, 4, 0.25, 6), (16, 1, 3, 0.6, 7),
+                                                (12, 1, 3, 0.6, 10), (6, 2, 4, 0.25, 8)])
 def test_forest_rhs_matches_oracle(prec, N, nb0, seed, prob, nf):
     lv = _forest(nb0, seed, prob)
     assert len(set(lv[:, 0])) >= 2
@@ -60,6 +61,25 @@ def test_forest_rhs_matches_oracle(prec, N, nb0, seed, prob, nf):
     kind, _ = hydro.forest_links(lv, nb0, N)
     assert info["n_level_faces"] == sum(k != 0 for row in kind for k in row) > 0
     assert info["n_reflux_leaves"] == sum(any(k == 1 for k in row) for row in kind) > 0
+
+
+@pytest.mark.parametrize("N,nb0,seed,prob", [(12, 1, 3, 0.6), (8, 2, 7, 0.25)])
+def test_mixed_forest_kernel_families_bitwise(N, nb0, seed, prob):
+    """The pipelined mixed kernel (default) and the register-load one give
+    the same bits on forests, partial tiles included, for the RHS and a
+    stage."""
+    lv = _forest(nb0, seed, prob)
+    U, dx0 = synth.smooth_forest_state(lv, nb0, N, nf=11, seed=47)
+    a = _run(lv, nb0, U, dx0, MX)
+    b = _run(lv, nb0, U, dx0, MX, flags=hydro.F_REGISTER_LOADS)
+    for x, y in zip(a[0], b[0]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a[1], b[1])
+    st = (U * 0.5, 0.75, 0.25, 1e-3)
+    a = _run(lv, nb0, U, dx0, MX, stage=st, flags=hydro.F_KNP)
+    b = _run(lv, nb0, U, dx0, MX, stage=st, flags=hydro.F_KNP | hydro.F_REGISTER_LOADS)
+    for x, y in zip(a[0], b[0]):
+        assert np.array_equal(x, y)
 
 
 def test_forest_one_sided_flux():
@@ -142,6 +162,37 @@ def test_conservation_across_levels(prec):
     tot = sum(got[s].sum(axis=(1, 2, 3)) * vol[s] for s in range(len(lv)))
     mag = sum(np.abs(got[s]).sum(axis=(1, 2, 3)) * vol[s] for s in range(len(lv)))
     assert np.all(np.abs(tot) <= (1e-14 if prec == hydro.FP64 else 1e-12) * mag), tot / mag
+
+
+def test_forest_rk3_step_in_a_cuda_graph():
+    """The forest entry points allocate nothing after their first call, so a
+    whole SSP-RK3 step (9 launches) records into a CUDA graph; its replay
+    gives the bits of the direct calls."""
+    lv = _forest(2, 7, 0.25)
+    U_h, dx0 = synth.smooth_forest_state(lv, 2, 8, nf=11, seed=46)
+    fo = hydro.Forest(lv, 2, 8, 11)
+    U = torch.from_numpy(U_h).cuda()
+    W1, W2, W3 = torch.empty_like(U), torch.empty_like(U), torch.empty_like(U)
+    am = torch.empty((3, len(lv)), dtype=torch.float64, device="cuda")
+    st = torch.cuda.Stream()
+
+    def step(out):
+        fo.stage(U, U, 0.0, 1.0, 1e-4, dx0, W1, am[0], stream=st)
+        fo.stage(W1, U, 0.75, 0.25, 1e-4, dx0, W2, am[1], stream=st)
+        fo.stage(W2, U, 1.0 / 3.0, 2.0 / 3.0, 1e-4, dx0, out, am[2], stream=st)
+
+    with torch.cuda.stream(st):
+        step(W3)  # first calls: kernel attributes, status word
+        torch.cuda.synchronize()
+        ref, ref_am = W3.clone(), am.clone()
+        W3.zero_()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            step(W3)
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(W3, ref) and torch.equal(am, ref_am)
+    fo.close()
 
 
 def test_forest_argument_checks():
