@@ -23,9 +23,11 @@ readings taken here:
    eight children (restriction), added in the order k = i + 2 j + 4 k of the
    child offsets and multiplied by 1/8.
 2. Each leaf's RHS is the single-block oracle on its ghosted block (face-
-   centre scheme, Kurganov-Tadmor or Kurganov-Noelle-Petrova flux, binary64
-   or mixed).  The 26-point variant reads edge ghosts and is not defined on
-   forests here.
+   centre scheme or the 26-point variant, Kurganov-Tadmor or Kurganov-
+   Noelle-Petrova flux, binary64 or mixed).  The face-centre scheme reads
+   the face ghost slabs only; the 26-point variant also reads edge and
+   corner ghosts (every cell with each coordinate in [-3, N+2] and at most
+   one of them at -3 or N+2), filled by the same rule.
 3. Flux correction.  Where a level-L leaf meets four level-(L+1) leaves
    across a face, the flux through each coarse cell face is replaced by the
    area mean of the four fine fluxes through it (added in the order (0,0),
@@ -96,10 +98,11 @@ def cell_average(forest, U, L, g):
     return acc * 0.125
 
 
-def ghosted_block(forest, U, s, ghost=3):
-    """Leaf s with its face ghost slabs (ghost layers deep) filled by reading
-    1; edge and corner ghosts, which the face-centre scheme never reads, are
-    zero.  Returns [nf][G][G][G]."""
+def ghosted_block(forest, U, s, ghost=3, quad26=False):
+    """Leaf s with its ghost cells filled by reading 1: the face slabs
+    (ghost layers deep) and, with quad26, the edge and corner cells the
+    26-point variant reads; other ghost cells are zero.  Returns
+    [nf][G][G][G]."""
     N = forest.N
     L = int(forest.leaves[s, 0])
     b = forest.leaves[s, 1:]
@@ -107,6 +110,19 @@ def ghosted_block(forest, U, s, ghost=3):
     G = N + 2 * ghost
     out = np.zeros((nf, G, G, G))
     out[:, ghost:ghost + N, ghost:ghost + N, ghost:ghost + N] = U[s]
+    if quad26:
+        r = range(-3, N + 3)
+        for z in r:
+            for y in r:
+                for x in r:
+                    c = (x, y, z)
+                    if all(0 <= v < N for v in c):
+                        continue
+                    if sum(v in (-3, N + 2) for v in c) > 1:
+                        continue
+                    g = tuple(int(b[e]) * N + c[e] for e in range(3))
+                    out[:, z + ghost, y + ghost, x + ghost] = cell_average(forest, U, L, g)
+        return out
     for d in range(3):
         ta, tb = _TANG[d]
         for side in (0, 1):
@@ -134,9 +150,7 @@ def _face_flux(faces, d, c, i):
 def rhs(leaves, nb0, U, dx0, gamma=5.0 / 3.0, mode=0):
     """dU/dt of every leaf (list of [nf][N][N][N]) and amax per leaf, with
     the flux correction of reading 3.  mode: the oracle's mode bits (binary32
-    reconstruction and flux, one-sided flux); the 26-point bit is refused."""
-    if mode & 4:
-        raise ValueError("the 26-point variant is not defined on forests")
+    reconstruction and flux, one-sided flux, the 26-point variant)."""
     U = [np.asarray(u, dtype=np.float64) for u in U]
     N = U[0].shape[-1]
     fo = Forest(leaves, nb0, N)
@@ -144,7 +158,8 @@ def rhs(leaves, nb0, U, dx0, gamma=5.0 / 3.0, mode=0):
     outs, amax, faces = [], np.zeros(n), []
     for s in range(n):
         dx = dx0 / (1 << int(fo.leaves[s, 0]))
-        o, a, flags, fc = rhs_block(ghosted_block(fo, U, s), 3, gamma, dx, mode, faces=True)
+        o, a, flags, fc = rhs_block(ghosted_block(fo, U, s, quad26=bool(mode & 4)), 3, gamma, dx, mode,
+                                    faces=True)
         if flags:
             raise ValueError("oracle flagged leaf %d (flags %d)" % (s, flags))
         outs.append(o)

@@ -292,7 +292,7 @@ def _leaf_hash(seed, level, bx, by, bz):
     return (h >> 11) / float(1 << 53)
 
 
-def forest_leaves(nb0, max_level, refine, seed=BASE_SEED, shuffle=True):
+def forest_leaves(nb0, max_level, refine, seed=BASE_SEED, shuffle=True, balance="face"):
     """Leaves of a 2:1 face-balanced octree forest over the periodic unit cube
     cut into nb0^3 root blocks.
 
@@ -300,7 +300,8 @@ def forest_leaves(nb0, max_level, refine, seed=BASE_SEED, shuffle=True):
     cube coordinates) is split; blocks at max_level are never split.  After
     that, any leaf with a face neighbour two or more levels finer is split
     until none is left (periodic neighbours included), so face neighbours
-    differ by at most one level.  Returns an int32 array [n][4] of
+    differ by at most one level; balance="full" extends this to the edge and
+    corner neighbours (all 26).  Returns an int32 array [n][4] of
     (level, bx, by, bz), block coordinates at the leaf's level in
     [0, nb0 2^level); shuffled by the seed unless shuffle is False (then
     sorted by level, bz, by, bx)."""
@@ -322,6 +323,8 @@ def forest_leaves(nb0, max_level, refine, seed=BASE_SEED, shuffle=True):
                 return key
         return None
 
+    offsets = [o for o in ((i, j, k) for k in (-1, 0, 1) for j in (-1, 0, 1) for i in (-1, 0, 1))
+               if (sum(map(abs, o)) == 1 if balance == "face" else any(o))]
     changed = True
     while changed:
         changed = False
@@ -330,19 +333,17 @@ def forest_leaves(nb0, max_level, refine, seed=BASE_SEED, shuffle=True):
                 continue
             L, b = leaf[0], leaf[1:]
             m = nb0 << L
-            for d in range(3):
-                for step in (-1, 1):
-                    q = list(b)
-                    q[d] = (q[d] + step) % m
-                    c = covering(L, q)
-                    if c is not None and c[0] < L - 1:
-                        leaves.discard(c)
-                        cl, cb = c[0], c[1:]
-                        for k in (0, 1):
-                            for j in (0, 1):
-                                for i in (0, 1):
-                                    leaves.add((cl + 1, 2 * cb[0] + i, 2 * cb[1] + j, 2 * cb[2] + k))
-                        changed = True
+            for o in offsets:
+                q = [(b[e] + o[e]) % m for e in range(3)]
+                c = covering(L, q)
+                if c is not None and c[0] < L - 1:
+                    leaves.discard(c)
+                    cl, cb = c[0], c[1:]
+                    for k in (0, 1):
+                        for j in (0, 1):
+                            for i in (0, 1):
+                                leaves.add((cl + 1, 2 * cb[0] + i, 2 * cb[1] + j, 2 * cb[2] + k))
+                    changed = True
     out = np.array(sorted(leaves, key=lambda t: (t[0], t[3], t[2], t[1])), dtype=np.int32).reshape(-1, 4)
     if shuffle:
         out = out[rng_for(seed, 0xF0CE57).permutation(len(out))]

@@ -181,8 +181,105 @@ def test_unbalanced_forest_is_refused():
         of.rhs(lv, 2, list(U), dx0)
 
 
-def test_26_point_variant_refused():
-    lv = _forest(7, 0.0)
-    U, dx0 = synth.smooth_forest_state(lv, NB0, N, nf=6)
-    with pytest.raises(ValueError):
-        of.rhs(lv, NB0, list(U), dx0, mode=oracle.QUAD26)
+# ----------------------------------------------------- 26-point variant --
+def _full_forest():
+    """Three levels, 2:1 balanced across faces, edges and corners (the
+    26-point variant reads edge and corner ghosts): 90 leaves."""
+    lv = synth.forest_leaves(3, 2, synth.random_refine(1, 0.1), seed=1, balance="full")
+    assert np.bincount(lv[:, 0]).tolist() == [19, 63, 8]
+    return lv
+
+
+def test_quad26_one_level_forest_is_the_periodic_domain():
+    nb0 = 2
+    lv = synth.forest_leaves(nb0, 0, lambda *a: False, seed=5)
+    glob = synth.plain_domain(seed=19, n=nb0 * N, nf=6)
+    blocks = synth.gather_blocks(glob, N, blocks=[tuple(l[1:]) for l in lv])
+    U = [b[:, 3:-3, 3:-3, 3:-3] for b in blocks]
+    dx0 = 1.0 / (nb0 * N)
+    got, gam = of.rhs(lv, nb0, U, dx0, mode=oracle.QUAD26)
+    for s in range(len(lv)):
+        ref, ra, _ = oracle.rhs_block(blocks[s], 3, 5.0 / 3.0, dx0, oracle.QUAD26)
+        assert np.array_equal(got[s], ref) and gam[s] == ra
+
+
+def test_quad26_constant_state_and_conservation():
+    lv = _full_forest()
+    n = len(lv)
+    shp = (n, N, N, N)
+    Uc = synth.conserved_from_states(np.full(shp, 1.1), np.full(shp, 0.3), np.full(shp, 0.1),
+                                     np.full(shp, -0.2), np.full(shp, 0.7), None)
+    got, _ = of.rhs(lv, 3, list(np.moveaxis(Uc, 0, 1)), 1.0 / 24, mode=oracle.QUAD26)
+    for o in got:
+        assert np.all(o == 0.0)
+    U, dx0 = synth.smooth_forest_state(lv, 3, N, nf=7, seed=23)
+    for mode in (oracle.QUAD26, oracle.QUAD26 | oracle.MODE_MIXED):
+        got, _ = of.rhs(lv, 3, list(U), dx0, mode=mode)
+        vol = (dx0 / (1 << lv[:, 0].astype(np.int64))) ** 3
+        tot = sum(got[s].sum(axis=(1, 2, 3)) * vol[s] for s in range(n))
+        mag = sum(np.abs(got[s]).sum(axis=(1, 2, 3)) * vol[s] for s in range(n))
+        assert np.all(np.abs(tot) <= 1e-14 * mag)
+
+
+def test_quad26_linear_field_edge_and_corner_ghosts():
+    """Edge and corner ghosts of a linear field follow the same closed form
+    as the face ghosts (field at the source cell's centre, or at the ghost's
+    own centre when finer leaves cover it)."""
+    lv = _full_forest()
+    nb0 = 3
+    coef = np.array([-0.4, 0.9, 1.7])
+    xyz = synth.forest_cell_centres(lv, nb0, N)
+    U = [np.stack([2.0 + np.tensordot(coef, xyz[s], axes=1)] * 6) for s in range(len(lv))]
+    fo = of.Forest(lv, nb0, N)
+    seen = {"same": 0, "coarse": 0, "fine": 0}
+    for s in range(0, len(lv), 7):
+        L, b = int(lv[s, 0]), lv[s, 1:]
+        gb = of.ghosted_block(fo, U, s, quad26=True)
+        w = 1.0 / ((nb0 << L) * N)
+        for c in [(-1, -1, 3), (-2, N + 1, -1), (N, -1, N + 1), (N + 1, N + 1, 0), (-3, -2, -1),
+                  (4, N, N + 2), (-1, N, N)]:
+            outside = sum(not (0 <= v < N) for v in c)
+            assert outside >= 2
+            centre = [((b[e] * N + c[e] + 0.5) * w) % 1.0 for e in range(3)]
+            src = _contains(lv, nb0, centre)
+            Ls = int(lv[src, 0])
+            if Ls <= L:
+                ws = 1.0 / ((nb0 << Ls) * N)
+                at = [(np.floor(x / ws) + 0.5) * ws for x in centre]
+                seen["same" if Ls == L else "coarse"] += 1
+            else:
+                at = centre
+                seen["fine"] += 1
+            got = gb[0, c[2] + 3, c[1] + 3, c[0] + 3]
+            assert got == pytest.approx(2.0 + coef @ np.array(at), rel=0, abs=1e-14)
+    assert min(seen.values()) > 0, seen
+
+
+def test_quad26_mirror_symmetry():
+    lv = _full_forest()
+    U, dx0 = synth.smooth_forest_state(lv, 3, N, nf=6, seed=24)
+    got, gam = of.rhs(lv, 3, list(U), dx0, mode=oracle.QUAD26)
+    mv = lv.copy()
+    mv[:, 2] = (3 << lv[:, 0]) - 1 - lv[:, 2]   # y -> 1 - y
+    MU = U[:, :, :, ::-1, :].copy()
+    MU[:, 2] *= -1
+    mg, mgam = of.rhs(mv, 3, list(MU), dx0, mode=oracle.QUAD26)
+    for s in range(len(lv)):
+        back = mg[s][:, :, ::-1, :].copy()
+        back[2] *= -1
+        scale = np.abs(got[s]).max(axis=(1, 2, 3), keepdims=True)
+        assert np.all(np.abs(back - got[s]) <= 1e-13 * scale)
+    assert np.allclose(mgam, gam, rtol=1e-14, atol=0)
+
+
+def test_full_balance_generator():
+    lv = _full_forest()
+    lmax = 2
+    lo, w = _boxes(lv, 3, lmax)
+    M = 3 << lmax
+    owner = np.zeros((M, M, M), dtype=np.int64)
+    for s, ((x, y, z), ww) in enumerate(zip(lo, w)):
+        owner[z:z + ww, y:y + ww, x:x + ww] = s
+    for o in [(i, j, k) for k in (-1, 0, 1) for j in (-1, 0, 1) for i in (-1, 0, 1) if (i, j, k) != (0, 0, 0)]:
+        nb = np.roll(owner, shift=(-o[2], -o[1], -o[0]), axis=(0, 1, 2))
+        assert np.abs(lv[owner, 0] - lv[nb, 0]).max() <= 1
