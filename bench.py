@@ -419,7 +419,7 @@ def forest_forms(steps, warmup, stream, nb0=16, radii=(0.35, 0.2), N=8, nf=11, g
 
     import paper_2210_06438_gb300 as hydro
 
-    leaves = synth.forest_leaves(nb0, len(radii), synth.sphere_refine((0.5, 0.5, 0.5), radii))
+    leaves = synth.forest_leaves(nb0, len(radii), synth.sphere_refine((0.5, 0.5, 0.5), radii), balance="full")
     U_h, dx0 = synth.smooth_forest_state(leaves, nb0, N, nf=nf)
     U = torch.from_numpy(U_h).cuda()
     del U_h
@@ -448,6 +448,16 @@ def forest_forms(steps, warmup, stream, nb0=16, radii=(0.35, 0.2), N=8, nf=11, g
     ms = time_steps(lambda: rk3(hydro.FP64), max(1, steps // 2), 1, stream)
     res["fp64_forest_rk3_step"] = {"value": 3 * cells / (ms * 1e-3), "ms": ms,
                                    "note": "three forest stages; value = stage cell-updates/s"}
+    if fo.info()["quad26"]:
+        for name, prec in (("fp64_forest_quad26", hydro.FP64), ("mixed_forest_quad26", hydro.FP32_FLUX_FP64_ACC)):
+            ms = time_steps(lambda: fo.rhs(U, dx0, out, am, gamma=gamma, prec=prec, stream=stream,
+                                           flags=hydro.F_QUAD26), max(1, steps // 3), 1, stream)
+            w = (out * vol[:, None, None, None, None]).sum(dim=(0, 2, 3, 4))
+            a = (out.abs() * vol[:, None, None, None, None]).sum(dim=(0, 2, 3, 4))
+            res[name] = {"value": cells / (ms * 1e-3), "ms": ms,
+                         "conservation_drift": float((w / a.clamp_min(1e-300)).abs().max()),
+                         "note": "the 26-point variant: gather of every leaf's ghosted block, "
+                                 "26-point tiles, flux correction"}
     info = fo.info()
     fo.close()
     levels = np.bincount(leaves[:, 0]).tolist()
@@ -455,7 +465,8 @@ def forest_forms(steps, warmup, stream, nb0=16, radii=(0.35, 0.2), N=8, nf=11, g
         "leaves": n, "leaves_by_level": levels, "cells": cells, "N": N, "fields": nf, "nb0": nb0,
         "refine_radii": list(radii), "level_faces": info["n_level_faces"],
         "reflux_leaves": info["n_reflux_leaves"], "forest_device_bytes": info["device_bytes"],
-        "note": "sphere refinement around the centre, 2:1 balanced, periodic; smooth random fields"}
+        "note": "sphere refinement around the centre, 2:1 balanced across faces, edges and corners, "
+                "periodic; smooth random fields"}
     return res
 
 

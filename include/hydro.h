@@ -317,7 +317,8 @@ typedef struct {
   int32_t max_level;
   int32_t n_level_faces;    /* leaf faces towards another level (auxiliary blocks) */
   int32_t n_reflux_leaves;  /* leaves with at least one finer face neighbour */
-  int32_t pad;
+  int32_t quad26;           /* 1 if edge and corner neighbours also differ by at most one
+                               level, so that HYDRO_F_QUAD26 is accepted */
   int64_t device_bytes;     /* tables, auxiliary blocks and flux registers */
 } hydro_forest_info_t;
 
@@ -344,12 +345,18 @@ int hydro_forest_info(const hydro_forest_t* forest, hydro_forest_info_t* info);
  * level 0.  hydro_forest_stage: U_out = alpha U0 + beta (U + dt dU/dt) in
  * the same launches (as hydro_domain_stage; U_out must not alias U, U0 may
  * alias U or U_out).  flags: HYDRO_F_KNP, HYDRO_F_REGISTER_LOADS (mixed form:
- * the register-load kernel instead of the pipelined one; same results) or 0
- * (the 26-point variant reads edge ghosts and is refused on forests:
- * HYDRO_EINVAL).  Three launches on
- * `stream` (level transfer, tiles, flux correction); nothing is allocated.
- * The auxiliary blocks and flux registers belong to the forest, so calls on
- * one forest must be ordered (one stream, or synchronised). */
+ * the register-load kernel instead of the pipelined one; same results),
+ * HYDRO_F_QUAD26 (the 26-point variant; its diagonal lines read edge and
+ * corner ghosts, filled by the same rule from the 26 neighbours: accepted
+ * only if those differ from every leaf by at most one level too, see
+ * hydro_forest_info_t.quad26; HYDRO_EINVAL otherwise) or 0.  Three launches
+ * on `stream` (level transfer, tiles, flux correction; with HYDRO_F_QUAD26:
+ * a gather of every leaf's ghosted block, the 26-point tiles, the flux
+ * correction).  Nothing is allocated, except that the first HYDRO_F_QUAD26
+ * call allocates the ghosted blocks (n_leaves F (N+6)^3 doubles, kept until
+ * hydro_forest_destroy): make it before any stream capture.  The auxiliary
+ * blocks, ghosted blocks and flux registers belong to the forest, so calls
+ * on one forest must be ordered (one stream, or synchronised). */
 int hydro_forest_rhs(hydro_forest_t* forest, const double* U, double dx0, double gamma,
                      double* out_dUdt, double* out_amax, hydro_precision_t prec, void* stream,
                      uint32_t flags);

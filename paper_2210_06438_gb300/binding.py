@@ -83,10 +83,10 @@ class ForestInfo(ctypes.Structure):
     _fields_ = [("n_leaves", ctypes.c_int32), ("N", ctypes.c_int32), ("n_fields", ctypes.c_int32),
                 ("nb0", ctypes.c_int32), ("max_level", ctypes.c_int32),
                 ("n_level_faces", ctypes.c_int32), ("n_reflux_leaves", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("quad26", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class PlanInfo(ctypes.Structure):

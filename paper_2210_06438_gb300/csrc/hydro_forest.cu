@@ -29,6 +29,7 @@
 #include "hydro.h"
 #include "hydro_internal.h"
 #include "hydro_kernels.cuh"
+#include "hydro_quad.cuh"
 
 namespace hydro_host {
 int ctx_status_ptr(hydro_dev::Status** st, int* n_sm, int* smem_optin);
@@ -171,6 +172,73 @@ forest_reflux_kernel(const int* __restrict__ links, const AuxDesc* __restrict__ 
   }
 }
 
+// The 26-point variant reads edge and corner ghosts too: each leaf's ghosted
+// block (G = N + 6) is gathered whole.  One thread per (leaf, cell of the
+// block with each coordinate in [-3, N+2] and at most one at -3 or N+2), all
+// fields.  nb26[27 s + (dx+1) + 3 (dy+1) + 9 (dz+1)] describes the block of
+// the leaf's level at offset (dx, dy, dz): x = 0 a leaf of that level (y),
+// -1 inside the coarser leaf y, +1 refined: kids[8 y + i + 2j + 4k] are its
+// children (those next to the leaf are leaves).
+__global__ void __launch_bounds__(256)
+forest_gather26_kernel(const double* __restrict__ U, double* __restrict__ ghost, const int2* __restrict__ nb26,
+                       const int* __restrict__ kids, const LeafGeo* __restrict__ geo, int nl, int N, int F,
+                       int nb0) {
+  const int G = N + 6;
+  const long long g3 = (long long)G * G * G, n3 = (long long)N * N * N, nn = (long long)N * N;
+  const long long total = (long long)nl * g3;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(i / g3);
+    const int r = (int)(i - s * g3);
+    const int cx = r % G - 3, cy = (r / G) % G - 3, cz = r / (G * G) - 3;
+    const int far = (cx == -3 || cx == N + 2) + (cy == -3 || cy == N + 2) + (cz == -3 || cz == N + 2);
+    if (far > 1) continue;
+    double* dst = ghost + (long long)s * F * g3 + r;
+    const int sx = cx < 0 ? -1 : (cx >= N ? 1 : 0), sy = cy < 0 ? -1 : (cy >= N ? 1 : 0),
+              sz = cz < 0 ? -1 : (cz >= N ? 1 : 0);
+    if (sx == 0 && sy == 0 && sz == 0) {
+      const double* src = U + (long long)s * F * n3 + ((long long)cz * N + cy) * N + cx;
+      for (int f = 0; f < F; f++) dst[f * g3] = __ldg(src + f * n3);
+      continue;
+    }
+    const int2 e = nb26[27 * s + (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)];
+    const LeafGeo og = geo[s];
+    const int M = nb0 << og.level;
+    auto wrap = [M](int q) { return q < 0 ? q + M : (q >= M ? q - M : q); };
+    const int px = wrap(og.bx + sx), py = wrap(og.by + sy), pz = wrap(og.bz + sz);
+    const int vx = cx - sx * N, vy = cy - sy * N, vz = cz - sz * N;  // cell in block p
+    const int gx = px * N + vx, gy = py * N + vy, gz = pz * N + vz;  // level cell index
+    if (e.x == 0) {
+      const double* src = U + (long long)e.y * F * n3 + ((long long)vz * N + vy) * N + vx;
+      for (int f = 0; f < F; f++) dst[f * g3] = __ldg(src + f * n3);
+    } else if (e.x < 0) {
+      const LeafGeo cg = geo[e.y];
+      const int lx = (gx >> 1) - cg.bx * N, ly = (gy >> 1) - cg.by * N, lz = (gz >> 1) - cg.bz * N;
+      const double* src = U + (long long)e.y * F * n3 + ((long long)lz * N + ly) * N + lx;
+      for (int f = 0; f < F; f++) dst[f * g3] = __ldg(src + f * n3);
+    } else {
+      const int fx = 2 * gx, fy = 2 * gy, fz = 2 * gz;
+      const int ch = (fx / N - 2 * px) + 2 * (fy / N - 2 * py) + 4 * (fz / N - 2 * pz);
+      const int leaf = __ldg(kids + 8 * e.y + ch);
+      const LeafGeo fg = geo[leaf];
+      const int lx = fx - fg.bx * N, ly = fy - fg.by * N, lz = fz - fg.bz * N;
+      const double* src = U + (long long)leaf * F * n3 + ((long long)lz * N + ly) * N + lx;
+      for (int f = 0; f < F; f++) {
+        const double* q = src + f * n3;
+        double t = __ldg(q);
+        t = t + __ldg(q + 1);
+        t = t + __ldg(q + N);
+        t = t + __ldg(q + N + 1);
+        t = t + __ldg(q + nn);
+        t = t + __ldg(q + nn + 1);
+        t = t + __ldg(q + nn + N);
+        t = t + __ldg(q + nn + N + 1);
+        dst[f * g3] = t * 0.125;
+      }
+    }
+  }
+}
+
 }  // namespace hydro_dev
 
 using hydro_dev::AuxDesc;
@@ -185,6 +253,10 @@ struct hydro_forest {
   int* rf = nullptr;          // [n_rf]
   double* aux = nullptr;      // [n_aux][F][N^3]
   double* reg = nullptr;      // [n_aux][F][N^2]
+  bool full = false;          // 26-neighbour 2:1 balance: the 26-point variant is available
+  int2* nb26 = nullptr;       // [nl][27]
+  int* kids = nullptr;
+  double* ghost = nullptr;    // [nl][F][(N+6)^3], allocated by the first 26-point call
   long long bytes = 0;
 };
 
@@ -192,22 +264,27 @@ namespace {
 
 // Forest tile kernels (the shapes the autotuner picks for sub-grid batches):
 // 0 binary64, register loads, 576 threads; 1 mixed, pipelined (576 threads);
-// 2 mixed, register loads, 256 threads (HYDRO_F_REGISTER_LOADS).
-constexpr int kLch = 64;
-constexpr int kThreads[3] = {576, hydro_host::kPipeThreads, 256};
-constexpr int kKinds[3] = {hydro_host::kKindTiles, hydro_host::kKindPipe, hydro_host::kKindTiles};
+// 2 mixed, register loads, 256 threads (HYDRO_F_REGISTER_LOADS); 3 and 4
+// the 26-point variant, binary64 and mixed.
+constexpr int kLch = 64, kNumKernels = 5;
+constexpr int kThreads[kNumKernels] = {576, hydro_host::kPipeThreads, 256, hydro_host::kQuadThreads,
+                                       hydro_host::kQuadThreads};
+constexpr int kKinds[kNumKernels] = {hydro_host::kKindTiles, hydro_host::kKindPipe, hydro_host::kKindTiles,
+                                     hydro_host::kKindQuad, hydro_host::kKindQuad};
 
 void* forest_func(int k) {
   switch (k) {
     case 0: return (void*)&hydro_dev::rhs_forest_kernel<0, 576, 1, 1>;
     case 1: return (void*)&hydro_dev::rhs_forest_pipe_kernel<hydro_host::kPipeThreads>;
-    default: return (void*)&hydro_dev::rhs_forest_kernel<1, 256, 1, 4>;
+    case 2: return (void*)&hydro_dev::rhs_forest_kernel<1, 256, 1, 4>;
+    case 3: return (void*)&hydro_dev::rhs_forest_quad_kernel<0>;
+    default: return (void*)&hydro_dev::rhs_forest_quad_kernel<1>;
   }
 }
 
 struct ForestDev {
   bool ready = false;
-  int n_sm = 0, occ[3] = {0, 0, 0};
+  int n_sm = 0, occ[kNumKernels] = {0, 0, 0, 0, 0};
 };
 ForestDev g_fdev[64];
 std::mutex g_fmu;
@@ -222,8 +299,8 @@ int forest_setup(int dev, ForestDev** out) {
     if ((e = cudaDeviceGetAttribute(&D.n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
       return hydro_host::cuda_fail(e, "cudaDeviceGetAttribute");
-    for (int m = 0; m < 3; m++) {
-      hydro_precision_t prec = m == 0 ? HYDRO_FP64 : HYDRO_FP32_FLUX_FP64_ACC;
+    for (int m = 0; m < kNumKernels; m++) {
+      hydro_precision_t prec = (m == 0 || m == 3) ? HYDRO_FP64 : HYDRO_FP32_FLUX_FP64_ACC;
       int smem = hydro_host::smem_bytes(prec, HYDRO_MAX_FIELDS, kLch, kKinds[m]);
       if ((e = cudaFuncSetAttribute(forest_func(m), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     optin - 1024)) != cudaSuccess)
@@ -255,6 +332,11 @@ struct Tables {
   std::vector<AuxDesc> desc;
   std::vector<int> rf;
   int max_level = 0;
+  // the 26-neighbour tables of the 26-point variant (built when every leaf's
+  // edge and corner neighbours also differ from it by at most one level)
+  bool full = false;
+  std::vector<int2> nb26;  // [nl][27]
+  std::vector<int> kids;   // [8 per refined neighbour block]
 };
 
 // Validate the forest and build its neighbour tables.
@@ -343,6 +425,42 @@ int build_tables(const hydro_leaf_t* lv, int32_t n, int32_t nb0, int32_t N, Tabl
     T.links[8 * s + 6] = L;
     if (finer) T.rf.push_back(s);
   }
+  // 26 neighbours (the face ones included): same level, coarser by one, or
+  // refined with every child next to the leaf a leaf of the next level
+  T.full = true;
+  T.nb26.assign((size_t)n * 27, make_int2(2, -1));
+  T.kids.clear();
+  for (int s = 0; s < n && T.full; s++) {
+    const hydro_leaf_t& l = lv[s];
+    const int L = l.level, M_L = nb0 << L;
+    for (int k = 0; k < 27 && T.full; k++) {
+      const int o[3] = {k % 3 - 1, (k / 3) % 3 - 1, k / 9 - 1};
+      if (!o[0] && !o[1] && !o[2]) continue;
+      const int p[3] = {(l.bx + o[0] + M_L) % M_L, (l.by + o[1] + M_L) % M_L, (l.bz + o[2] + M_L) % M_L};
+      int t = find(L, p[0], p[1], p[2]);
+      if (t >= 0) {
+        T.nb26[27 * s + k] = make_int2(0, t);
+      } else if (L > 0 && (t = find(L - 1, p[0] >> 1, p[1] >> 1, p[2] >> 1)) >= 0) {
+        T.nb26[27 * s + k] = make_int2(-1, t);
+      } else {
+        const int base = (int)(T.kids.size() / 8);
+        for (int c = 0; c < 8; c++) {
+          const int b[3] = {c & 1, (c >> 1) & 1, c >> 2};
+          bool next = true;  // the child touches the leaf
+          for (int e = 0; e < 3; e++)
+            if ((o[e] == 1 && b[e] == 1) || (o[e] == -1 && b[e] == 0)) next = false;
+          t = find(L + 1, 2 * p[0] + b[0], 2 * p[1] + b[1], 2 * p[2] + b[2]);
+          if (next && t < 0) T.full = false;
+          T.kids.push_back(next ? t : -1);
+        }
+        T.nb26[27 * s + k] = make_int2(1, base);
+      }
+    }
+  }
+  if (!T.full) {
+    T.nb26.clear();
+    T.kids.clear();
+  }
   return HYDRO_OK;
 }
 
@@ -358,6 +476,9 @@ int upload(T** dst, const std::vector<T>& v, long long& bytes) {
 }
 
 void release(hydro_forest* f) {
+  cudaFree(f->nb26);
+  cudaFree(f->kids);
+  cudaFree(f->ghost);
   cudaFree(f->links);
   cudaFree(f->geo);
   cudaFree(f->desc);
@@ -370,7 +491,9 @@ int forest_launch(hydro_forest* fo, const double* U, const double* U0, double al
                   int stage, double dx0, double gamma, double* out, double* amax, hydro_precision_t prec,
                   void* stream, uint32_t flags) {
   if (!fo || !U || !out || !amax || (stage && !U0)) return HYDRO_EINVAL;
-  if (flags & ~(uint32_t)(HYDRO_F_KNP | HYDRO_F_REGISTER_LOADS)) return HYDRO_EINVAL;
+  if (flags & ~(uint32_t)(HYDRO_F_KNP | HYDRO_F_REGISTER_LOADS | HYDRO_F_QUAD26)) return HYDRO_EINVAL;
+  const bool quad26 = (flags & HYDRO_F_QUAD26) != 0;
+  if (quad26 && !fo->full) return HYDRO_EINVAL;  // edge/corner neighbours more than one level apart
   if (!(dx0 > 0.0) || !std::isfinite(dx0) || !(gamma > 1.0) || !std::isfinite(gamma)) return HYDRO_EINVAL;
   if (prec != HYDRO_FP64 && prec != HYDRO_FP32_FLUX_FP64_ACC) return HYDRO_EINVAL;
   if (stage && (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(dt))) return HYDRO_EINVAL;
@@ -397,29 +520,57 @@ int forest_launch(hydro_forest* fo, const double* U, const double* U0, double al
   const long long n_tiles = (long long)fo->nl * tpe * tpe * tpe;
   if (tpe > 1 && (e = cudaMemsetAsync(amax, 0, (size_t)fo->nl * sizeof(double), st)) != cudaSuccess)
     return hydro_host::cuda_fail(e, "cudaMemsetAsync(amax)");
-  // 1. level transfer
-  if (fo->n_aux > 0) {
-    const long long cells = (long long)fo->n_aux * 3 * N * N;
-    const int grid = (int)std::min<long long>((cells + 255) / 256, (long long)D->n_sm * 8);
-    hydro_dev::forest_ghost_kernel<<<grid, 256, 0, st>>>(U, fo->aux, fo->desc, fo->geo, fo->n_aux, N, F,
-                                                         fo->nb0);
-    if ((e = cudaGetLastError()) != cudaSuccess) return hydro_host::cuda_fail(e, "forest ghost launch");
-  }
-  // 2. tiles
   int ex2;
   const bool pow2 = std::frexp(dx0, &ex2) == 0.5 && ex2 > -120 && ex2 < 120;
-  hydro_dev::ForestTiles ft{U, fo->aux, fo->links, fo->reg, fo->nl, N, F, tpe, 1.0 / dx0, (short)(pow2 ? 2 : 0)};
   hydro_dev::StageArgs sa{U, stage ? U0 : U, alpha, beta, dt, stage};
-  const int m = prec == HYDRO_FP64 ? 0 : ((flags & HYDRO_F_REGISTER_LOADS) ? 2 : 1);
-  const int threads = kThreads[m];
   int nt = (int)n_tiles, lch = kLch, ws = 1, scheme = (flags & HYDRO_F_KNP) ? 1 : 0;
-  const long long g64 = (long long)D->occ[m] * D->n_sm;
-  const int grid = (int)(n_tiles < g64 ? n_tiles : g64);
-  size_t smem = (size_t)hydro_host::smem_bytes(prec, F, lch, kKinds[m]);
-  void* args[] = {(void*)&ft, (void*)&nt, (void*)&lch, (void*)&out, (void*)&amax, (void*)&status,
-                  (void*)&gamma, (void*)&ws, (void*)&scheme, (void*)&sa};
-  if ((e = cudaLaunchKernel(forest_func(m), dim3(grid), dim3(threads), args, smem, st)) != cudaSuccess)
-    return hydro_host::cuda_fail(e, "forest tile launch");
+  if (quad26) {
+    // 1. the ghosted blocks, edges and corners included
+    const int G = N + 6;
+    if (!fo->ghost) {
+      const size_t gb = (size_t)fo->nl * F * G * G * G * sizeof(double);
+      if (cudaMalloc(&fo->ghost, gb) != cudaSuccess) {
+        fo->ghost = nullptr;
+        return HYDRO_ENOMEM;
+      }
+      fo->bytes += (long long)gb;
+    }
+    const long long cells = (long long)fo->nl * G * G * G;
+    const int gg = (int)std::min<long long>((cells + 255) / 256, (long long)D->n_sm * 8);
+    hydro_dev::forest_gather26_kernel<<<gg, 256, 0, st>>>(U, fo->ghost, fo->nb26, fo->kids, fo->geo, fo->nl, N,
+                                                          F, fo->nb0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return hydro_host::cuda_fail(e, "forest gather launch");
+    // 2. the 26-point tiles
+    const int m = prec == HYDRO_FP64 ? 3 : 4;
+    hydro_dev::ForestQuadTiles fq{fo->ghost, fo->links, fo->reg, fo->nl, N, F, tpe, 1.0 / dx0,
+                                  (short)(pow2 ? 2 : 0)};
+    const long long g64 = (long long)D->occ[m] * D->n_sm;
+    const int grid = (int)(n_tiles < g64 ? n_tiles : g64);
+    size_t smem = (size_t)hydro_host::smem_bytes(prec, F, lch, kKinds[m]);
+    void* args[] = {(void*)&fq, (void*)&nt, (void*)&lch, (void*)&out, (void*)&amax, (void*)&status,
+                    (void*)&gamma, (void*)&ws, (void*)&scheme, (void*)&sa};
+    if ((e = cudaLaunchKernel(forest_func(m), dim3(grid), dim3(kThreads[m]), args, smem, st)) != cudaSuccess)
+      return hydro_host::cuda_fail(e, "forest 26-point launch");
+  } else {
+    // 1. level transfer
+    if (fo->n_aux > 0) {
+      const long long cells = (long long)fo->n_aux * 3 * N * N;
+      const int grid = (int)std::min<long long>((cells + 255) / 256, (long long)D->n_sm * 8);
+      hydro_dev::forest_ghost_kernel<<<grid, 256, 0, st>>>(U, fo->aux, fo->desc, fo->geo, fo->n_aux, N, F,
+                                                           fo->nb0);
+      if ((e = cudaGetLastError()) != cudaSuccess) return hydro_host::cuda_fail(e, "forest ghost launch");
+    }
+    // 2. tiles
+    hydro_dev::ForestTiles ft{U, fo->aux, fo->links, fo->reg, fo->nl, N, F, tpe, 1.0 / dx0, (short)(pow2 ? 2 : 0)};
+    const int m = prec == HYDRO_FP64 ? 0 : ((flags & HYDRO_F_REGISTER_LOADS) ? 2 : 1);
+    const long long g64 = (long long)D->occ[m] * D->n_sm;
+    const int grid = (int)(n_tiles < g64 ? n_tiles : g64);
+    size_t smem = (size_t)hydro_host::smem_bytes(prec, F, lch, kKinds[m]);
+    void* args[] = {(void*)&ft, (void*)&nt, (void*)&lch, (void*)&out, (void*)&amax, (void*)&status,
+                    (void*)&gamma, (void*)&ws, (void*)&scheme, (void*)&sa};
+    if ((e = cudaLaunchKernel(forest_func(m), dim3(grid), dim3(kThreads[m]), args, smem, st)) != cudaSuccess)
+      return hydro_host::cuda_fail(e, "forest tile launch");
+  }
   // 3. flux correction
   if (fo->n_rf > 0) {
     const long long cells = (long long)fo->n_rf * N * N * N;
@@ -469,10 +620,12 @@ int hydro_forest_create(const hydro_leaf_t* leaves, int32_t n_leaves, int32_t nb
   f->max_level = T.max_level;
   f->n_aux = (int)T.desc.size();
   f->n_rf = (int)T.rf.size();
+  f->full = T.full;
   std::vector<LeafGeo> geo((size_t)n_leaves);
   for (int s = 0; s < n_leaves; s++) geo[s] = {leaves[s].level, leaves[s].bx, leaves[s].by, leaves[s].bz};
   if ((rc = upload(&f->links, T.links, f->bytes)) || (rc = upload(&f->geo, geo, f->bytes)) ||
-      (rc = upload(&f->desc, T.desc, f->bytes)) || (rc = upload(&f->rf, T.rf, f->bytes))) {
+      (rc = upload(&f->desc, T.desc, f->bytes)) || (rc = upload(&f->rf, T.rf, f->bytes)) ||
+      (rc = upload(&f->nb26, T.nb26, f->bytes)) || (rc = upload(&f->kids, T.kids, f->bytes))) {
     release(f);
     delete f;
     return rc;
@@ -501,6 +654,7 @@ int hydro_forest_info(const hydro_forest_t* f, hydro_forest_info_t* info) {
   info->max_level = f->max_level;
   info->n_level_faces = f->n_aux;
   info->n_reflux_leaves = f->n_rf;
+  info->quad26 = f->full ? 1 : 0;
   info->device_bytes = f->bytes;
   return HYDRO_OK;
 }

@@ -40,6 +40,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <type_traits>
 
 namespace hydro_dev {
 
@@ -798,11 +799,12 @@ struct ForestCapture {
   const int* row;
   int nl, N, F, ox, oy, oz, f0;
   // Record the fluxes of the lines [l0, l0 + lch) of direction d, just
-  // computed in QS (slot j = field f0 + j, or the field pair f0 + 2j, +1),
-  // through the faces that lie on the leaf's boundary towards another level.
-  template <int MODE, int NT>
-  __device__ __forceinline__ void faces(const typename Prec<MODE>::V* QS, int fs, int lch, int l0, int ng,
-                                        int d, int ex, int ey, int ez) const {
+  // computed in QS (slot j = field f0 + j, or for binary32 pairs the fields
+  // f0 + 2j, f0 + 2j + 1), through the faces that lie on the leaf's boundary
+  // towards another level.
+  template <int NT, class V>
+  __device__ __forceinline__ void faces(const V* QS, int fs, int lch, int l0, int ng, int d, int ex, int ey,
+                                        int ez) const {
     const int e_d = d == 0 ? ex : (d == 1 ? ey : ez);
     const int e_a = d == 0 ? ey : ex, e_b = d == 2 ? ey : ez;
     const int o_d = d == 0 ? ox : (d == 1 ? oy : oz);
@@ -816,14 +818,14 @@ struct ForestCapture {
       const int blk = side ? hi : lo;
       const int l = l0 + ll, a = l % TE, b = l / TE;
       if (blk < nl || a >= e_a || b >= e_b) continue;
-      const auto v = QS[j * fs + ll * NFC + (side ? e_d : 0)];
+      const V v = QS[j * fs + ll * NFC + (side ? e_d : 0)];
       double* dst = reg + (long long)(blk - nl) * F * nn + (long long)(o_b + b) * N + (o_a + a);
-      if constexpr (MODE == 0) {
-        dst[(f0 + j) * nn] = v;
-      } else {
+      if constexpr (std::is_same<V, float2>::value) {
         const int f = f0 + 2 * j;
         dst[f * nn] = (double)v.x;
         if (f + 1 < F) dst[(f + 1) * nn] = (double)v.y;
+      } else {
+        dst[(f0 + j) * nn] = (double)v;
       }
     }
   }
@@ -867,9 +869,8 @@ struct ForestTiles {
 };
 
 struct NoCapture {
-  template <int MODE, int NT>
-  __device__ __forceinline__ void faces(const typename Prec<MODE>::V*, int, int, int, int, int, int, int,
-                                        int) const {}
+  template <int NT, class V>
+  __device__ __forceinline__ void faces(const V*, int, int, int, int, int, int, int, int) const {}
 };
 
 // One pass of steps A2-A4 over a group of `ng` field slots (V elements) for
@@ -945,7 +946,7 @@ __device__ __forceinline__ void group_pass(
         }
       }
       __syncthreads();
-      cap.template faces<MODE, NT>(QS, fs, lch, l0, ng, d, ex, ey, ez);
+      cap.template faces<NT>(QS, fs, lch, l0, ng, d, ex, ey, ez);
       // ---- A4: flux differences into the owned cells, x then y then z
 #pragma unroll
       for (int k = 0; k < CPT; k++) {
@@ -1489,7 +1490,7 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
     if constexpr (DOM == 2) {
       const ForestCapture cap = fetch.capture(tile, 0);
 #pragma unroll 1
-      for (int d = 0; d < 3; d++) cap.template faces<1, PNT>(qs(d, 0, 0), FS, NLN, 0, 3, d, ex, ey, ez);
+      for (int d = 0; d < 3; d++) cap.template faces<PNT>(qs(d, 0, 0), FS, NLN, 0, 3, d, ex, ey, ez);
     }
     diff_pass(3);
     store_group<1, PNT, (DOM != 0)>(out, tile, ex, ey, ez, 0, 6, acc, stage);
@@ -1550,7 +1551,7 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
       if constexpr (DOM == 2) {
         const ForestCapture cap = fetch.capture(tile, 6);
 #pragma unroll 1
-        for (int d = 0; d < 3; d++) cap.template faces<1, PNT>(qs(d, 0, 0), FS, NLN, 0, npair, d, ex, ey, ez);
+        for (int d = 0; d < 3; d++) cap.template faces<PNT>(qs(d, 0, 0), FS, NLN, 0, npair, d, ex, ey, ez);
       }
       diff_pass(npair);
       store_group<1, PNT, (DOM != 0)>(out, tile, ex, ey, ez, 6, nsp, acc, stage);

@@ -102,8 +102,10 @@ __device__ __forceinline__ void two_diff1(float a, float b, float& s, float& e) 
 
 // DOMAIN: the tiles belong to a periodic cube of pad[0]^3 sub-grids stored
 // without ghosts (as in tile_loop); `stage` may turn the output into an
-// explicit stage update.
-template <int MODE, class Fetch, bool DOMAIN = false>
+// explicit stage update.  CAP: forest leaves read from their gathered
+// ghosted blocks; the fluxes through faces towards other levels are recorded
+// (`fetch.capture`), and `stage` applies (outputs in the forest layout).
+template <int MODE, class Fetch, bool DOMAIN = false, bool CAP = false>
 __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, double* __restrict__ out,
                                                double* __restrict__ amax_out, Status* __restrict__ status,
                                                double gamma_d, int write_status, bool knp,
@@ -301,6 +303,7 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
           if (f < F) FF[f * QFACES + face] = fsum[f] / R(36);
       }
       __syncthreads();
+      if constexpr (CAP) fetch.capture(tile, 0).template faces<QNT>(FF, QFACES, NLN, 0, F, d, ex, ey, ez);
       // ---- A4: flux differences of the owned cells
 #pragma unroll
       for (int k = 0; k < QCPT; k++) {
@@ -352,7 +355,7 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
               double v;
               if constexpr (MODE == 0) v = acc[k][f] * scale;
               else v = pair_value(acc[k][f].h, acc[k][f].l, scale, sf, pow2);
-              if constexpr (DOMAIN) {
+              if constexpr (DOMAIN || CAP) {
                 if (stage.on) {
                   long long e = (o - out) + f * n3;  // same index in U, U0 and out
                   v = fma(stage.alpha, __ldg(stage.U0 + e), stage.beta * fma(stage.dt, v, __ldg(stage.U + e)));
@@ -406,6 +409,52 @@ rhs_domain_quad_kernel(DomainTiles dom, int n_tiles, int lch, double* __restrict
   (void)lch;
   tile_loop_quad<MODE, DomainTiles, true>(dom, n_tiles, out, amax_out, status, gamma_d, write_status,
                                           scheme == 1, stage);
+}
+
+// Forest leaves for the 26-point variant: leaf s = t / tpe^3 read from its
+// ghosted block ghost + s F G^3 (G = N + 6, gathered across levels before
+// the launch); outputs, amax and the flux registers as for ForestTiles.
+struct ForestQuadTiles {
+  const double* __restrict__ ghost;
+  const int* __restrict__ links;
+  double* __restrict__ reg;
+  int nl, N, F, tpe;
+  double inv_dx0;
+  short flags;  // bit 1: dx0 a power of two
+  __device__ __forceinline__ Tile operator()(int t) const {
+    const int tps = tpe * tpe * tpe;
+    const int s = t / tps, k = t - s * tps;
+    const int G = N + 6;
+    Tile tile;
+    tile.U = ghost + (long long)s * F * G * G * G;
+    tile.out_off = (long long)s * F * N * N * N;
+    tile.amax_off = s;
+    tile.inv_dx = inv_dx0 * (double)(1u << __ldg(links + 8 * s + 6));
+    tile.sub = s;
+    tile.N = N;
+    tile.F = F;
+    tile.G = G;
+    tile.ox = (short)((k % tpe) * TE);
+    tile.oy = (short)(((k / tpe) % tpe) * TE);
+    tile.oz = (short)((k / (tpe * tpe)) * TE);
+    tile.flags = (short)((tps > 1 ? 1 : 0) | (flags & 2));
+    tile.pad[0] = 0;
+    tile.pad[1] = 0;
+    return tile;
+  }
+  __device__ __forceinline__ ForestCapture capture(const Tile& tile, int f0) const {
+    return ForestCapture{reg, links + 8 * tile.sub, nl, N, F, tile.ox, tile.oy, tile.oz, f0};
+  }
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(QNT, MODE == 0 ? 1 : 2)
+rhs_forest_quad_kernel(ForestQuadTiles ft, int n_tiles, int lch, double* __restrict__ out,
+                       double* __restrict__ amax_out, Status* __restrict__ status, double gamma_d,
+                       int write_status, int scheme, StageArgs stage) {
+  (void)lch;
+  tile_loop_quad<MODE, ForestQuadTiles, false, true>(ft, n_tiles, out, amax_out, status, gamma_d, write_status,
+                                                     scheme == 1, stage);
 }
 
 }  // namespace hydro_dev

@@ -195,6 +195,85 @@ def test_forest_rk3_step_in_a_cuda_graph():
     fo.close()
 
 
+# ------------------------------------------------- 26-point variant --
+def _full_forest():
+    return synth.forest_leaves(3, 2, synth.random_refine(1, 0.1), seed=1, balance="full")
+
+
+@pytest.mark.parametrize("prec", [hydro.FP64, MX])
+@pytest.mark.parametrize("case", ["three_levels_8", "two_levels_16"])
+def test_quad26_forest_matches_oracle(prec, case):
+    if case == "three_levels_8":
+        lv, nb0, N, nf = _full_forest(), 3, 8, 7
+    else:
+        lv, nb0, N, nf = synth.forest_leaves(1, 2, synth.random_refine(3, 0.6), seed=3, balance="full"), 1, 16, 6
+    U, dx0 = synth.smooth_forest_state(lv, nb0, N, nf=nf, seed=48)
+    got, gam, info = _run(lv, nb0, U, dx0, prec, flags=hydro.F_QUAD26)
+    assert info["quad26"] == 1
+    mode = oracle.QUAD26 | (0 if prec == hydro.FP64 else oracle.MODE_MIXED)
+    ref, ram = of.rhs(lv, nb0, list(U), dx0, mode=mode)
+    _check(prec, got, gam, ref, ram, U, _dxs(lv, dx0))
+    vol = np.array(_dxs(lv, dx0)) ** 3
+    tot = sum(got[s].sum(axis=(1, 2, 3)) * vol[s] for s in range(len(lv)))
+    mag = sum(np.abs(got[s]).sum(axis=(1, 2, 3)) * vol[s] for s in range(len(lv)))
+    assert np.all(np.abs(tot) <= (1e-14 if prec == hydro.FP64 else 1e-12) * mag)
+
+
+def test_quad26_forest_stage_and_one_sided_flux():
+    lv = _full_forest()
+    U, dx0 = synth.smooth_forest_state(lv, 3, 8, nf=6, seed=49)
+    U0, _ = synth.smooth_forest_state(lv, 3, 8, nf=6, seed=50)
+    a, b, dt = 1.0 / 3.0, 2.0 / 3.0, 1e-3
+    got, gam, _ = _run(lv, 3, U, dx0, hydro.FP64, flags=hydro.F_QUAD26 | hydro.F_KNP, stage=(U0, a, b, dt))
+    mode = oracle.QUAD26 | oracle.FLUX_KNP
+    ref, ram = of.stage(lv, 3, list(U), list(U0), a, b, dt, dx0, mode=mode)
+    dU, _ = of.rhs(lv, 3, list(U), dx0, mode=mode)
+    dxs = _dxs(lv, dx0)
+    for s in range(len(lv)):
+        Umax = np.abs(U[s]).reshape(6, -1).max(axis=1)
+        for f in range(6):
+            rt = 1e-12 * max(np.abs(dU[s][f]).max(), ram[s] * Umax[f] / dxs[s])
+            assert np.abs(got[s][f] - ref[s][f]).max() <= 4e-16 * np.abs(ref[s][f]).max() + b * dt * rt
+    assert np.allclose(gam, ram, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("prec", [hydro.FP64, MX])
+def test_quad26_one_level_forest_equals_domain_kernel(prec):
+    nb0, N = 2, 8
+    lv = synth.forest_leaves(nb0, 0, lambda *a: False, seed=8)
+    glob = synth.plain_domain(seed=51, n=nb0 * N, nf=9)
+    blocks = synth.gather_blocks(glob, N, blocks=[tuple(l[1:]) for l in lv])
+    U = np.ascontiguousarray(blocks[:, :, 3:-3, 3:-3, 3:-3])
+    dx0 = 1.0 / (nb0 * N)
+    got, gam, _ = _run(lv, nb0, U, dx0, prec, flags=hydro.F_QUAD26)
+    order = [int(x + nb0 * (y + nb0 * z)) for _, x, y, z in lv]
+    dom = np.empty_like(U)
+    dom[order] = U
+    Ud = torch.from_numpy(dom).cuda()
+    out = torch.empty_like(Ud)
+    am = torch.empty(len(lv), dtype=torch.float64, device="cuda")
+    hydro.domain_rhs(Ud, nb0, N, 9, dx0, out, am, prec=prec, flags=hydro.F_QUAD26)
+    torch.cuda.synchronize()
+    o, a = out.cpu().numpy(), am.cpu().numpy()
+    for s in range(len(lv)):
+        assert np.array_equal(got[s], o[order[s]])
+        assert gam[s] == a[order[s]]
+
+
+def test_quad26_needs_full_balance():
+    lv = _forest(2, 7, 0.25)  # balanced across faces only
+    U, dx0 = synth.smooth_forest_state(lv, 2, 8, nf=6)
+    fo = hydro.Forest(lv, 2, 8, 6)
+    assert fo.info()["quad26"] == 0
+    Ud = torch.from_numpy(U).cuda()
+    out = torch.empty_like(Ud)
+    am = torch.empty(len(lv), dtype=torch.float64, device="cuda")
+    with pytest.raises(hydro.HydroError) as ei:
+        fo.rhs(Ud, dx0, out, am, flags=hydro.F_QUAD26)
+    assert ei.value.code == hydro.HYDRO_EINVAL
+    fo.close()
+
+
 def test_forest_argument_checks():
     lv = _forest(2, 4, 0.25)
     U, dx0 = synth.smooth_forest_state(lv, 2, 8, nf=6)
@@ -202,7 +281,7 @@ def test_forest_argument_checks():
     Ud = torch.from_numpy(U).cuda()
     out = torch.empty_like(Ud)
     am = torch.empty(len(lv), dtype=torch.float64, device="cuda")
-    for kw in (dict(flags=hydro.F_QUAD26), dict(dx0=-1.0), dict(gamma=1.0), dict(out=Ud)):
+    for kw in (dict(flags=16), dict(dx0=-1.0), dict(gamma=1.0), dict(out=Ud)):
         with pytest.raises(hydro.HydroError) as ei:
             fo.rhs(Ud, kw.get("dx0", dx0), kw.get("out", out), am, gamma=kw.get("gamma", 5.0 / 3.0),
                    flags=kw.get("flags", 0))
