@@ -470,6 +470,26 @@ def forest_forms(steps, warmup, stream, nb0=16, radii=(0.35, 0.2), N=8, nf=11, g
     return res
 
 
+def sedov_forest_form(prec, nb0=4, radii=(0.42, 0.36), flags=0):
+    """The Sedov blast on a forest refined around the centre: level-2
+    resolution (128^3 cells' width at nb0 = 4) where the shock runs, level 1
+    outside; measures against the similarity solution as for sedov_form."""
+    from tests.sedov_exact import Sedov
+    from tests.sedov_run import forest_shock_measures
+
+    ex = Sedov(5.0 / 3.0)
+    r = sedov_forest_run(nb0=nb0, radii=radii, prec=prec, t_end=ex.time_for_radius(0.35), flags=flags)
+    lv = r["leaves"]
+    Rp, L1 = forest_shock_measures(lv, nb0, r["U"][:, 0].cpu().numpy(), ex, r["t"])
+    cells = len(lv) * 512
+    return {"value": 3 * cells * r["steps"] / (r["ms"] * 1e-3), "unit": "stage cell-updates/s",
+            "steps": r["steps"], "ms": r["ms"], "t_end": r["t"], "R_peak": Rp,
+            "R_exact": ex.shock_radius(r["t"]), "L1_rho": L1, "cells": cells,
+            "leaves_by_level": np.bincount(lv[:, 0]).tolist(),
+            "note": "Sedov blast to R = 0.35 on a forest refined around the centre (%d leaves of 8^3, "
+                    "11 fields, radii %s), SSP-RK3 of forest stages, one global dt" % (len(lv), list(radii))}
+
+
 def sedov_form(n, prec, flags=0):
     """One Sedov run at n^3 with its measures against the similarity solution."""
     from tests.sedov_exact import Sedov
@@ -679,7 +699,11 @@ def run_ours(args, rank, world):
         sedov = {"sedov_fp64_64": sedov_form(64, hydro.FP64),
                  "sedov_mixed_64": sedov_form(64, hydro.FP32_FLUX_FP64_ACC),
                  "sedov_fp64_quad26_64": sedov_form(64, hydro.FP64, hydro.F_QUAD26),
-                 "sedov_mixed_quad26_64": sedov_form(64, hydro.FP32_FLUX_FP64_ACC, hydro.F_QUAD26)}
+                 "sedov_mixed_quad26_64": sedov_form(64, hydro.FP32_FLUX_FP64_ACC, hydro.F_QUAD26),
+                 "sedov_fp64_128": sedov_form(128, hydro.FP64)}
+        if not args.no_forest:
+            sedov["sedov_fp64_forest"] = sedov_forest_form(hydro.FP64)
+            sedov["sedov_mixed_forest"] = sedov_forest_form(hydro.FP32_FLUX_FP64_ACC)
 
     # ---- end to end through the C ABI with host buffers.  Inputs and outputs
     # live in pinned host memory; the plan's descriptors point there and the
@@ -825,6 +849,32 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_forest(args, nb0=16, radii=(0.35, 0.2), N=8, nf=11):
+    """The forest RHS of forest_forms for ncu: `warmup` untimed and `steps`
+    timed calls, each three launches (level transfer, tiles, flux correction;
+    the 26-point variant: gather, tiles, flux correction)."""
+    import torch
+
+    import paper_2210_06438_gb300 as hydro
+
+    stream = torch.cuda.current_stream()
+    leaves = synth.forest_leaves(nb0, len(radii), synth.sphere_refine((0.5, 0.5, 0.5), radii), balance="full")
+    U_h, dx0 = synth.smooth_forest_state(leaves, nb0, N, nf=nf)
+    U = torch.from_numpy(U_h).cuda()
+    out = torch.empty_like(U)
+    am = torch.empty(len(leaves), dtype=torch.float64, device="cuda")
+    fo = hydro.Forest(leaves, nb0, N, nf)
+    prec = hydro.FP64 if args.profile in ("forest64", "forest64_quad26") else hydro.FP32_FLUX_FP64_ACC
+    flags = hydro.F_QUAD26 if args.profile.endswith("quad26") else 0
+    ms = time_steps(lambda: fo.rhs(U, dx0, out, am, prec=prec, stream=stream, flags=flags), args.steps,
+                    args.warmup, stream)
+    rc, bad = hydro.status(stream)
+    info = fo.info()
+    fo.close()
+    print(json.dumps({"profile": args.profile, "ms": ms, "cells": len(leaves) * N ** 3, "status": rc,
+                      "launches_before_timed": 3 * args.warmup, "forest": info}), flush=True)
+
+
 def run_profile(args):
     """A short run of one form for ncu: the tuned plan, `warmup` untimed and
     `steps` timed executions.  Prints how many launches of the tile kernel
@@ -836,6 +886,8 @@ def run_profile(args):
 
     hydro.load(build_if_missing=True)
     stream = torch.cuda.current_stream()
+    if args.profile.startswith("forest"):
+        return run_profile_forest(args)
     batch = polytrope_batch(n=args.domain)
     prec = hydro.FP64 if args.profile == "fp64" else hydro.FP32_FLUX_FP64_ACC
     plan = hydro.Plan(batch.desc, ghost=3, gamma=GAMMA, prec=prec, autotune=True, stream=stream,
@@ -871,7 +923,8 @@ def main():
     ap.add_argument("--no-quad26", action="store_true", help="skip the 26-point quadrature forms")
     ap.add_argument("--rate", type=float, default=20000.0, help="serving arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
-    ap.add_argument("--profile", choices=["fp64", "mixed"], default=None,
+    ap.add_argument("--profile", choices=["fp64", "mixed", "forest64", "forestmx", "forest64_quad26",
+                                          "forestmx_quad26"], default=None,
                     help="short run of one form for ncu (no JSON bench line)")
     args = ap.parse_args()
     if args.profile:
