@@ -508,6 +508,26 @@ def sedov_form(n, prec, flags=0):
 
 
 # ---------------------------------------------------------- cpu baseline --
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    import subprocess
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def oracle_sample_rate(blocks_host, dx, seconds=10.0, threads=None, mode=0):
     """The oracle (as it stands) over a sample of sub-grids, repeated until
     `seconds` of wall time; returns (cells/s, threads, repetitions)."""
@@ -797,9 +817,14 @@ def run_ours(args, rank, world):
         idx = np.linspace(0, batch.n - 1, args.cpu_sample).astype(int)
         host_blocks = [batch.blocks[int(i)].cpu().numpy() for i in idx]
         rate, thr, reps = oracle_sample_rate(host_blocks, batch.dx, seconds=args.cpu_seconds)
+        one = host_blocks[::max(1, len(host_blocks) // 128)]
+        rate1, _, reps1 = oracle_sample_rate(one, batch.dx, seconds=min(3.0, args.cpu_seconds), threads=1)
         cpu = {"value": rate, "unit": "cell-updates/s", "cores": thr, "kind": "oracle",
                "sample": "%d evenly spaced sub-grids of the workload, %d passes, FP64, OpenMP over "
-                         "sub-grids" % (len(idx), reps)}
+                         "sub-grids" % (len(idx), reps),
+               "one_core": {"value": rate1, "sample": "%d of those sub-grids, %d passes, 1 thread"
+                                                      % (len(one), reps1)},
+               "cpu_model": cpu_model()}
 
     value = cells * world / (ms64 * 1e-3)
     line = {

@@ -274,6 +274,27 @@ def test_quad26_needs_full_balance():
     fo.close()
 
 
+@pytest.mark.parametrize("flags", [0, hydro.F_QUAD26])
+def test_forest_nonphysical_input_is_flagged(flags):
+    """A negative density inside one leaf is recorded in the status word with
+    that leaf's index (the ghost transfers pass it on unflagged: only the
+    tile that reads the cell flags it); the call completes and the word
+    clears when read."""
+    lv = _full_forest()
+    U, dx0 = synth.smooth_forest_state(lv, 3, 8, nf=6, seed=52)
+    # a cell of a coarsest-level leaf four cells from its faces: neighbours of
+    # the same level read three cells deep and finer ones two, so only the
+    # leaf itself reads it
+    s_bad = int(np.flatnonzero(lv[:, 0] == 0)[0])
+    U[s_bad, 0, 4, 4, 4] = -1.0
+    hydro.status()  # clear
+    got, gam, _ = _run(lv, 3, U, dx0, hydro.FP64, flags=flags)
+    rc, bad = hydro.status()
+    assert rc == hydro.HYDRO_ENONPHYS and bad == s_bad
+    hydro.status()
+    assert hydro.status() == (hydro.HYDRO_OK, -1)
+
+
 def test_forest_argument_checks():
     lv = _forest(2, 4, 0.25)
     U, dx0 = synth.smooth_forest_state(lv, 2, 8, nf=6)
