@@ -147,30 +147,37 @@ def _face_flux(faces, d, c, i):
     return faces[2][:, i, y, x]
 
 
-def rhs(leaves, nb0, U, dx0, gamma=5.0 / 3.0, mode=0):
+def rhs(leaves, nb0, U, dx0, gamma=5.0 / 3.0, mode=0, only=None):
     """dU/dt of every leaf (list of [nf][N][N][N]) and amax per leaf, with
     the flux correction of reading 3.  mode: the oracle's mode bits (binary32
-    reconstruction and flux, one-sided flux, the 26-point variant)."""
+    reconstruction and flux, one-sided flux, the 26-point variant).
+    only: a list of leaves; then only those are evaluated (with the face
+    fluxes of their finer neighbours for the correction) and the results are
+    dicts keyed by leaf."""
     U = [np.asarray(u, dtype=np.float64) for u in U]
     N = U[0].shape[-1]
     fo = Forest(leaves, nb0, N)
     n = len(fo.leaves)
-    outs, amax, faces = [], np.zeros(n), []
-    for s in range(n):
-        dx = dx0 / (1 << int(fo.leaves[s, 0]))
-        o, a, flags, fc = rhs_block(ghosted_block(fo, U, s, quad26=bool(mode & 4)), 3, gamma, dx, mode,
-                                    faces=True)
-        if flags:
-            raise ValueError("oracle flagged leaf %d (flags %d)" % (s, flags))
-        outs.append(o)
-        amax[s] = a
-        faces.append(fc)
-    # reading 3: corrections at faces towards finer leaves, x then y then z
-    for s in range(n):
+    cache = {}
+
+    def leaf(s):
+        """(uncorrected dU/dt, amax, face fluxes) of leaf s."""
+        if s not in cache:
+            dx = dx0 / (1 << int(fo.leaves[s, 0]))
+            o, a, flags, fc = rhs_block(ghosted_block(fo, U, s, quad26=bool(mode & 4)), 3, gamma, dx, mode,
+                                        faces=True)
+            if flags:
+                raise ValueError("oracle flagged leaf %d (flags %d)" % (s, flags))
+            cache[s] = (o, a, fc)
+        return cache[s]
+
+    def corrected(s):
+        """Reading 3: corrections at faces towards finer leaves, x then y then z."""
+        o, a, fcs = leaf(s)
         L = int(fo.leaves[s, 0])
         b = fo.leaves[s, 1:]
         dx = dx0 / (1 << L)
-        corr = [np.zeros_like(outs[s]) for _ in range(3)]
+        corr = [np.zeros_like(o) for _ in range(3)]
         for d in range(3):
             ta, tb = _TANG[d]
             for side in (0, 1):
@@ -183,7 +190,7 @@ def rhs(leaves, nb0, U, dx0, gamma=5.0 / 3.0, mode=0):
                         beyond[d] += -1 if side == 0 else 1
                         if fo.leaf_at(L, beyond) is not None:
                             continue  # same level or coarser: nothing to correct here
-                        Fc = _face_flux(faces[s], d, c, 0 if side == 0 else N)
+                        Fc = _face_flux(fcs, d, c, 0 if side == 0 else N)
                         acc = None
                         for t in range(4):
                             gf = [2 * v for v in beyond]
@@ -194,12 +201,23 @@ def rhs(leaves, nb0, U, dx0, gamma=5.0 / 3.0, mode=0):
                             if hit is None or hit[1] != L + 1:
                                 raise ValueError("forest is not 2:1 balanced at leaf %d" % s)
                             sf, _, cf = hit
-                            Ff = _face_flux(faces[sf], d, fo.local(sf, cf), N if side == 0 else 0)
+                            Ff = _face_flux(leaf(sf)[2], d, fo.local(sf, cf), N if side == 0 else 0)
                             acc = Ff.copy() if acc is None else acc + Ff
                         mean = acc * 0.25
                         corr[d][:, c[2], c[1], c[0]] = sgn * (mean - Fc) / dx
         for d in range(3):
-            outs[s] = outs[s] + corr[d]
+            o = o + corr[d]
+        return o, a
+
+    if only is not None:
+        res = {s: corrected(int(s)) for s in only}
+        return {s: r[0] for s, r in res.items()}, {s: r[1] for s, r in res.items()}
+    outs, amax = [], np.zeros(n)
+    for s in range(n):
+        leaf(s)
+    for s in range(n):
+        o, amax[s] = corrected(s)
+        outs.append(o)
     return outs, amax
 
 

@@ -351,3 +351,28 @@ def test_sedov_on_a_forest():
     Rp, L1 = forest_shock_measures(lv, 2, U[:, 0], ex, r["t"])
     assert abs(Rp - ex.shock_radius(r["t"])) <= 1.0 / 32, (Rp, ex.shock_radius(r["t"]))
     assert U[:, 0].min() > 0 and L1 < 0.5
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", [hydro.FP64, MX])
+def test_bench_forest_full_size_sampled(prec):
+    """The forest of the benchmark (21848 leaves of 8^3 in three levels, 11.2M
+    cells, 11 fields) through the same entry point and launch shapes as
+    bench.forest_forms; sampled leaves of every kind (each level, coarse
+    leaves corrected by finer neighbours, fine leaves next to coarser ones)
+    against the forest oracle evaluated for those leaves only."""
+    nb0, radii = 16, (0.35, 0.2)
+    lv = synth.forest_leaves(nb0, 2, synth.sphere_refine((0.5, 0.5, 0.5), radii), balance="full")
+    U, dx0 = synth.smooth_forest_state(lv, nb0, 8, nf=11)
+    got, gam, info = _run(lv, nb0, U, dx0, prec)
+    assert info["n_leaves"] == 21848
+    kind, _ = hydro.forest_links(lv, nb0, 8)
+    rng = np.random.default_rng(53)
+    groups = [np.flatnonzero(lv[:, 0] == L) for L in range(3)]
+    groups.append(np.array([s for s in range(len(lv)) if 1 in kind[s]]))   # corrected by finer leaves
+    groups.append(np.array([s for s in range(len(lv)) if -1 in kind[s]]))  # next to coarser leaves
+    pick = sorted({int(x) for g in groups for x in rng.choice(g, 4, replace=False)})
+    mode = 0 if prec == hydro.FP64 else oracle.MODE_MIXED
+    ref, ram = of.rhs(lv, nb0, U, dx0, mode=mode, only=pick)
+    _check(prec, [got[s] for s in pick], gam[pick], [ref[s] for s in pick], np.array([ram[s] for s in pick]),
+           U[pick], [dx0 / (1 << int(lv[s, 0])) for s in pick])

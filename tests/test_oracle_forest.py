@@ -283,3 +283,15 @@ def test_full_balance_generator():
     for o in [(i, j, k) for k in (-1, 0, 1) for j in (-1, 0, 1) for i in (-1, 0, 1) if (i, j, k) != (0, 0, 0)]:
         nb = np.roll(owner, shift=(-o[2], -o[1], -o[0]), axis=(0, 1, 2))
         assert np.abs(lv[owner, 0] - lv[nb, 0]).max() <= 1
+
+
+def test_subset_evaluation_equals_the_full_one():
+    """`only=` (used for sampled checks of large forests) gives the full
+    evaluation's values for the chosen leaves, bit for bit."""
+    lv = _forest(7, 0.25)
+    U, dx0 = synth.smooth_forest_state(lv, NB0, N, nf=6, seed=25)
+    full, fam = of.rhs(lv, NB0, list(U), dx0)
+    pick = [0, 5, int(np.flatnonzero(lv[:, 0] == 0)[0]), int(np.flatnonzero(lv[:, 0] == 2)[0]), len(lv) - 1]
+    part, pam = of.rhs(lv, NB0, list(U), dx0, only=pick)
+    for s in pick:
+        assert np.array_equal(part[s], full[s]) and pam[s] == fam[s]
