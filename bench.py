@@ -321,14 +321,54 @@ def serving_run(rate, duration, per_task, budget=40 << 30, n_streams=4, max_batc
 
 
 # ------------------------------------------------------------- Sedov --
+def rk3_device_loop(step_pair, clock, t_end, stream, chunk=16):
+    """A time loop with the step computed on the device.  step_pair(forward)
+    runs one step (hydro_courant, then three *_stage_dt launches) from one
+    state buffer to the other (forward: first to second).  Two CUDA graphs of
+    `chunk` (even) steps are recorded, one per buffer the state starts in,
+    so a replay leaves it where it was.  Returns run(), which advances to
+    t_end: graph replays while t_end is more than 2 chunk dt away, single
+    steps after that (the device clamps the last dt to t_end), with one host
+    read of the clock per replay or step; run() returns (steps, whether the
+    final state is in the second buffer)."""
+    import torch
+
+    assert chunk % 2 == 0
+    graphs = {}
+    for first in (True, False):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for i in range(chunk):
+                step_pair(first == (i % 2 == 0))
+        graphs[first] = g
+
+    def run():
+        t, dt_last, k, at_first = 0.0, 0.0, 0, True
+        while t < t_end:
+            if dt_last > 0.0 and t_end - t > 2.0 * chunk * dt_last:
+                graphs[at_first].replay()
+            else:
+                step_pair(at_first)
+                at_first = not at_first
+            stream.synchronize()
+            c = clock.cpu()
+            t, dt_last, k = float(c[0]), float(c[1]), int(c[2])
+        return k, not at_first
+
+    return run
+
+
 def sedov_gpu_run(n=64, prec=0, cfl=0.3, t_end=None, dts=None, gamma=5.0 / 3.0, flags=0,
                   stream=None):
     """The Sedov point explosion (synth.sedov_domain, 11 fields) integrated on
     the GPU with SSP-RK3 steps of three fused stages of the domain form
     (ghost shells gathered in the kernel), to t_end or along `dts`.  The time
     step follows the rule of tests/sedov_run.py (dt = cfl dx / the largest
-    signal speed of the previous step's stages).  Returns a dict with the
-    final state (device, domain layout), t, the steps' dt and the wall time."""
+    signal speed of the previous step's stages); to t_end it is computed on
+    the device (hydro_courant) and the steps are replayed from CUDA graphs
+    (rk3_device_loop), along `dts` the host passes each dt.  Returns a dict
+    with the final state (device, domain layout), t, the steps' dt and the
+    wall time."""
     import torch
 
     import paper_2210_06438_gb300 as hydro
@@ -343,6 +383,37 @@ def sedov_gpu_run(n=64, prec=0, cfl=0.3, t_end=None, dts=None, gamma=5.0 / 3.0, 
     st = stream if stream is not None else torch.cuda.current_stream()
     kw = dict(gamma=gamma, prec=prec, stream=st, flags=flags)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dts is None:
+        # the time step on the device (hydro_courant + hydro_domain_stage_dt), CUDA-graph replay
+        st = stream if stream is not None else torch.cuda.Stream()
+        kw["stream"] = st
+        A, B = U, torch.empty_like(U)
+        clock = torch.zeros(3, dtype=torch.float64, device="cuda")
+        hist = torch.zeros(1 << 16, dtype=torch.float64, device="cuda")
+        dtp = clock[1:2]
+
+        def step_pair(forward):
+            src, dst = (A, B) if forward else (B, A)
+            hydro.courant(am, 3, nb ** 3, nb ** 3, clock, cfl, t_end, dx_uniform=dx, dt_hist=hist,
+                          hist_len=hist.numel(), stream=st)
+            hydro.domain_stage_dt(src, src, 0.0, 1.0, dtp, nb, N, nf, dx, W1, am[0], **kw)
+            hydro.domain_stage_dt(W1, src, 0.75, 0.25, dtp, nb, N, nf, dx, W2, am[1], **kw)
+            hydro.domain_stage_dt(W2, src, 1.0 / 3.0, 2.0 / 3.0, dtp, nb, N, nf, dx, dst, am[2], **kw)
+
+        torch.cuda.synchronize()
+        hydro.domain_rhs(A, nb, N, nf, dx, W1, am[0], **kw)  # first call on the device: setup
+        run = rk3_device_loop(step_pair, clock, t_end, st)
+        st.synchronize()
+        with torch.cuda.stream(st):
+            ev0.record(st)
+            hydro.domain_rhs(A, nb, N, nf, dx, W1, am[0], **kw)  # a_0
+            am[1:].copy_(am[0].expand(2, -1))
+            k, flipped = run()
+            ev1.record(st)
+        st.synchronize()
+        c = clock.cpu()
+        return {"U": B if flipped else A, "t": float(c[0]), "dts": hist[:k].cpu().tolist(), "steps": k,
+                "ms": ev0.elapsed_time(ev1), "n": n, "dx": dx}
     ev0.record(st)
     hydro.domain_rhs(U, nb, N, nf, dx, W1, am[0], **kw)
     a_next = float(am[0].max())
@@ -369,8 +440,10 @@ def sedov_forest_run(nb0=2, N=8, radii=(0.45, 0.25), prec=0, cfl=0.3, t_end=None
     forest stages (ghost slabs across levels, fused tiles, flux correction),
     to t_end or along `dts`.  One global step for all levels: dt = cfl min
     over leaves of dx_leaf / a_leaf, a_leaf the leaf's largest signal speed
-    over the previous step's stages.  Returns a dict with the final state
-    (device, [n][nf][N^3]), the leaves, t, the steps' dt and the wall time."""
+    over the previous step's stages (to t_end: on the device, steps replayed
+    from CUDA graphs, as in sedov_gpu_run).  Returns a dict with the final
+    state (device, [n][nf][N^3]), the leaves, t, the steps' dt and the wall
+    time."""
     import torch
 
     import paper_2210_06438_gb300 as hydro
@@ -386,6 +459,39 @@ def sedov_forest_run(nb0=2, N=8, radii=(0.45, 0.25), prec=0, cfl=0.3, t_end=None
     st = stream if stream is not None else torch.cuda.current_stream()
     kw = dict(gamma=gamma, prec=prec, stream=st, flags=flags)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dts is None:
+        # the time step on the device (hydro_courant + hydro_forest_stage_dt), CUDA-graph replay
+        st = stream if stream is not None else torch.cuda.Stream()
+        kw["stream"] = st
+        A, B = U, torch.empty_like(U)
+        clock = torch.zeros(3, dtype=torch.float64, device="cuda")
+        hist = torch.zeros(1 << 16, dtype=torch.float64, device="cuda")
+        dtp = clock[1:2]
+
+        def step_pair(forward):
+            src, dst = (A, B) if forward else (B, A)
+            hydro.courant(am, 3, n, n, clock, cfl, t_end, dx=dxs, dt_hist=hist, hist_len=hist.numel(),
+                          stream=st)
+            fo.stage_dt(src, src, 0.0, 1.0, dtp, dx0, W1, am[0], **kw)
+            fo.stage_dt(W1, src, 0.75, 0.25, dtp, dx0, W2, am[1], **kw)
+            fo.stage_dt(W2, src, 1.0 / 3.0, 2.0 / 3.0, dtp, dx0, dst, am[2], **kw)
+
+        torch.cuda.synchronize()
+        fo.rhs(A, dx0, W1, am[0], **kw)  # first call on the device: setup
+        run = rk3_device_loop(step_pair, clock, t_end, st)
+        st.synchronize()
+        with torch.cuda.stream(st):
+            ev0.record(st)
+            fo.rhs(A, dx0, W1, am[0], **kw)  # a_0
+            am[1:].copy_(am[0].expand(2, -1))
+            k, flipped = run()
+            ev1.record(st)
+        st.synchronize()
+        c = clock.cpu()
+        info = fo.info()
+        fo.close()
+        return {"U": B if flipped else A, "leaves": leaves, "t": float(c[0]), "dts": hist[:k].cpu().tolist(),
+                "steps": k, "ms": ev0.elapsed_time(ev1), "nb0": nb0, "dx0": dx0, "info": info}
     ev0.record(st)
     fo.rhs(U, dx0, W1, am[0], **kw)
     a_leaf = am[0].clone()

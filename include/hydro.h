@@ -277,6 +277,14 @@ int hydro_domain_stage(const double* U, const double* U0, double alpha, double b
                        int32_t nb, int32_t N, int32_t n_fields, double dx, double gamma,
                        double* U_out, double* out_amax, hydro_precision_t prec, void* stream,
                        uint32_t flags);
+/* hydro_domain_stage with dt read from DEVICE memory (one double, 8-byte
+ * aligned) when the kernel runs, e.g. written by hydro_courant earlier on
+ * the same stream: a time loop then needs no host round trip and records
+ * into a CUDA graph. */
+int hydro_domain_stage_dt(const double* U, const double* U0, double alpha, double beta,
+                          const double* dt, int32_t nb, int32_t N, int32_t n_fields, double dx,
+                          double gamma, double* U_out, double* out_amax, hydro_precision_t prec,
+                          void* stream, uint32_t flags);
 
 /* ---------------------------------------------------------------------------
  * Forests: the adaptive mesh of the paper's application (Cartesian adaptive
@@ -363,8 +371,32 @@ int hydro_forest_rhs(hydro_forest_t* forest, const double* U, double dx0, double
 int hydro_forest_stage(hydro_forest_t* forest, const double* U, const double* U0, double alpha,
                        double beta, double dt, double dx0, double gamma, double* U_out,
                        double* out_amax, hydro_precision_t prec, void* stream, uint32_t flags);
+/* hydro_forest_stage with dt read from DEVICE memory (as hydro_domain_stage_dt). */
+int hydro_forest_stage_dt(hydro_forest_t* forest, const double* U, const double* U0, double alpha,
+                          double beta, const double* dt, double dx0, double gamma, double* U_out,
+                          double* out_amax, hydro_precision_t prec, void* stream, uint32_t flags);
 /* Free the forest's device memory (synchronises its device). */
 int hydro_forest_destroy(hydro_forest_t* forest);
+
+/* ---------------------------------------------------------------------------
+ * hydro_courant -- the Courant time step on the device (one small launch on
+ * `stream`), from the largest signal speeds that earlier RHS or stage
+ * launches wrote (Sec. IV-B), so that explicit steps need no host round trip.
+ *   amax      DEVICE, n_rows rows of n values, row r at amax + r*row_stride
+ *             (row_stride >= n): e.g. the three stages of the previous step;
+ *             a_s = max over the rows of the sub-grid's value.
+ *   dx        DEVICE array of n cell widths (sub-grids of several levels):
+ *             q = cfl * min_s(dx_s / a_s); or NULL with dx_uniform > 0:
+ *             q = (cfl * dx_uniform) / max_s a_s.
+ *   clock     DEVICE, 3 doubles {t, dt, steps}, read and updated in place:
+ *             dt = min(q, t_end - t) (0 once t >= t_end), t += dt, steps += 1.
+ *   dt_hist   optional DEVICE array: dt_hist[steps] = dt while steps < hist_len.
+ * The paper has no such routine; it is the step rule of the time loops of the
+ * tests and benchmark moved onto the device.  HYDRO_EINVAL on null or
+ * misaligned pointers, n < 1, n_rows < 1, row_stride < n, cfl <= 0. */
+int hydro_courant(const double* amax, int32_t n_rows, int64_t row_stride, int64_t n,
+                  const double* dx, double dx_uniform, double cfl, double t_end, double* clock,
+                  double* dt_hist, int64_t hist_len, void* stream);
 
 /* ---------------------------------------------------------------------------
  * hydro_rhs_noalloc -- hydro_rhs_ex for callers that cannot allocate memory.

@@ -160,6 +160,11 @@ def load(build_if_missing: bool = False):
         "hydro_forest_stage": (ctypes.c_int, [P, P, P, dbl, dbl, dbl, dbl, dbl, P, P, ctypes.c_int,
                                               P, u32]),
         "hydro_forest_destroy": (ctypes.c_int, [P]),
+        "hydro_forest_stage_dt": (ctypes.c_int, [P, P, P, dbl, dbl, P, dbl, dbl, P, P, ctypes.c_int, P,
+                                                 u32]),
+        "hydro_domain_stage_dt": (ctypes.c_int, [P, P, dbl, dbl, P, i32, i32, i32, dbl, dbl, P, P,
+                                                 ctypes.c_int, P, u32]),
+        "hydro_courant": (ctypes.c_int, [P, i32, i64, i64, P, dbl, dbl, dbl, P, P, i64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -293,6 +298,13 @@ class Forest:
                                          _ptr(amax), int(prec), _stream(stream), int(flags)),
                "hydro_forest_stage")
 
+    def stage_dt(self, U, U0, alpha, beta, dt_dev, dx0, U_out, amax, gamma=5.0 / 3.0, prec=FP64,
+                 stream=None, flags=0):
+        _check(load().hydro_forest_stage_dt(self._h, _ptr(U), _ptr(U0), float(alpha), float(beta),
+                                            _ptr(dt_dev), float(dx0), float(gamma), _ptr(U_out),
+                                            _ptr(amax), int(prec), _stream(stream), int(flags)),
+               "hydro_forest_stage_dt")
+
     def info(self) -> dict:
         fi = ForestInfo()
         _check(load().hydro_forest_info(self._h, ctypes.byref(fi)), "hydro_forest_info")
@@ -308,6 +320,24 @@ class Forest:
             self.close()
         except Exception:
             pass
+
+
+def domain_stage_dt(U, U0, alpha, beta, dt_dev, nb, N, n_fields, dx, U_out, amax, gamma=5.0 / 3.0,
+                    prec=FP64, stream=None, flags=0):
+    """hydro_domain_stage_dt: the stage with dt read from device memory (dt_dev)."""
+    _check(load().hydro_domain_stage_dt(_ptr(U), _ptr(U0), float(alpha), float(beta), _ptr(dt_dev),
+                                        int(nb), int(N), int(n_fields), float(dx), float(gamma),
+                                        _ptr(U_out), _ptr(amax), int(prec), _stream(stream),
+                                        int(flags)), "hydro_domain_stage_dt")
+
+
+def courant(amax, n_rows, row_stride, n, clock, cfl, t_end, dx=None, dx_uniform=0.0, dt_hist=None,
+            hist_len=0, stream=None):
+    """hydro_courant: dt from the largest signal speeds, on the device."""
+    _check(load().hydro_courant(_ptr(amax), int(n_rows), int(row_stride), int(n),
+                                _ptr(dx) if dx is not None else None, float(dx_uniform), float(cfl),
+                                float(t_end), _ptr(clock), _ptr(dt_hist) if dt_hist is not None else None,
+                                int(hist_len), _stream(stream)), "hydro_courant")
 
 
 def rhs_per_subgrid(desc, out, amax, streams: Iterable, ghost=3, gamma=5.0 / 3.0, prec=FP64,

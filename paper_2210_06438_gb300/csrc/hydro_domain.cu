@@ -89,7 +89,8 @@ int domain_setup(DomDev** out) {
 
 int domain_launch(const double* U, const double* U0, double alpha, double beta, double dt, int stage,
                   int32_t nb, int32_t N, int32_t F, double dx, double gamma, double* out,
-                  double* amax, hydro_precision_t prec, void* stream, uint32_t flags) {
+                  double* amax, hydro_precision_t prec, void* stream, uint32_t flags,
+                  const double* dtp = nullptr) {
   if (!U || !out || !amax || (stage && !U0)) return HYDRO_EINVAL;
   if (nb < 1 || N < 2 || N > HYDRO_MAX_N || F < 6 || F > HYDRO_MAX_FIELDS) return HYDRO_EINVAL;
   if (nb * N < 6) return HYDRO_EINVAL;  // the ghost shell must not wrap onto the tile itself
@@ -121,7 +122,8 @@ int domain_launch(const double* U, const double* U0, double alpha, double beta, 
   int ex2;
   bool pow2 = std::frexp(dx, &ex2) == 0.5 && ex2 > -120 && ex2 < 120;
   hydro_dev::DomainTiles dom{U, nb, N, F, tpe, 1.0 / dx, (short)(pow2 ? 2 : 0)};
-  hydro_dev::StageArgs sa{U, stage ? U0 : U, alpha, beta, dt, stage};
+  if (dtp && (reinterpret_cast<uintptr_t>(dtp) & 7)) return HYDRO_EINVAL;
+  hydro_dev::StageArgs sa{U, stage ? U0 : U, alpha, beta, dt, stage, dtp};
   const int k = shape_of(prec, (flags & HYDRO_F_QUAD26) != 0);
   const Shape& sh = kShape[k];
   int nt = (int)n_tiles, lch = sh.lch, ws = 1, scheme = (flags & HYDRO_F_KNP) ? 1 : 0;
@@ -152,6 +154,15 @@ int hydro_domain_stage(const double* U, const double* U0, double alpha, double b
                        uint32_t flags) {
   return domain_launch(U, U0, alpha, beta, dt, 1, nb, N, n_fields, dx, gamma, U_out, out_amax, prec,
                        stream, flags);
+}
+
+int hydro_domain_stage_dt(const double* U, const double* U0, double alpha, double beta, const double* dt,
+                          int32_t nb, int32_t N, int32_t n_fields, double dx, double gamma,
+                          double* U_out, double* out_amax, hydro_precision_t prec, void* stream,
+                          uint32_t flags) {
+  if (!dt) return HYDRO_EINVAL;
+  return domain_launch(U, U0, alpha, beta, 0.0, 1, nb, N, n_fields, dx, gamma, U_out, out_amax, prec,
+                       stream, flags, dt);
 }
 
 }  // extern "C"

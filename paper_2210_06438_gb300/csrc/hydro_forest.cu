@@ -116,11 +116,13 @@ forest_ghost_kernel(const double* __restrict__ U, double* __restrict__ aux, cons
 // One thread per cell of the leaves that have finer face neighbours (rf),
 // all fields; cells not on such a face return at once.  The corrections of
 // the x, y and z faces are added in that order; `scale` is 1 for dU/dt and
-// beta dt for a stage.
+// beta dt for a stage (beta *dtp when dtp is set).
 __global__ void __launch_bounds__(256)
 forest_reflux_kernel(const int* __restrict__ links, const AuxDesc* __restrict__ desc,
                      const int* __restrict__ rf, int n_rf, int nl, int N, int F,
-                     const double* __restrict__ reg, double* __restrict__ out, double inv_dx0, double scale) {
+                     const double* __restrict__ reg, double* __restrict__ out, double inv_dx0, double scale,
+                     double beta, const double* __restrict__ dtp) {
+  if (dtp) scale = beta * __ldg(dtp);  // a stage whose dt is in device memory
   const long long nn = (long long)N * N, n3 = nn * N;
   const long long total = (long long)n_rf * n3;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -489,7 +491,7 @@ void release(hydro_forest* f) {
 
 int forest_launch(hydro_forest* fo, const double* U, const double* U0, double alpha, double beta, double dt,
                   int stage, double dx0, double gamma, double* out, double* amax, hydro_precision_t prec,
-                  void* stream, uint32_t flags) {
+                  void* stream, uint32_t flags, const double* dtp = nullptr) {
   if (!fo || !U || !out || !amax || (stage && !U0)) return HYDRO_EINVAL;
   if (flags & ~(uint32_t)(HYDRO_F_KNP | HYDRO_F_REGISTER_LOADS | HYDRO_F_QUAD26)) return HYDRO_EINVAL;
   const bool quad26 = (flags & HYDRO_F_QUAD26) != 0;
@@ -522,7 +524,8 @@ int forest_launch(hydro_forest* fo, const double* U, const double* U0, double al
     return hydro_host::cuda_fail(e, "cudaMemsetAsync(amax)");
   int ex2;
   const bool pow2 = std::frexp(dx0, &ex2) == 0.5 && ex2 > -120 && ex2 < 120;
-  hydro_dev::StageArgs sa{U, stage ? U0 : U, alpha, beta, dt, stage};
+  if (dtp && (reinterpret_cast<uintptr_t>(dtp) & 7)) return HYDRO_EINVAL;
+  hydro_dev::StageArgs sa{U, stage ? U0 : U, alpha, beta, dt, stage, dtp};
   int nt = (int)n_tiles, lch = kLch, ws = 1, scheme = (flags & HYDRO_F_KNP) ? 1 : 0;
   if (quad26) {
     // 1. the ghosted blocks, edges and corners included
@@ -577,7 +580,7 @@ int forest_launch(hydro_forest* fo, const double* U, const double* U0, double al
     const int g = (int)std::min<long long>((cells + 255) / 256, (long long)D->n_sm * 8);
     const double scale = stage ? beta * dt : 1.0;
     hydro_dev::forest_reflux_kernel<<<g, 256, 0, st>>>(fo->links, fo->desc, fo->rf, fo->n_rf, fo->nl, N, F,
-                                                       fo->reg, out, 1.0 / dx0, scale);
+                                                       fo->reg, out, 1.0 / dx0, scale, beta, stage ? dtp : nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return hydro_host::cuda_fail(e, "forest reflux launch");
   }
   return HYDRO_OK;
@@ -668,6 +671,13 @@ int hydro_forest_stage(hydro_forest_t* forest, const double* U, const double* U0
                        double dt, double dx0, double gamma, double* U_out, double* out_amax,
                        hydro_precision_t prec, void* stream, uint32_t flags) {
   return forest_launch(forest, U, U0, alpha, beta, dt, 1, dx0, gamma, U_out, out_amax, prec, stream, flags);
+}
+
+int hydro_forest_stage_dt(hydro_forest_t* forest, const double* U, const double* U0, double alpha, double beta,
+                          const double* dt, double dx0, double gamma, double* U_out, double* out_amax,
+                          hydro_precision_t prec, void* stream, uint32_t flags) {
+  if (!dt) return HYDRO_EINVAL;
+  return forest_launch(forest, U, U0, alpha, beta, 0.0, 1, dx0, gamma, U_out, out_amax, prec, stream, flags, dt);
 }
 
 int hydro_forest_destroy(hydro_forest_t* f) {

@@ -989,6 +989,8 @@ struct StageArgs {
   const double* __restrict__ U0;
   double alpha, beta, dt;
   int on;
+  const double* __restrict__ dtp;  // if set, dt is read here (device memory)
+  __device__ __forceinline__ double step() const { return dtp ? __ldg(dtp) : dt; }
 };
 
 // Store dU/dt = -(sum of differences)/dx of the fields f0 .. f0+nf-1 (or,
@@ -1026,7 +1028,7 @@ __device__ __forceinline__ void store_group(
             if constexpr (STAGE) {
               if (stage.on) {
                 long long e = (o - out) + j * n3;  // same index in U, U0 and out
-                v = fma(stage.alpha, __ldg(stage.U0 + e), stage.beta * fma(stage.dt, v, __ldg(stage.U + e)));
+                v = fma(stage.alpha, __ldg(stage.U0 + e), stage.beta * fma(stage.step(), v, __ldg(stage.U + e)));
               }
             }
             o[j * n3] = v;

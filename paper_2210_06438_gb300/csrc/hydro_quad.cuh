@@ -358,7 +358,7 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
               if constexpr (DOMAIN || CAP) {
                 if (stage.on) {
                   long long e = (o - out) + f * n3;  // same index in U, U0 and out
-                  v = fma(stage.alpha, __ldg(stage.U0 + e), stage.beta * fma(stage.dt, v, __ldg(stage.U + e)));
+                  v = fma(stage.alpha, __ldg(stage.U0 + e), stage.beta * fma(stage.step(), v, __ldg(stage.U + e)));
                 }
               }
               o[f * n3] = v;
