@@ -17,6 +17,7 @@ cores.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -614,6 +615,21 @@ def sedov_form(n, prec, flags=0):
 
 
 # ---------------------------------------------------------- cpu baseline --
+def oracle_small_configs(seconds=1.5):
+    """The oracle on the two small workloads: one 8^3 sub-grid with 6 fields
+    (iid cells) and the 64^3 periodic domain of 512 sub-grids with 11 fields
+    (smooth fields), at one thread and at all host cores."""
+    U1, dx1 = synth.one_subgrid(nf=6)
+    glob = synth.plain_domain(n=64, nf=11)
+    blocks = list(synth.gather_blocks(glob, 8))
+    res = {}
+    for name, bl, dx in (("one_subgrid_8^3_6_fields", [U1], dx1), ("plain_domain_64^3_11_fields", blocks, 1.0 / 64)):
+        r1, _, _ = oracle_sample_rate(bl, dx, seconds=seconds, threads=1)
+        ra, thr, _ = oracle_sample_rate(bl, dx, seconds=seconds)
+        res[name] = {"one_core": r1, "all_cores": ra, "cores": thr, "unit": "cell-updates/s"}
+    return res
+
+
 def cpu_model():
     """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
     import subprocess
@@ -764,9 +780,35 @@ def run_ours(args, rank, world):
     ps_sweep = {str(k): timed_pool(hydro.FP64, 1, pool[:k]) for k in (1, 4, 16) if k <= len(pool)}
     ps_sweep[str(len(pool))] = ms_ps64
 
+    # ---- the maximum-aggregation knob of strategy 3 (Sec. V-D, VI-B): the same
+    # sub-grids in launches of A sub-grids each (hydro_rhs_ex on consecutive
+    # slices of the descriptor array, round-robin over 8 streams)
+    agg_sweep = {"1": {"ms": ps_sweep.get("16", ms_ps64), "launches": batch.n,
+                       "note": "one launch per sub-grid (hydro_rhs_per_subgrid, 16 streams)"}}
+    sg_size = ctypes.sizeof(hydro.Subgrid)
+    desc_base = ctypes.addressof(batch.desc)
+    per_sub_doubles = batch.nf * 512
+
+    def run_agg(A, streams):
+        for k, i in enumerate(range(0, batch.n, A)):
+            d = ctypes.cast(desc_base + i * sg_size, ctypes.POINTER(hydro.Subgrid))
+            hydro.rhs(d, out.data_ptr() + i * per_sub_doubles * 8, amax.data_ptr() + i * 8, ghost=3,
+                      gamma=GAMMA, prec=hydro.FP64, stream=streams[k % len(streams)], n=min(A, batch.n - i))
+
+    for A in (16, 64, 256, 1024, 4096, batch.n):
+        run_agg(A, pool[:8])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run_agg(A, pool[:8])
+        torch.cuda.synchronize()
+        ms_a = (time.perf_counter() - t0) * 1e3
+        agg_sweep[str(A)] = {"ms": ms_a, "launches": -(-batch.n // A)}
+    for v in agg_sweep.values():
+        v["value"] = cells * world / (v["ms"] * 1e-3)
+
     # ---- per-replay distribution of the headline plan (CUDA events around each replay)
     reps = []
-    for _ in range(30):
+    for _ in range(50):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         plan64.execute(out, amax, stream)
@@ -930,7 +972,7 @@ def run_ours(args, rank, world):
                          "sub-grids" % (len(idx), reps),
                "one_core": {"value": rate1, "sample": "%d of those sub-grids, %d passes, 1 thread"
                                                       % (len(one), reps1)},
-               "cpu_model": cpu_model()}
+               "cpu_model": cpu_model(), "other_workloads": oracle_small_configs()}
 
     value = cells * world / (ms64 * 1e-3)
     line = {
@@ -960,6 +1002,7 @@ def run_ours(args, rank, world):
             "fp64_per_subgrid": {"value": cells * world / (ms_ps64 * 1e-3), "ms": ms_ps64,
                                  "streams": args.streams, "launches": batch.n,
                                  "ms_by_streams": ps_sweep},
+            "fp64_by_subgrids_per_launch": agg_sweep,
             "fp64_domain": {"value": cells * world / (ms_dom64 * 1e-3), "ms": ms_dom64,
                             "note": "ghost shells gathered in the kernel from ghost-free storage"},
             "mixed_domain": {"value": cells * world / (ms_dommx * 1e-3), "ms": ms_dommx,
