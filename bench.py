@@ -887,6 +887,8 @@ def run_ours(args, rank, world):
                                for s in range(batch.n)])
     plan_host = hydro.Plan(hdesc, ghost=3, gamma=GAMMA, prec=hydro.FP64, autotune=True, stream=stream,
                            n=batch.n)
+    info_host = {k: plan_host.info()[k] for k in ("threads_per_cta", "ctas_per_sm", "lines_per_chunk",
+                                                  "prefetch")}
     e2e_read = []
 
     def e2e_step():
@@ -988,7 +990,7 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
                 "how": "inputs and outputs in pinned host memory, read and written in place by the "
                        "kernel over NVLink-C2C (h2d = the read region's bytes); result read on the host",
-                "bitwise_equal_to_device_run": e2e_same,
+                "bitwise_equal_to_device_run": e2e_same, "plan": info_host,
                 "explicit_copies": {"value": cells * world / (ms_e2e_copy * 1e-3), "ms_per_step": ms_e2e_copy,
                                     "h2d_bytes_per_step": h2d_copy, "d2h_bytes_per_step": d2h}},
         "gpu_launches": args.steps,

@@ -213,7 +213,7 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
     int cands = 0;
     for (int vi = 0; vi < num_variants(); vi++)
       for (int li = 0; li < 3; li++)
-      for (int pf = 0; pf < 3; pf += 2) {
+      for (int pf = 0; pf < 3; pf++) {  // L2 prefetch: off, row segments, planes
         LaunchCfg c;
         variant(vi, &c);
         if (!variant_exists(prec, c)) continue;
