@@ -201,12 +201,15 @@ def _full_forest():
 
 
 @pytest.mark.parametrize("prec", [hydro.FP64, MX])
-@pytest.mark.parametrize("case", ["three_levels_8", "two_levels_16"])
+@pytest.mark.parametrize("case", ["three_levels_8", "two_levels_16", "two_levels_12", "three_levels_6"])
 def test_quad26_forest_matches_oracle(prec, case):
     if case == "three_levels_8":
         lv, nb0, N, nf = _full_forest(), 3, 8, 7
-    else:
-        lv, nb0, N, nf = synth.forest_leaves(1, 2, synth.random_refine(3, 0.6), seed=3, balance="full"), 1, 16, 6
+    elif case == "three_levels_6":  # the smallest leaf: a 3-cell slab is half a finer leaf
+        lv, nb0, N, nf = _full_forest(), 3, 6, 8
+    else:  # 16^3 (two tiles per edge) and 12^3 (partial tiles)
+        N = 16 if case == "two_levels_16" else 12
+        lv, nb0, nf = synth.forest_leaves(1, 2, synth.random_refine(3, 0.6), seed=3, balance="full"), 1, 6
     U, dx0 = synth.smooth_forest_state(lv, nb0, N, nf=nf, seed=48)
     got, gam, info = _run(lv, nb0, U, dx0, prec, flags=hydro.F_QUAD26)
     assert info["quad26"] == 1
