@@ -134,35 +134,46 @@ void fill_tile(Tile& t, const hydro_subgrid_t& d, int ghost, int64_t out_off, in
   t.flags = (short)((multi ? 1 : 0) | (pow2 ? 2 : 0));
 }
 
-// Work list: one Tile per 8^3 tile.  `order` (optional) permutes sub-grids.
+// Work list: one Tile per 8^3 tile, in descriptor order or (sort_by_cost)
+// the largest field counts first.  The fields of a sub-grid's tiles are
+// filled once and copied per tile.
 void build_tiles(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, std::vector<Tile>& tiles,
                  std::vector<int64_t>* first_tile, bool sort_by_cost, int* Fmax, bool* any_multi) {
   std::vector<int64_t> off(n + 1, 0);
-  for (int64_t s = 0; s < n; s++)
+  int64_t n_tiles = 0;
+  for (int64_t s = 0; s < n; s++) {
     off[s + 1] = off[s] + (int64_t)sg[s].n_fields * sg[s].N * sg[s].N * sg[s].N;
-  std::vector<int64_t> order(n);
-  for (int64_t s = 0; s < n; s++) order[s] = s;
-  if (sort_by_cost)  // largest field count first: the longest tiles start first
+    const int64_t nt = (sg[s].N + hydro_dev::TE - 1) / hydro_dev::TE;
+    n_tiles += nt * nt * nt;
+  }
+  std::vector<int64_t> order;
+  if (sort_by_cost) {  // largest field count first: the longest tiles start first
+    order.resize(n);
+    for (int64_t s = 0; s < n; s++) order[s] = s;
     std::stable_sort(order.begin(), order.end(),
                      [&](int64_t a, int64_t b) { return sg[a].n_fields > sg[b].n_fields; });
+  }
   tiles.clear();
+  tiles.reserve((size_t)n_tiles);
   if (first_tile) first_tile->assign(n + 1, 0);
   *Fmax = 6;
   *any_multi = false;
   for (int64_t k = 0; k < n; k++) {
-    int64_t s = order[k];
+    const int64_t s = sort_by_cost ? order[k] : k;
     const hydro_subgrid_t& d = sg[s];
-    int nt = (d.N + hydro_dev::TE - 1) / hydro_dev::TE;
-    bool multi = nt > 1;
+    const int nt = (d.N + hydro_dev::TE - 1) / hydro_dev::TE;
+    const bool multi = nt > 1;
     *any_multi |= multi;
     *Fmax = std::max(*Fmax, (int)d.n_fields);
     if (first_tile) (*first_tile)[s] = (int64_t)tiles.size();
+    Tile t;
+    fill_tile(t, d, ghost, off[s], s, (int)s, 0, 0, 0, multi);
     for (int tz = 0; tz < nt; tz++)
       for (int ty = 0; ty < nt; ty++)
         for (int tx = 0; tx < nt; tx++) {
-          Tile t;
-          memset(&t, 0, sizeof t);
-          fill_tile(t, d, ghost, off[s], s, (int)s, tx, ty, tz, multi);
+          t.ox = (short)(tx * hydro_dev::TE);
+          t.oy = (short)(ty * hydro_dev::TE);
+          t.oz = (short)(tz * hydro_dev::TE);
           tiles.push_back(t);
         }
   }
