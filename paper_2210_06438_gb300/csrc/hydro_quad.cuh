@@ -183,95 +183,65 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
       const int Sa = d == 0 ? LL : 1, Sb = d == 2 ? LL : LL * LL;
       const int Gd = d == 0 ? 1 : (d == 1 ? G : G * G);
       const int Ga = d == 0 ? G : 1, Gb = d == 2 ? G : G * G;
-      // ---- A2/A3: the faces of this direction, 9 points each
-#pragma unroll 1
-      for (int k = 0; k < QFPT; k++) {
-        const int face = tid + k * QNT, l = face / NFC, i = face - l * NFC;
+      if constexpr (MODE == 0) {
+        // ---- A2/A3: the faces of this direction, 9 points each.  Thread t
+        // walks three consecutive faces i0..i0+2 of line l = t/3.  The points
+        // are taken in pairs (o, -o): one reconstruction of cell c along
+        // e_d + o gives the left state at +o of face (c, c+1) (upper end) and
+        // the right state at -o of face (c-1, c) (lower end), one along e_d - o
+        // the other two, so every reconstruction serves two points; the centre
+        // point (o = 0) is one line along e_d.  The weighted point fluxes are
+        // summed in FF (the thread owns its faces' entries).
+        const int l = tid / 3, i0 = 3 * (tid - 3 * l);
         const int ca = l % TE, cb = l / TE;
-        const bool fvalid = ca < e_a && cb < e_b && i <= e_d;
-        // the low cell (i-1 along d) and the high cell (i)
-        const int il = qidx(0, 0, 0) + (i - 1) * Sd + ca * Sa + cb * Sb, ir = il + Sd;
-        const int gl0 = ogl + (i - 1) * Gd + ca * Ga + cb * Gb, gr0 = gl0 + Gd;
-        R fsum[MAXF];
-#pragma unroll
-        for (int f = 0; f < MAXF; f++) fsum[f] = R(0);
-        // faces outside a partial tile are skipped: their stencils may leave
-        // the stored block
-#pragma unroll 1
-        for (int p = 0; p < (fvalid ? 9 : 0); p++) {
-          const int o1 = p % 3 - 1, o2 = p / 3 - 1;
-          // lines e_d + o1 e_a + o2 e_b through the low cell, e_d - o1 e_a - o2 e_b
-          // through the high cell
-          const int sl = Sd + o1 * Sa + o2 * Sb, sr = Sd - o1 * Sa - o2 * Sb;
-          const int gsl = Gd + o1 * Ga + o2 * Gb, gsr = Gd - o1 * Ga - o2 * Gb;
-          R wl[MAXF], wr[MAXF];
-#pragma unroll
-          for (int f = 0; f < 6; f++) {
-            R ql[5], qr[5], lo, hi;
-#pragma unroll
-            for (int m = 0; m < 5; m++) {
-              ql[m] = P[f * QBLK + il + (m - 2) * sl];
-              qr[m] = P[f * QBLK + ir + (m - 2) * sr];
-            }
-            if constexpr (MODE == 0) {
-              ppm5_64(ql, lo, hi);
-              wl[f] = hi;
-              ppm5_64(qr, lo, hi);
-              wr[f] = lo;
-            } else {
-              ppm5_32(ql, lo, hi);
-              wl[f] = hi;
-              ppm5_32(qr, lo, hi);
-              wr[f] = lo;
-            }
+        const bool lvalid = ca < e_a && cb < e_b;
+        const int c_last = min(i0 + 2, e_d);  // the high cell of the last valid face
+  #pragma unroll
+        for (int k = 0; k < 3; k++)
+  #pragma unroll
+          for (int f = 0; f < MAXF; f++)
+            if (f < F) FF[f * QFACES + l * NFC + i0 + k] = R(0);
+        // shared-memory index and stored-block offset of the line's cell 0
+        const int is0 = qidx(0, 0, 0) + ca * Sa + cb * Sb;
+        const int gs0 = ogl + ca * Ga + cb * Gb;
+        // the 5 values of field f along e_d + s (o1 e_a + o2 e_b) through cell c
+        auto stencil = [&](int f, int c, int o1, int o2, int s, R* q) {
+          const int sm = Sd + s * (o1 * Sa + o2 * Sb), ic = is0 + c * Sd;
+          if (f < 6) {
+  #pragma unroll
+            for (int m = 0; m < 5; m++) q[m] = P[f * QBLK + ic + (m - 2) * sm];
+            return;
           }
-          // species X_k = rho_k / rho on the stencil cells
-#pragma unroll
-          for (int f = 6; f < MAXF; f++) {
-            if (f - 6 >= nsp) break;
-            const double* base = tile.U + f * plane;
-            R ql[5], qr[5], lo, hi;
-#pragma unroll
-            for (int m = 0; m < 5; m++) {
-              int ol, orr;
-              if constexpr (DOMAIN) {
-                // tile coordinates of the stencil cells (axis d, then a, b)
-                const int cd = i - 1, vd = 1;
-                const int lx = d == 0 ? cd + (m - 2) * vd : ca + (m - 2) * o1;
-                const int ly = d == 1 ? cd + (m - 2) * vd : (d == 0 ? ca + (m - 2) * o1 : cb + (m - 2) * o2);
-                const int lz = d == 2 ? cd + (m - 2) * vd : cb + (m - 2) * o2;
-                const int rx = d == 0 ? cd + 1 + (m - 2) * vd : ca - (m - 2) * o1;
-                const int ry = d == 1 ? cd + 1 + (m - 2) * vd : (d == 0 ? ca - (m - 2) * o1 : cb - (m - 2) * o2);
-                const int rz = d == 2 ? cd + 1 + (m - 2) * vd : cb - (m - 2) * o2;
-                ol = off_of(lx, ly, lz);
-                orr = off_of(rx, ry, rz);
-              } else {
-                ol = gl0 + (m - 2) * gsl;
-                orr = gr0 + (m - 2) * gsr;
-              }
-              const double ul = __ldg(base + ol), ur = __ldg(base + orr);
-              const R rl = RR[il + (m - 2) * sl], rr = RR[ir + (m - 2) * sr];
-              if constexpr (MODE == 0) {
-                ql[m] = ul * rl;
-                qr[m] = ur * rr;
-              } else {
-                ql[m] = d2f_int(ul) * rl;
-                qr[m] = d2f_int(ur) * rr;
-              }
-            }
-            if constexpr (MODE == 0) {
-              ppm5_64(ql, lo, hi);
-              wl[f] = hi;
-              ppm5_64(qr, lo, hi);
-              wr[f] = lo;
+          const double* base = tile.U + f * plane;
+  #pragma unroll
+          for (int m = 0; m < 5; m++) {
+            int og;
+            if constexpr (DOMAIN) {
+              const int t = c + (m - 2), u = ca + (m - 2) * s * o1, v = cb + (m - 2) * s * o2;
+              const int x = d == 0 ? t : u, y = d == 1 ? t : (d == 0 ? u : v), z = d == 2 ? t : v;
+              og = off_of(x, y, z);
             } else {
-              ppm5_32(ql, lo, hi);
-              wl[f] = hi;
-              ppm5_32(qr, lo, hi);
-              wr[f] = lo;
+              og = gs0 + c * Gd + (m - 2) * (Gd + s * (o1 * Ga + o2 * Gb));
             }
+            const double uq = __ldg(base + og);
+            const R r = RR[ic + (m - 2) * sm];
+            if constexpr (MODE == 0) q[m] = uq * r;
+            else q[m] = d2f_int(uq) * r;
           }
-          // central-upwind flux at the point
+        };
+        // lower and upper PPM values of every field of cell c along e_d + s o
+        auto ends = [&](int c, int o1, int o2, int s, R* lo, R* hi) {
+  #pragma unroll
+          for (int f = 0; f < MAXF; f++) {
+            if (f >= F) break;
+            R q[5];
+            stencil(f, c, o1, o2, s, q);
+            if constexpr (MODE == 0) ppm5_64(q, lo[f], hi[f]);
+            else ppm5_32(q, lo[f], hi[f]);
+          }
+        };
+        // central-upwind flux at one point of face i, weighted into FF
+        auto point = [&](int i, const R* wl, const R* wr, R cw) {
           R fh[MAXF], g_l, g_r, a;
           if constexpr (MODE == 0) {
             a = kt_hydro64(wl, wr, d, gamma, inv_gm1, knp, fh, 1, g_l, g_r);
@@ -282,25 +252,178 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
             a = kt_hydro32(pl, pr, d, gamma, inv_gm1, knp, fo, 1, g_l, g_r);
             fh[0] = fo[0].x, fh[1] = fo[0].y, fh[2] = fo[1].x, fh[3] = fo[1].y, fh[4] = fo[2].x, fh[5] = fo[2].y;
           }
-#pragma unroll
+  #pragma unroll
           for (int f = 6; f < MAXF; f++)
             if (f - 6 < nsp) {
               if constexpr (MODE == 0) fh[f] = fma(wl[f], g_l, wr[f] * g_r);
               else fh[f] = fmaf(wl[f], g_l, wr[f] * g_r);
             }
-          const R cw = R((o1 == 0 ? 4 : 1) * (o2 == 0 ? 4 : 1));
-#pragma unroll
+          R* ff = FF + l * NFC + i;
+  #pragma unroll
           for (int f = 0; f < MAXF; f++)
             if (f < F) {
-              if constexpr (MODE == 0) fsum[f] = fma(cw, fh[f], fsum[f]);
-              else fsum[f] = fmaf(cw, fh[f], fsum[f]);
+              if constexpr (MODE == 0) ff[f * QFACES] = fma(cw, fh[f], ff[f * QFACES]);
+              else ff[f * QFACES] = fmaf(cw, fh[f], ff[f * QFACES]);
             }
           if constexpr (MODE == 0) amax = dmaxp(amax, a);
           else amax = fmaxf(amax, a);
+        };
+        // pairs (o, -o) with o = (-1,-1), (0,-1), (1,-1), (-1,0), then the centre
+  #pragma unroll 1
+        for (int pp = 0; pp < (lvalid && i0 <= e_d ? 5 : 0); pp++) {
+          const int o1 = pp < 4 ? pp % 3 - 1 : 0, o2 = pp < 4 ? pp / 3 - 1 : 0;
+          const R cw = R((o1 == 0 ? 4 : 1) * (o2 == 0 ? 4 : 1));  // Simpson weight, same for -o
+          R Lp[MAXF], Lm[MAXF];  // left states at +o and -o of face (c, c+1), from cell c
+  #pragma unroll 1
+          for (int c = i0 - 1; c <= c_last; c++) {
+            if (pp < 4) {
+              // face (c-1, c): the right state at +o is the lower end along
+              // e_d - o, at -o the lower end along e_d + o
+              R lo_m[MAXF], hi_m[MAXF];
+              ends(c, o1, o2, -1, lo_m, hi_m);
+              if (c >= i0) point(c, Lp, lo_m, cw);
+              R lo_p[MAXF], hi_p[MAXF];
+              ends(c, o1, o2, 1, lo_p, hi_p);
+              if (c >= i0) point(c, Lm, lo_p, cw);
+  #pragma unroll
+              for (int f = 0; f < MAXF; f++) {
+                Lp[f] = hi_p[f];
+                Lm[f] = hi_m[f];
+              }
+            } else {
+              R lo_p[MAXF], hi_p[MAXF];
+              ends(c, 0, 0, 1, lo_p, hi_p);
+              if (c >= i0) point(c, Lp, lo_p, cw);
+  #pragma unroll
+              for (int f = 0; f < MAXF; f++) Lp[f] = hi_p[f];
+            }
+          }
         }
-#pragma unroll
-        for (int f = 0; f < MAXF; f++)
-          if (f < F) FF[f * QFACES + face] = fsum[f] / R(36);
+  #pragma unroll
+        for (int k = 0; k < 3; k++)
+  #pragma unroll
+          for (int f = 0; f < MAXF; f++)
+            if (f < F) FF[f * QFACES + l * NFC + i0 + k] /= R(36);
+      } else {
+        // ---- A2/A3: the faces of this direction, 9 points each
+  #pragma unroll 1
+        for (int k = 0; k < QFPT; k++) {
+          const int face = tid + k * QNT, l = face / NFC, i = face - l * NFC;
+          const int ca = l % TE, cb = l / TE;
+          const bool fvalid = ca < e_a && cb < e_b && i <= e_d;
+          // the low cell (i-1 along d) and the high cell (i)
+          const int il = qidx(0, 0, 0) + (i - 1) * Sd + ca * Sa + cb * Sb, ir = il + Sd;
+          const int gl0 = ogl + (i - 1) * Gd + ca * Ga + cb * Gb, gr0 = gl0 + Gd;
+          R fsum[MAXF];
+  #pragma unroll
+          for (int f = 0; f < MAXF; f++) fsum[f] = R(0);
+          // faces outside a partial tile are skipped: their stencils may leave
+          // the stored block
+  #pragma unroll 1
+          for (int p = 0; p < (fvalid ? 9 : 0); p++) {
+            const int o1 = p % 3 - 1, o2 = p / 3 - 1;
+            // lines e_d + o1 e_a + o2 e_b through the low cell, e_d - o1 e_a - o2 e_b
+            // through the high cell
+            const int sl = Sd + o1 * Sa + o2 * Sb, sr = Sd - o1 * Sa - o2 * Sb;
+            const int gsl = Gd + o1 * Ga + o2 * Gb, gsr = Gd - o1 * Ga - o2 * Gb;
+            R wl[MAXF], wr[MAXF];
+  #pragma unroll
+            for (int f = 0; f < 6; f++) {
+              R ql[5], qr[5], lo, hi;
+  #pragma unroll
+              for (int m = 0; m < 5; m++) {
+                ql[m] = P[f * QBLK + il + (m - 2) * sl];
+                qr[m] = P[f * QBLK + ir + (m - 2) * sr];
+              }
+              if constexpr (MODE == 0) {
+                ppm5_64(ql, lo, hi);
+                wl[f] = hi;
+                ppm5_64(qr, lo, hi);
+                wr[f] = lo;
+              } else {
+                ppm5_32(ql, lo, hi);
+                wl[f] = hi;
+                ppm5_32(qr, lo, hi);
+                wr[f] = lo;
+              }
+            }
+            // species X_k = rho_k / rho on the stencil cells
+  #pragma unroll
+            for (int f = 6; f < MAXF; f++) {
+              if (f - 6 >= nsp) break;
+              const double* base = tile.U + f * plane;
+              R ql[5], qr[5], lo, hi;
+  #pragma unroll
+              for (int m = 0; m < 5; m++) {
+                int ol, orr;
+                if constexpr (DOMAIN) {
+                  // tile coordinates of the stencil cells (axis d, then a, b)
+                  const int cd = i - 1, vd = 1;
+                  const int lx = d == 0 ? cd + (m - 2) * vd : ca + (m - 2) * o1;
+                  const int ly = d == 1 ? cd + (m - 2) * vd : (d == 0 ? ca + (m - 2) * o1 : cb + (m - 2) * o2);
+                  const int lz = d == 2 ? cd + (m - 2) * vd : cb + (m - 2) * o2;
+                  const int rx = d == 0 ? cd + 1 + (m - 2) * vd : ca - (m - 2) * o1;
+                  const int ry = d == 1 ? cd + 1 + (m - 2) * vd : (d == 0 ? ca - (m - 2) * o1 : cb - (m - 2) * o2);
+                  const int rz = d == 2 ? cd + 1 + (m - 2) * vd : cb - (m - 2) * o2;
+                  ol = off_of(lx, ly, lz);
+                  orr = off_of(rx, ry, rz);
+                } else {
+                  ol = gl0 + (m - 2) * gsl;
+                  orr = gr0 + (m - 2) * gsr;
+                }
+                const double ul = __ldg(base + ol), ur = __ldg(base + orr);
+                const R rl = RR[il + (m - 2) * sl], rr = RR[ir + (m - 2) * sr];
+                if constexpr (MODE == 0) {
+                  ql[m] = ul * rl;
+                  qr[m] = ur * rr;
+                } else {
+                  ql[m] = d2f_int(ul) * rl;
+                  qr[m] = d2f_int(ur) * rr;
+                }
+              }
+              if constexpr (MODE == 0) {
+                ppm5_64(ql, lo, hi);
+                wl[f] = hi;
+                ppm5_64(qr, lo, hi);
+                wr[f] = lo;
+              } else {
+                ppm5_32(ql, lo, hi);
+                wl[f] = hi;
+                ppm5_32(qr, lo, hi);
+                wr[f] = lo;
+              }
+            }
+            // central-upwind flux at the point
+            R fh[MAXF], g_l, g_r, a;
+            if constexpr (MODE == 0) {
+              a = kt_hydro64(wl, wr, d, gamma, inv_gm1, knp, fh, 1, g_l, g_r);
+            } else {
+              float2 pl[3] = {make_float2(wl[0], wl[1]), make_float2(wl[2], wl[3]), make_float2(wl[4], wl[5])};
+              float2 pr[3] = {make_float2(wr[0], wr[1]), make_float2(wr[2], wr[3]), make_float2(wr[4], wr[5])};
+              float2 fo[3];
+              a = kt_hydro32(pl, pr, d, gamma, inv_gm1, knp, fo, 1, g_l, g_r);
+              fh[0] = fo[0].x, fh[1] = fo[0].y, fh[2] = fo[1].x, fh[3] = fo[1].y, fh[4] = fo[2].x, fh[5] = fo[2].y;
+            }
+  #pragma unroll
+            for (int f = 6; f < MAXF; f++)
+              if (f - 6 < nsp) {
+                if constexpr (MODE == 0) fh[f] = fma(wl[f], g_l, wr[f] * g_r);
+                else fh[f] = fmaf(wl[f], g_l, wr[f] * g_r);
+              }
+            const R cw = R((o1 == 0 ? 4 : 1) * (o2 == 0 ? 4 : 1));
+  #pragma unroll
+            for (int f = 0; f < MAXF; f++)
+              if (f < F) {
+                if constexpr (MODE == 0) fsum[f] = fma(cw, fh[f], fsum[f]);
+                else fsum[f] = fmaf(cw, fh[f], fsum[f]);
+              }
+            if constexpr (MODE == 0) amax = dmaxp(amax, a);
+            else amax = fmaxf(amax, a);
+          }
+  #pragma unroll
+          for (int f = 0; f < MAXF; f++)
+            if (f < F) FF[f * QFACES + face] = fsum[f] / R(36);
+        }
       }
       __syncthreads();
       if constexpr (CAP) fetch.capture(tile, 0).template faces<QNT>(FF, QFACES, NLN, 0, F, d, ex, ey, ez);
