@@ -196,9 +196,9 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
         const int ca = l % TE, cb = l / TE;
         const bool lvalid = ca < e_a && cb < e_b;
         const int c_last = min(i0 + 2, e_d);  // the high cell of the last valid face
-  #pragma unroll
+#pragma unroll
         for (int k = 0; k < 3; k++)
-  #pragma unroll
+#pragma unroll
           for (int f = 0; f < MAXF; f++)
             if (f < F) FF[f * QFACES + l * NFC + i0 + k] = R(0);
         // shared-memory index and stored-block offset of the line's cell 0
@@ -208,12 +208,12 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
         auto stencil = [&](int f, int c, int o1, int o2, int s, R* q) {
           const int sm = Sd + s * (o1 * Sa + o2 * Sb), ic = is0 + c * Sd;
           if (f < 6) {
-  #pragma unroll
+#pragma unroll
             for (int m = 0; m < 5; m++) q[m] = P[f * QBLK + ic + (m - 2) * sm];
             return;
           }
           const double* base = tile.U + f * plane;
-  #pragma unroll
+#pragma unroll
           for (int m = 0; m < 5; m++) {
             int og;
             if constexpr (DOMAIN) {
@@ -223,58 +223,38 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
             } else {
               og = gs0 + c * Gd + (m - 2) * (Gd + s * (o1 * Ga + o2 * Gb));
             }
-            const double uq = __ldg(base + og);
-            const R r = RR[ic + (m - 2) * sm];
-            if constexpr (MODE == 0) q[m] = uq * r;
-            else q[m] = d2f_int(uq) * r;
+            q[m] = __ldg(base + og) * RR[ic + (m - 2) * sm];
           }
         };
         // lower and upper PPM values of every field of cell c along e_d + s o
         auto ends = [&](int c, int o1, int o2, int s, R* lo, R* hi) {
-  #pragma unroll
+#pragma unroll
           for (int f = 0; f < MAXF; f++) {
             if (f >= F) break;
             R q[5];
             stencil(f, c, o1, o2, s, q);
-            if constexpr (MODE == 0) ppm5_64(q, lo[f], hi[f]);
-            else ppm5_32(q, lo[f], hi[f]);
+            ppm5_64(q, lo[f], hi[f]);
           }
         };
         // central-upwind flux at one point of face i, weighted into FF
         auto point = [&](int i, const R* wl, const R* wr, R cw) {
-          R fh[MAXF], g_l, g_r, a;
-          if constexpr (MODE == 0) {
-            a = kt_hydro64(wl, wr, d, gamma, inv_gm1, knp, fh, 1, g_l, g_r);
-          } else {
-            float2 pl[3] = {make_float2(wl[0], wl[1]), make_float2(wl[2], wl[3]), make_float2(wl[4], wl[5])};
-            float2 pr[3] = {make_float2(wr[0], wr[1]), make_float2(wr[2], wr[3]), make_float2(wr[4], wr[5])};
-            float2 fo[3];
-            a = kt_hydro32(pl, pr, d, gamma, inv_gm1, knp, fo, 1, g_l, g_r);
-            fh[0] = fo[0].x, fh[1] = fo[0].y, fh[2] = fo[1].x, fh[3] = fo[1].y, fh[4] = fo[2].x, fh[5] = fo[2].y;
-          }
-  #pragma unroll
-          for (int f = 6; f < MAXF; f++)
-            if (f - 6 < nsp) {
-              if constexpr (MODE == 0) fh[f] = fma(wl[f], g_l, wr[f] * g_r);
-              else fh[f] = fmaf(wl[f], g_l, wr[f] * g_r);
-            }
+          R fh[6], g_l, g_r;
+          const R a = kt_hydro64(wl, wr, d, gamma, inv_gm1, knp, fh, 1, g_l, g_r);
           R* ff = FF + l * NFC + i;
-  #pragma unroll
-          for (int f = 0; f < MAXF; f++)
-            if (f < F) {
-              if constexpr (MODE == 0) ff[f * QFACES] = fma(cw, fh[f], ff[f * QFACES]);
-              else ff[f * QFACES] = fmaf(cw, fh[f], ff[f * QFACES]);
-            }
-          if constexpr (MODE == 0) amax = dmaxp(amax, a);
-          else amax = fmaxf(amax, a);
+#pragma unroll
+          for (int f = 0; f < 6; f++) ff[f * QFACES] = fma(cw, fh[f], ff[f * QFACES]);
+#pragma unroll
+          for (int f = 6; f < MAXF; f++)
+            if (f - 6 < nsp) ff[f * QFACES] = fma(cw, fma(wl[f], g_l, wr[f] * g_r), ff[f * QFACES]);
+          amax = dmaxp(amax, a);
         };
         // pairs (o, -o) with o = (-1,-1), (0,-1), (1,-1), (-1,0), then the centre
-  #pragma unroll 1
+#pragma unroll 1
         for (int pp = 0; pp < (lvalid && i0 <= e_d ? 5 : 0); pp++) {
           const int o1 = pp < 4 ? pp % 3 - 1 : 0, o2 = pp < 4 ? pp / 3 - 1 : 0;
           const R cw = R((o1 == 0 ? 4 : 1) * (o2 == 0 ? 4 : 1));  // Simpson weight, same for -o
           R Lp[MAXF], Lm[MAXF];  // left states at +o and -o of face (c, c+1), from cell c
-  #pragma unroll 1
+#pragma unroll 1
           for (int c = i0 - 1; c <= c_last; c++) {
             if (pp < 4) {
               // face (c-1, c): the right state at +o is the lower end along
@@ -285,7 +265,7 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
               R lo_p[MAXF], hi_p[MAXF];
               ends(c, o1, o2, 1, lo_p, hi_p);
               if (c >= i0) point(c, Lm, lo_p, cw);
-  #pragma unroll
+#pragma unroll
               for (int f = 0; f < MAXF; f++) {
                 Lp[f] = hi_p[f];
                 Lm[f] = hi_m[f];
@@ -294,19 +274,19 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
               R lo_p[MAXF], hi_p[MAXF];
               ends(c, 0, 0, 1, lo_p, hi_p);
               if (c >= i0) point(c, Lp, lo_p, cw);
-  #pragma unroll
+#pragma unroll
               for (int f = 0; f < MAXF; f++) Lp[f] = hi_p[f];
             }
           }
         }
-  #pragma unroll
+#pragma unroll
         for (int k = 0; k < 3; k++)
-  #pragma unroll
+#pragma unroll
           for (int f = 0; f < MAXF; f++)
             if (f < F) FF[f * QFACES + l * NFC + i0 + k] /= R(36);
       } else {
         // ---- A2/A3: the faces of this direction, 9 points each
-  #pragma unroll 1
+#pragma unroll 1
         for (int k = 0; k < QFPT; k++) {
           const int face = tid + k * QNT, l = face / NFC, i = face - l * NFC;
           const int ca = l % TE, cb = l / TE;
@@ -315,11 +295,11 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
           const int il = qidx(0, 0, 0) + (i - 1) * Sd + ca * Sa + cb * Sb, ir = il + Sd;
           const int gl0 = ogl + (i - 1) * Gd + ca * Ga + cb * Gb, gr0 = gl0 + Gd;
           R fsum[MAXF];
-  #pragma unroll
+#pragma unroll
           for (int f = 0; f < MAXF; f++) fsum[f] = R(0);
           // faces outside a partial tile are skipped: their stencils may leave
           // the stored block
-  #pragma unroll 1
+#pragma unroll 1
           for (int p = 0; p < (fvalid ? 9 : 0); p++) {
             const int o1 = p % 3 - 1, o2 = p / 3 - 1;
             // lines e_d + o1 e_a + o2 e_b through the low cell, e_d - o1 e_a - o2 e_b
@@ -327,10 +307,10 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
             const int sl = Sd + o1 * Sa + o2 * Sb, sr = Sd - o1 * Sa - o2 * Sb;
             const int gsl = Gd + o1 * Ga + o2 * Gb, gsr = Gd - o1 * Ga - o2 * Gb;
             R wl[MAXF], wr[MAXF];
-  #pragma unroll
+#pragma unroll
             for (int f = 0; f < 6; f++) {
               R ql[5], qr[5], lo, hi;
-  #pragma unroll
+#pragma unroll
               for (int m = 0; m < 5; m++) {
                 ql[m] = P[f * QBLK + il + (m - 2) * sl];
                 qr[m] = P[f * QBLK + ir + (m - 2) * sr];
@@ -348,12 +328,12 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
               }
             }
             // species X_k = rho_k / rho on the stencil cells
-  #pragma unroll
+#pragma unroll
             for (int f = 6; f < MAXF; f++) {
               if (f - 6 >= nsp) break;
               const double* base = tile.U + f * plane;
               R ql[5], qr[5], lo, hi;
-  #pragma unroll
+#pragma unroll
               for (int m = 0; m < 5; m++) {
                 int ol, orr;
                 if constexpr (DOMAIN) {
@@ -404,14 +384,14 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
               a = kt_hydro32(pl, pr, d, gamma, inv_gm1, knp, fo, 1, g_l, g_r);
               fh[0] = fo[0].x, fh[1] = fo[0].y, fh[2] = fo[1].x, fh[3] = fo[1].y, fh[4] = fo[2].x, fh[5] = fo[2].y;
             }
-  #pragma unroll
+#pragma unroll
             for (int f = 6; f < MAXF; f++)
               if (f - 6 < nsp) {
                 if constexpr (MODE == 0) fh[f] = fma(wl[f], g_l, wr[f] * g_r);
                 else fh[f] = fmaf(wl[f], g_l, wr[f] * g_r);
               }
             const R cw = R((o1 == 0 ? 4 : 1) * (o2 == 0 ? 4 : 1));
-  #pragma unroll
+#pragma unroll
             for (int f = 0; f < MAXF; f++)
               if (f < F) {
                 if constexpr (MODE == 0) fsum[f] = fma(cw, fh[f], fsum[f]);
@@ -420,7 +400,7 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
             if constexpr (MODE == 0) amax = dmaxp(amax, a);
             else amax = fmaxf(amax, a);
           }
-  #pragma unroll
+#pragma unroll
           for (int f = 0; f < MAXF; f++)
             if (f < F) FF[f * QFACES + face] = fsum[f] / R(36);
         }
