@@ -16,9 +16,13 @@
 //          with each coordinate in [-3, e+2] and at most one of them at -3 or
 //          e+2) into shared memory; species are read through the read-only
 //          cache and divided by rho on use;
-//   faces  per direction, each thread owns three of the 576 faces and sums the
-//          weighted fluxes of its 9 points in registers, then writes the face
-//          fluxes to shared memory;
+//   faces  per direction, each thread owns three of the 576 faces.  Binary64:
+//          the three are consecutive faces of one line, walked with the
+//          points in pairs (o, -o) so that each single-cell reconstruction
+//          gives a state at two points; the weighted point fluxes are summed
+//          in shared memory.  Mixed: every point's two states are
+//          reconstructed and the weighted fluxes summed in registers (fewer
+//          live values: two CTAs per SM without spills);
 //   A4     each thread owns up to three cells and accumulates x, y, z flux
 //          differences (binary64, or exact binary32 pairs in the mixed form).
 #pragma once
