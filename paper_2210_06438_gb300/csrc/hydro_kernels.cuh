@@ -193,8 +193,13 @@ __device__ __forceinline__ double dabs(double x) {
 __device__ __forceinline__ double dcopysign(double m, double s) {  // |m| with the sign of s
   return __hiloint2double((hiw(m) & 0x7fffffff) | (hiw(s) & 0x80000000), __double2loint(m));
 }
-__device__ __forceinline__ double dtwice(double x) {  // 2x, x non-zero
-  return __hiloint2double(hiw(x) + 0x00100000, __double2loint(x));
+// 2x, x non-zero: one integer add to the exponent field.  Written in PTX so
+// that the compiler keeps it on the integer pipe (in plain C it may be
+// recognised as x + x and issued to the binary64 pipe, the scarce one here).
+__device__ __forceinline__ double dtwice(double x) {
+  long long b = __double_as_longlong(x);
+  asm("add.s64 %0, %0, 0x0010000000000000;" : "+l"(b));
+  return __longlong_as_double(b);
 }
 __device__ __forceinline__ double dhalf(double x) {  // x/2 (zero stays zero)
   int h = hiw(x);
