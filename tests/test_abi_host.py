@@ -70,3 +70,26 @@ def test_plan_and_server_argument_checks(lib):
         hydro.Server(budget_bytes=0, dry_run_ns=1000)
     with pytest.raises(hydro.HydroError):
         hydro.Server(n_streams=0, dry_run_ns=1000)
+
+
+def test_time_step_entry_points_check_arguments_before_the_device(lib):
+    """hydro_courant and the stages that read dt from device memory refuse bad
+    arguments without touching a GPU."""
+    P = 0x10000  # an aligned address that is never dereferenced
+    bad = [
+        dict(amax=0), dict(n_rows=0), dict(row_stride=3), dict(n=0), dict(cfl=0.0),
+        dict(cfl=float("nan")), dict(clock=0), dict(dx=0, dx_uniform=0.0), dict(hist_len=4, dt_hist=0),
+        dict(amax=P + 4),  # misaligned
+    ]
+    for kw in bad:
+        a = dict(amax=P, n_rows=3, row_stride=8, n=8, dx=0, dx_uniform=0.1, cfl=0.3, t_end=1.0, clock=P,
+                 dt_hist=0, hist_len=0)
+        a.update(kw)
+        rc = lib.hydro_courant(a["amax"], a["n_rows"], a["row_stride"], a["n"], a["dx"], a["dx_uniform"],
+                               a["cfl"], a["t_end"], a["clock"], a["dt_hist"], a["hist_len"], None)
+        assert rc == hydro.HYDRO_EINVAL, kw
+    # a null dt pointer
+    assert lib.hydro_domain_stage_dt(P, P, 0.0, 1.0, None, 4, 8, 6, 0.1, 5.0 / 3.0, P * 2, P, 0, None,
+                                     0) == hydro.HYDRO_EINVAL
+    assert lib.hydro_forest_stage_dt(None, P, P, 0.0, 1.0, P, 0.1, 5.0 / 3.0, P * 2, P, 0, None,
+                                     0) == hydro.HYDRO_EINVAL
