@@ -308,3 +308,33 @@ def test_pinned_host_buffers_are_read_in_place(prec):
     p.close()
     assert np.array_equal(amax.numpy(), ram)
     assert np.array_equal(out[:ref[0].size].numpy().reshape(ref[0].shape), ref[0])
+
+
+@pytest.mark.parametrize("prec,flags", [(hydro.FP64, 0), (hydro.FP32_FLUX_FP64_ACC, 0), (hydro.FP64, hydro.F_QUAD26),
+                                        (hydro.FP32_FLUX_FP64_ACC, hydro.F_REGISTER_LOADS)])
+def test_flux_homogeneity_under_power_of_two_scaling(prec, flags):
+    """The property the oracle pin checks, on the GPU path: rho, rho v, E,
+    rho X scaled by lam and tau by mu (powers of two, thermal data) scale each
+    field's dU/dt by exactly that factor and leave amax unchanged, bit for
+    bit, through every kernel step (seeds, Newton steps, conversions)."""
+    rng = synth.rng_for(92, 0)
+    G, nf, n = 14, 8, 6
+    blocks = []
+    for _ in range(n):
+        rho = rng.uniform(0.5, 2.0, (G, G, G))
+        v = [rng.normal(0.0, 0.1, (G, G, G)) for _ in range(3)]
+        p = rng.uniform(0.5, 2.0, (G, G, G))
+        X = np.moveaxis(rng.dirichlet(np.ones(nf - 6), size=(G, G, G)), -1, 0)
+        blocks.append(synth.conserved_from_states(rho, v[0], v[1], v[2], p, X))
+    ref, ra = gh.run_gpu(gh.to_dev(blocks), [0.125] * n, prec=prec, flags=flags)
+    for lam, mu in ((4.0, 0.125), (0.25, 2.0)):
+        scaled = []
+        for b in blocks:
+            V = b * lam
+            V[5] = b[5] * mu
+            scaled.append(V)
+        got, ga = gh.run_gpu(gh.to_dev(scaled), [0.125] * n, prec=prec, flags=flags)
+        assert np.array_equal(ga, ra)
+        for s in range(n):
+            for f in range(nf):
+                assert np.array_equal(got[s][f], ref[s][f] * (mu if f == 5 else lam)), (s, f, lam)
