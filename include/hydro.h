@@ -303,8 +303,9 @@ int hydro_domain_stage_dt(const double* U, const double* U0, double alpha, doubl
  *   - finer neighbours (four leaves): each ghost cell takes the mean of the
  *     eight fine cells it covers, summed in the order i + 2j + 4k of their
  *     offsets, times 1/8 (restriction).
- * Then the tile kernel runs on every leaf (face-centre scheme) and records
- * the fluxes through faces towards other levels; last, every coarse cell
+ * Then the tile kernel runs on every leaf (face-centre scheme, or the
+ * 26-point variant: see the flags below) and records the fluxes through
+ * faces towards other levels; last, every coarse cell
  * next to finer leaves has the flux through that face replaced by the mean
  * of the four fine fluxes (summed (0,0), (1,0), (0,1), (1,1) over the two
  * tangential offsets, times 1/4; x, then y, then z faces), so that the RHS
@@ -327,7 +328,8 @@ typedef struct {
   int32_t n_reflux_leaves;  /* leaves with at least one finer face neighbour */
   int32_t quad26;           /* 1 if edge and corner neighbours also differ by at most one
                                level, so that HYDRO_F_QUAD26 is accepted */
-  int64_t device_bytes;     /* tables, auxiliary blocks and flux registers */
+  int64_t device_bytes;     /* tables, auxiliary blocks and flux registers (and the ghosted
+                               blocks once a 26-point call has allocated them) */
 } hydro_forest_info_t;
 
 /* Face neighbours of a forest's leaves, computed on the host (no GPU call):
