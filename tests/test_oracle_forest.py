@@ -297,17 +297,20 @@ def test_subset_evaluation_equals_the_full_one():
         assert np.array_equal(part[s], full[s]) and pam[s] == fam[s]
 
 
-def test_forest_homogeneity_under_power_of_two_scaling():
+@pytest.mark.parametrize("quad26", [False, True])
+def test_forest_homogeneity_under_power_of_two_scaling(quad26):
     """The homogeneity pin on a three-level forest: the level transfer
     (copies and means of 8), the per-leaf RHS and the flux correction all
     scale exactly, so scaling rho, rho v, E, rho X by 4 and tau by 1/8 scales
-    every leaf's dU/dt by the same factor, bit for bit."""
-    lv = _forest(4, 0.25)
-    U, dx0 = synth.smooth_forest_state(lv, NB0, N, nf=7, seed=26)
-    ref, ram = of.rhs(lv, NB0, list(U), dx0)
+    every leaf's dU/dt by the same factor, bit for bit (face-centre scheme,
+    and the 26-point variant on a fully balanced forest)."""
+    lv, nb0 = (_full_forest(), 3) if quad26 else (_forest(4, 0.25), NB0)
+    mode = oracle.QUAD26 if quad26 else 0
+    U, dx0 = synth.smooth_forest_state(lv, nb0, N, nf=7, seed=26)
+    ref, ram = of.rhs(lv, nb0, list(U), dx0, mode=mode)
     V = U * 4.0
     V[:, 5] = U[:, 5] * 0.125
-    got, gam = of.rhs(lv, NB0, list(V), dx0)
+    got, gam = of.rhs(lv, nb0, list(V), dx0, mode=mode)
     assert np.array_equal(gam, ram)
     for s in range(len(lv)):
         for f in range(7):
