@@ -379,3 +379,20 @@ def test_bench_forest_full_size_sampled(prec):
     ref, ram = of.rhs(lv, nb0, U, dx0, mode=mode, only=pick)
     _check(prec, [got[s] for s in pick], gam[pick], [ref[s] for s in pick], np.array([ram[s] for s in pick]),
            U[pick], [dx0 / (1 << int(lv[s, 0])) for s in pick])
+
+
+@pytest.mark.parametrize("prec,flags", [(hydro.FP64, 0), (MX, 0), (hydro.FP64, hydro.F_QUAD26)])
+def test_forest_homogeneity_under_power_of_two_scaling(prec, flags):
+    """Level transfers, tiles and flux correction scale exactly: rho, rho v,
+    E, rho X times 4 and tau times 1/8 scale every leaf's dU/dt by the same
+    factor on the GPU, bit for bit, and leave amax unchanged."""
+    lv = _full_forest()
+    U, dx0 = synth.smooth_forest_state(lv, 3, 8, nf=7, seed=54)
+    ref, ra, _ = _run(lv, 3, U, dx0, prec, flags=flags)
+    V = U * 4.0
+    V[:, 5] = U[:, 5] * 0.125
+    got, ga, _ = _run(lv, 3, V, dx0, prec, flags=flags)
+    assert np.array_equal(ga, ra)
+    for s in range(len(lv)):
+        for f in range(7):
+            assert np.array_equal(got[s][f], ref[s][f] * (0.125 if f == 5 else 4.0)), (s, f)
