@@ -177,6 +177,53 @@ def time_steps(fn, steps, warmup, stream):
     return a.elapsed_time(b) / steps
 
 
+def time_flushed(fn, steps, warmup, stream, flush=None):
+    """Per-step CUDA-event times (ms) of fn on `stream`, with an L2 flush
+    (a write of a buffer larger than L2) before every step, outside the
+    events.  Returns (median, p10, p90)."""
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    ts = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return (float(np.median(ts)), float(np.percentile(ts, 10)), float(np.percentile(ts, 90)))
+
+
+def fp64_probe_peak(stream, reps=7, iters=20000):
+    """Measured binary64 peak (GFLOP/s): the library's fused multiply-add
+    probe (hydro_probe_fp64), timed with CUDA events on `stream`, median of
+    `reps` launches after one warm-up launch."""
+    import torch
+
+    import paper_2210_06438_gb300 as hydro
+
+    hydro.probe_fp64(4, 1000, stream)
+    ts = []
+    n = 0.0
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        n = hydro.probe_fp64(4, iters, stream)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.median(ts))
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return {"gflops": 2.0 * n / (ms * 1e-3) * 1e-9, "ms": ms, "fma_per_launch": n, "sms": n_sm,
+            "launches": reps}
+
+
 def normwise_error(got, ref, ref_amax, batch):
     """max over (sub-grid, field) of max|got - ref| / max(max|ref|, S), with
     the flux-divergence floor S = amax * max|U_f| / dx of the parity tests."""
@@ -630,6 +677,37 @@ def oracle_small_configs(seconds=1.5):
     return res
 
 
+def oracle_sample_parity(blocks_host, dx, gpu):
+    """The GPU results of the benchmark workload against the oracle on the
+    CPU-baseline sample (each sub-grid whole): binary64 form against the
+    oracle's binary64 mode under the 1e-12 gate of the parity tests, the
+    mixed form's normwise error against the binary64 oracle (per sub-grid and
+    field, max|gpu - oracle| / max|oracle|, worst over the sample) and against
+    the oracle's mixed mode in binary32 ulps of the flux-divergence scale."""
+    import oracle
+
+    threads = os.cpu_count() or 1
+    ref, ram, fl = oracle.rhs_batch(blocks_host, GAMMA, dx, 0, threads=threads)
+    ref1, ram1, _ = oracle.rhs_batch(blocks_host, GAMMA, dx, 1, threads=threads)
+    n = len(blocks_host)
+    nf = blocks_host[0].shape[0]
+    r0 = np.stack([r.reshape(nf, -1) for r in ref])
+    r1 = np.stack([r.reshape(nf, -1) for r in ref1])
+    umax = np.stack([np.abs(b).reshape(nf, -1).max(axis=1) for b in blocks_host])
+    floor = ram[:, None] * umax / dx
+    fp64 = (np.abs(gpu["fp64"] - r0).max(axis=2) / np.maximum(np.maximum(np.abs(r0).max(axis=2), floor),
+                                                               1e-300)).max()
+    mx = (np.abs(gpu["mixed"] - r0).max(axis=2) / np.maximum(np.abs(r0).max(axis=2), 1e-300)).max()
+    S32 = 2.0 * ram1[:, None] * (umax + np.where((np.arange(nf) >= 1) & (np.arange(nf) <= 4), umax[:, 4:5], 0.0))
+    ulps = (np.abs(gpu["mixed"] - r1).max(axis=2) / (2.0 ** -24 * S32 / dx)).max()
+    return {"subgrids": n, "oracle_flags": int(fl.any()),
+            "fp64_vs_oracle_err_over_1e-12": float(fp64 / 1e-12),
+            "fp64_amax_rel": float((np.abs(gpu["fp64_amax"] - ram) / ram).max()),
+            "mixed_vs_oracle_fp64_normwise": float(mx),
+            "mixed_vs_oracle_mixed_ulps_of_S32": float(ulps),
+            "mixed_amax_rel_vs_oracle_mixed": float((np.abs(gpu["mixed_amax"] - ram1) / ram1).max())}
+
+
 def cpu_model():
     """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
     import subprocess
@@ -707,6 +785,157 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ smaller workloads --
+def small_workloads(stream, steps, warmup, streams_pool):
+    """The three smaller workloads of the benchmark suite, each timed on the
+    GPU in the aggregated form and the one-launch-per-sub-grid form:
+
+      one_subgrid  one 8^3 sub-grid, 6 fields (iid states): per-call latency
+                   of hydro_rhs_ex and of a graph-replayed plan (p50/p99 of
+                   >= 200 calls, host wall clock and device events) -- the
+                   paper's context is one Reconstruct (~300 us) and one Flux
+                   (~150 us) launch for one 8^3 sub-grid on an A100 (Sec. V-A)
+      plain_512    the 64^3 periodic domain (512 sub-grids of 8^3, 11 fields,
+                   smooth random fields; Table I's 262144 cells): one fused
+                   plan vs 512 per-sub-grid launches on 1/4/16/128 streams
+      uneven_4096  the 3-level octree batch (3072 8^3 + 1024 16^3 sub-grids,
+                   6 or 11 fields, shuffled): autotuned plan vs per-sub-grid
+                   launches on 128 streams
+    Every timed step of plain_512 and one_subgrid follows an L2 flush (a 512
+    MB write); uneven_4096's inputs (1.3 GB) exceed L2."""
+    import time
+
+    import torch
+
+    import paper_2210_06438_gb300 as hydro
+
+    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")  # 512 MB > L2
+    res = {}
+    precs = (("fp64", hydro.FP64), ("mixed", hydro.FP32_FLUX_FP64_ACC))
+
+    # ---- one sub-grid
+    U, dx = synth.one_subgrid(nf=6)
+    Ud = torch.from_numpy(U).cuda()
+    desc = hydro.descriptors([(Ud, dx, 8, 6)])
+    out = torch.empty(6 * 512, dtype=torch.float64, device="cuda")
+    am = torch.empty(1, dtype=torch.float64, device="cuda")
+    one = {"cells": 512}
+    for name, prec in precs:
+        plan = hydro.Plan(desc, ghost=3, gamma=GAMMA, prec=prec, stream=stream)
+        for form, call in (("rhs_ex", lambda: hydro.rhs(desc, out, am, ghost=3, gamma=GAMMA, prec=prec,
+                                                        stream=stream)),
+                           ("plan", lambda: plan.execute(out, am, stream))):
+            for _ in range(20):
+                call()
+            torch.cuda.synchronize()
+            wall, dev = [], []
+            for _ in range(max(200, steps)):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                t0 = time.perf_counter()
+                a.record(stream)
+                call()
+                b.record(stream)
+                b.synchronize()
+                wall.append((time.perf_counter() - t0) * 1e6)
+                dev.append(a.elapsed_time(b) * 1e3)
+            one["%s_%s" % (name, form)] = {
+                "wall_us_p50": float(np.percentile(wall, 50)), "wall_us_p99": float(np.percentile(wall, 99)),
+                "device_us_p50": float(np.percentile(dev, 50)), "device_us_p99": float(np.percentile(dev, 99)),
+                "calls": len(wall)}
+        plan.close()
+    one["note"] = ("call-to-completion latency of one 8^3 sub-grid (6 fields); wall: host clock around the "
+                   "call and the stream synchronisation; device: CUDA events around the call")
+    res["one_subgrid"] = one
+    del Ud, out
+
+    # ---- 512 sub-grids of the 64^3 periodic domain
+    glob = synth.plain_domain(n=64, nf=11)
+    blocks = torch.from_numpy(np.ascontiguousarray(synth.gather_blocks(glob, 8))).cuda()
+    n = blocks.shape[0]
+    desc = hydro.descriptors([(int(blocks[s].data_ptr()), 1.0 / 64, 8, 11) for s in range(n)])
+    out = torch.empty(n * 11 * 512, dtype=torch.float64, device="cuda")
+    am = torch.empty(n, dtype=torch.float64, device="cuda")
+    cells = n * 512
+    plain = {"cells": cells, "subgrids": n, "inputs_bytes": blocks.numel() * 8}
+    for name, prec in precs:
+        plan = hydro.Plan(desc, ghost=3, gamma=GAMMA, prec=prec, autotune=True, stream=stream, n=n)
+        ms, p10, p90 = time_flushed(lambda: plan.execute(out, am, stream), max(steps, 20), warmup, stream, flush)
+        plan.close()
+        ent = {"fused_ms": ms, "fused_ms_p10_p90": [p10, p90], "fused_value": cells / (ms * 1e-3)}
+        for k in (1, 4, 16, len(streams_pool)):
+            def per_sub(k=k):
+                hydro.rhs_per_subgrid(desc, out, am, streams_pool[:k], ghost=3, gamma=GAMMA, prec=prec, n=n)
+            per_sub()
+            torch.cuda.synchronize()
+            t = []
+            for _ in range(max(3, min(steps, 10))):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                per_sub()
+                torch.cuda.synchronize()
+                t.append((time.perf_counter() - t0) * 1e3)
+            ent["per_subgrid_ms_streams_%d" % k] = float(np.median(t))
+        best = min(v for kk, v in ent.items() if kk.startswith("per_subgrid_ms"))
+        ent["per_subgrid_best_value"] = cells / (best * 1e-3)
+        ent["fused_over_best_per_subgrid"] = best / ms
+        plain[name] = ent
+    plain["note"] = ("64^3 periodic domain, 512 sub-grids of 8^3, 11 fields; fused: autotuned plan, one "
+                     "graph replay, CUDA events; per-sub-grid: 512 launches (hydro_rhs_per_subgrid) on a "
+                     "round-robin stream pool, host clock to completion; L2 flushed before every step")
+    res["plain_512"] = plain
+    del blocks, out
+
+    # ---- uneven octree batch
+    leaves = synth.uneven_octree()
+    host = [synth.leaf_block(synth.BASE_SEED, l) for l in leaves]
+    dev_blocks = [torch.from_numpy(b).cuda() for b in host]
+    del host
+    desc = hydro.descriptors([(b, l[2], l[0], l[1]) for b, l in zip(dev_blocks, leaves)])
+    n = len(leaves)
+    cells = int(sum(l[0] ** 3 for l in leaves))
+    out = torch.empty(hydro.output_doubles(desc, n), dtype=torch.float64, device="cuda")
+    am = torch.empty(n, dtype=torch.float64, device="cuda")
+    alg = int(sum(synth.algorithmic_bytes(l[0], l[1]) for l in leaves))
+    uneven = {"cells": cells, "subgrids": n, "n8": int(sum(l[0] == 8 for l in leaves)),
+              "n16": int(sum(l[0] == 16 for l in leaves)), "alg_bytes": alg}
+    for name, prec in precs:
+        plan = hydro.Plan(desc, ghost=3, gamma=GAMMA, prec=prec, autotune=True, stream=stream, n=n)
+        info = plan.info()
+        ms, p10, p90 = time_flushed(lambda: plan.execute(out, am, stream), max(steps, 10), warmup, stream)
+        plan.close()
+        ms_ex = time_steps(lambda: hydro.rhs(desc, out, am, ghost=3, gamma=GAMMA, prec=prec, stream=stream, n=n),
+                           max(steps, 10), warmup, stream)
+        def per_sub():
+            hydro.rhs_per_subgrid(desc, out, am, streams_pool, ghost=3, gamma=GAMMA, prec=prec, n=n)
+        per_sub()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(max(3, min(steps, 5))):
+            t0 = time.perf_counter()
+            per_sub()
+            torch.cuda.synchronize()
+            t.append((time.perf_counter() - t0) * 1e3)
+        ms_ps = float(np.median(t))
+        uneven[name] = {"plan_ms": ms, "plan_ms_p10_p90": [p10, p90], "plan_value": cells / (ms * 1e-3),
+                        "plan_gbs_alg": alg / (ms * 1e-3) * 1e-9,
+                        "rhs_ex_ms": ms_ex, "rhs_ex_value": cells / (ms_ex * 1e-3),
+                        "per_subgrid_ms": ms_ps, "per_subgrid_value": cells / (ms_ps * 1e-3),
+                        "streams": len(streams_pool), "plan": {k: info[k] for k in (
+                            "threads_per_cta", "ctas_per_sm", "lines_per_chunk", "n_tiles", "n_candidates")}}
+    uneven["note"] = ("3-level octree, 75 % 8^3 / 25 % 16^3 sub-grids, 6 or 11 fields each, shuffled; plan: "
+                      "autotuned, graph replay (CUDA events); rhs_ex: direct call per step (work list "
+                      "built and cost-sorted on the host each call); per-sub-grid: one launch each on "
+                      "the stream pool (host clock)")
+    res["uneven_4096"] = uneven
+    del dev_blocks, out, flush
+    torch.cuda.empty_cache()
+    return res
+
+
 # ------------------------------------------------------------------ ours --
 def run_ours(args, rank, world):
     import torch
@@ -748,12 +977,21 @@ def run_ours(args, rank, world):
     rc, bad = hydro.status(stream)
     if rc != hydro.HYDRO_OK:
         raise RuntimeError("nonphysical input flagged in sub-grid %d" % bad)
+    fp64_peak = fp64_probe_peak(stream)
     out64 = out.clone()
     amax64 = amax.clone()
     drift64 = conservation_drift(out64, batch)
     msmx = time_steps(lambda: planmx.execute(out, amax, stream), args.steps, args.warmup, stream)
     mixed_err = normwise_error(out, out64, amax64, batch)
     drift = conservation_drift(out, batch)
+    # the GPU results of the sub-grids the CPU-baseline leg samples, kept for
+    # its comparison with the oracle
+    sample_idx = np.linspace(0, batch.n - 1, args.cpu_sample).astype(int)
+    ti = torch.from_numpy(sample_idx).to(dev)
+    gpu_sample = {"fp64": out64.view(batch.n, batch.nf, -1)[ti].cpu().numpy(),
+                  "fp64_amax": amax64[ti].cpu().numpy(),
+                  "mixed": out.view(batch.n, batch.nf, -1)[ti].cpu().numpy(),
+                  "mixed_amax": amax[ti].cpu().numpy()}
     del out64
 
     # ---- per-sub-grid launch form (strategy-2 analogue), 128-stream pool
@@ -805,6 +1043,9 @@ def run_ours(args, rank, world):
         agg_sweep[str(A)] = {"ms": ms_a, "launches": -(-batch.n // A)}
     for v in agg_sweep.values():
         v["value"] = cells * world / (v["ms"] * 1e-3)
+
+    # ---- the smaller workloads of the suite (one sub-grid, 512, the uneven batch)
+    small = {} if args.no_small else small_workloads(stream, args.steps, args.warmup, pool)
 
     # ---- per-replay distribution of the headline plan (CUDA events around each replay)
     reps = []
@@ -942,15 +1183,20 @@ def run_ours(args, rank, world):
 
     # ---- roofline of the dominant kernel (the binary64 tile kernel)
     peaks = measured_peaks()
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
     flops = fp64_ops_per_cell(8, 11) * cells
-    peak_fp64 = fp64_peak_gflops(peaks.get("sm_max_mhz", 2070.0))
+    peak_fp64 = fp64_peak["gflops"]
     ach = flops / (ms64 * 1e-3) * 1e-9
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    n_sm = fp64_peak["sms"]
     roof = {"bound": "alu", "achieved": ach, "peak": peak_fp64, "unit": "GFLOP/s (fp64)",
             "frac": ach / peak_fp64, "traffic": recorded_traffic("fp64", info64["n_tiles"]),
-            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz" %
-            peaks.get("sm_max_mhz", 2070.0),
+            "peak_source": "measured: hydro_probe_fp64 (independent binary64 FMAs on all %d SMs, CUDA "
+                           "events, median of %d launches of %.2f ms) = %.2f DFMA/clk/SM at the sampled "
+                           "median SM clock; derived nominal 2 DFMA/clk/SM x %d SMs x %.0f MHz = %.1f GFLOP/s"
+                           % (n_sm, fp64_peak["launches"], fp64_peak["ms"],
+                              peak_fp64 * 1e9 / 2 / n_sm / ((clocks.get("sm_mhz") or 2070.0) * 1e6),
+                              n_sm, clocks.get("sm_mhz") or 2070.0,
+                              fp64_peak_gflops(clocks.get("sm_mhz") or 2070.0, n_sm)),
             "hbm": {"achieved_gbs": batch.alg_bytes / (ms64 * 1e-3) * 1e-9, "peak_gbs": hbm_peak,
                     "frac": batch.alg_bytes / (ms64 * 1e-3) * 1e-9 / hbm_peak,
                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}}
@@ -967,6 +1213,7 @@ def run_ours(args, rank, world):
         idx = np.linspace(0, batch.n - 1, args.cpu_sample).astype(int)
         host_blocks = [batch.blocks[int(i)].cpu().numpy() for i in idx]
         rate, thr, reps = oracle_sample_rate(host_blocks, batch.dx, seconds=args.cpu_seconds)
+        sample_parity = oracle_sample_parity(host_blocks, batch.dx, gpu_sample)
         one = host_blocks[::max(1, len(host_blocks) // 128)]
         rate1, _, reps1 = oracle_sample_rate(one, batch.dx, seconds=min(3.0, args.cpu_seconds), threads=1)
         cpu = {"value": rate, "unit": "cell-updates/s", "cores": thr, "kind": "oracle",
@@ -974,7 +1221,8 @@ def run_ours(args, rank, world):
                          "sub-grids" % (len(idx), reps),
                "one_core": {"value": rate1, "sample": "%d of those sub-grids, %d passes, 1 thread"
                                                       % (len(one), reps1)},
-               "cpu_model": cpu_model(), "other_workloads": oracle_small_configs()}
+               "cpu_model": cpu_model(), "other_workloads": oracle_small_configs(),
+               "parity_on_sample": sample_parity}
 
     value = cells * world / (ms64 * 1e-3)
     line = {
@@ -999,7 +1247,9 @@ def run_ours(args, rank, world):
             "fp64_aggregated": {"value": value, "ms": ms64, "conservation_drift": drift64,
                                 "replay_ms": rep_pct},
             "mixed_aggregated": {"value": cells * world / (msmx * 1e-3), "ms": msmx,
-                                 "roofline": mixed_roof, "max_rel_err_vs_fp64": mixed_err,
+                                 "roofline": mixed_roof, "max_rel_err_vs_fp64_gpu": mixed_err,
+                                 "max_rel_err_vs_fp64_oracle": (cpu or {}).get("parity_on_sample", {}).get(
+                                     "mixed_vs_oracle_fp64_normwise"),
                                  "conservation_drift": drift},
             "fp64_per_subgrid": {"value": cells * world / (ms_ps64 * 1e-3), "ms": ms_ps64,
                                  "streams": args.streams, "launches": batch.n,
@@ -1014,6 +1264,7 @@ def run_ours(args, rank, world):
             "mixed_rk3_step": {"value": 3 * cells * world / (ms_rkmx * 1e-3), "ms": ms_rkmx},
             **quad,
             **forest,
+            **small,
             **sedov,
             "mixed_per_subgrid": {"value": cells * world / (ms_psmx * 1e-3), "ms": ms_psmx,
                                   "streams": args.streams, "launches": batch.n},
@@ -1097,6 +1348,8 @@ def main():
     ap.add_argument("--no-sedov", action="store_true", help="skip the Sedov blast runs")
     ap.add_argument("--no-forest", action="store_true", help="skip the adaptive-forest forms")
     ap.add_argument("--no-quad26", action="store_true", help="skip the 26-point quadrature forms")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the smaller workloads (one sub-grid, 512 sub-grids, the uneven batch)")
     ap.add_argument("--rate", type=float, default=20000.0, help="serving arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--profile", choices=["fp64", "mixed", "forest64", "forestmx", "forest64_quad26",
@@ -1119,7 +1372,7 @@ def main():
     if world > 1:
         # replicas: the scaling run times the headline and the forms beside it;
         # the serving, Sedov and 26-point runs stay single-GPU extras
-        args.no_serving = args.no_sedov = args.no_quad26 = args.no_forest = True
+        args.no_serving = args.no_sedov = args.no_quad26 = args.no_forest = args.no_small = True
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -405,29 +405,38 @@ int hydro_courant(const double* amax, int32_t n_rows, int64_t row_stride, int64_
  * The paper has no counterpart: this is a service of the library.
  *
  * Who needs it: code that must not call cudaMalloc or any allocating routine
- * -- work recorded into a CUDA graph under a capture mode that forbids
- * allocation, real-time loops where an allocation (which may synchronise the
- * device) is not acceptable, or processes whose device memory belongs to
- * another allocator (a framework's caching allocator) that must not be
- * bypassed.  hydro_rhs_ex allocates a work list on its first calls; this
- * entry point allocates nothing, on the device or the host heap.  The caller
- * still provides the inputs and the outputs.
+ * -- real-time loops where an allocation (which may synchronise the device)
+ * is not acceptable, or processes whose device memory belongs to another
+ * allocator (a framework's caching allocator) that must not be bypassed or
+ * that has handed out all of it.  hydro_rhs_ex allocates its work list on
+ * its first calls; this entry point allocates nothing, on the device or the
+ * host heap.  The caller still provides the inputs and the outputs.
  *
  * How: the sub-grid descriptors are copied into a fixed device array that is
  * part of the library image (HYDRO_NOALLOC_MAX_SUBGRIDS entries, 192 KiB; it
  * occupies device memory on every GPU that loads the library until the
- * process exits), and the same tile kernel as hydro_rhs_ex reads them there.
- * Results are bitwise equal to hydro_rhs_ex's for the same batch.
- *   - Uniform batches only: N and n_fields must be > 0 and every descriptor
- *     must match them (HYDRO_EINVAL otherwise); dx may differ per sub-grid.
+ * process exits), and a register-load tile kernel reads them there (256
+ * threads per CTA, 32 lines per chunk).  The per-cell arithmetic is that of
+ * hydro_rhs_ex's kernels in both precision forms, so the results are bitwise
+ * equal to hydro_rhs_ex's for the same batch.
+ *   - Uniform batches only: 2 <= N <= HYDRO_MAX_N and 6 <= n_fields <=
+ *     HYDRO_MAX_FIELDS (0, "any", is not accepted here), and every
+ *     descriptor must match them; dx may differ per sub-grid.  Otherwise
+ *     HYDRO_EINVAL, nothing runs.
  *   - n_subgrids > HYDRO_NOALLOC_MAX_SUBGRIDS: HYDRO_ETOOBIG, nothing runs.
- *   - The first call on a device resolves the array's device address and
- *     sets the kernels' attributes for that device; make that first call
- *     before any stream capture.
- *   - Every call reuses the same array: two calls whose work overlaps on the
- *     GPU (different streams, not ordered) race on it.  Calls on one stream,
- *     or otherwise ordered, are safe; the descriptor array passed in may be
- *     reused as soon as the call returns.
+ *   - The first call on a device (with that device current) resolves the
+ *     array's device address and sets the kernels' attributes for that
+ *     device; make that first call before any stream capture.
+ *   - The descriptor array is copied with cudaMemcpyAsync on `stream`.  From
+ *     pageable host memory the copy has taken the data when the call
+ *     returns, and the array may be reused at once; from page-locked (pinned)
+ *     host memory the copy runs in stream order, so the array must stay
+ *     unchanged until the stream has passed this call.
+ *   - Every call reuses the same device array, which keeps the last call's
+ *     descriptors: two calls whose work overlaps on the GPU (different
+ *     streams, not ordered) race on it.  Calls on one stream, or otherwise
+ *     ordered, are safe.  out_amax is cleared by the call itself where
+ *     sub-grids span several tiles.
  *   - Nonphysical inputs are not recorded (hydro_status does not see this
  *     entry point's launches).
  * Other arguments and the output layout are those of hydro_rhs_ex. */
@@ -435,6 +444,19 @@ int hydro_courant(const double* amax, int32_t n_rows, int64_t row_stride, int64_
 int hydro_rhs_noalloc(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t N,
                       int32_t ghost, int32_t n_fields, double gamma, double* out_dUdt,
                       double* out_amax, hydro_precision_t prec, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * hydro_probe_fp64 -- a measurement aid, not part of the method (the paper
+ * has no counterpart): the binary64 form is bound by the binary64 pipe, so
+ * its roofline needs the rate that pipe reaches on the GPU in use.  Enqueues
+ * on `stream` one launch of a kernel that runs only independent binary64
+ * fused multiply-adds (blocks_per_sm x SMs CTAs of 256 threads, 8 chains of
+ * `iters` steps per thread) and writes their number to *fma_per_launch
+ * (host).  The caller times the launch, e.g. with CUDA events on `stream`;
+ * 2 * *fma_per_launch / seconds is the measured binary64 peak in flop/s.
+ * Allocates nothing.  HYDRO_EINVAL for blocks_per_sm outside [1, 64],
+ * iters < 1 or a null result pointer; HYDRO_ECUDA if the launch fails. */
+int hydro_probe_fp64(int32_t blocks_per_sm, int32_t iters, void* stream, double* fma_per_launch);
 
 /* Packed output length (doubles) of a batch; -1 on bad arguments. */
 int64_t hydro_output_doubles(const hydro_subgrid_t* subgrids, int64_t n_subgrids);

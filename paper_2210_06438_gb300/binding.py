@@ -149,6 +149,7 @@ def load(build_if_missing: bool = False):
         "hydro_server_destroy": (ctypes.c_int, [P]),
         "hydro_now_ns": (i64, []),
         "hydro_rhs_noalloc": (ctypes.c_int, [SG, i64, i32, i32, i32, dbl, P, P, ctypes.c_int, P]),
+        "hydro_probe_fp64": (ctypes.c_int, [i32, i32, P, ctypes.POINTER(ctypes.c_double)]),
         "hydro_domain_rhs": (ctypes.c_int, [P, i32, i32, i32, dbl, dbl, P, P, ctypes.c_int, P, u32]),
         "hydro_domain_stage": (ctypes.c_int, [P, P, dbl, dbl, dbl, i32, i32, i32, dbl, dbl, P, P,
                                               ctypes.c_int, P, u32]),
@@ -238,6 +239,15 @@ def rhs_noalloc(desc, out, amax, N, n_fields, ghost=3, gamma=5.0 / 3.0, prec=FP6
     n = len(desc) if n is None else n
     _check(load().hydro_rhs_noalloc(desc, n, int(N), ghost, int(n_fields), float(gamma), _ptr(out),
                                     _ptr(amax), int(prec), _stream(stream)), "hydro_rhs_noalloc")
+
+
+def probe_fp64(blocks_per_sm=4, iters=10000, stream=None):
+    """hydro_probe_fp64: enqueue the binary64 fused multiply-add probe on
+    `stream`; returns the number of fused multiply-adds it runs."""
+    n = ctypes.c_double(0.0)
+    _check(load().hydro_probe_fp64(int(blocks_per_sm), int(iters), _stream(stream), ctypes.byref(n)),
+           "hydro_probe_fp64")
+    return n.value
 
 
 def domain_rhs(U, nb, N, n_fields, dx, out, amax, gamma=5.0 / 3.0, prec=FP64, stream=None,

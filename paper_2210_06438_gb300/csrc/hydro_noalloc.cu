@@ -1,15 +1,15 @@
 // hydro_noalloc.cu -- an RHS entry point that allocates no memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA
-// graph that is being captured with a relaxed or global capture mode,
-// real-time loops where a device allocation (which may synchronise the whole
-// device) is not allowed, or hosts whose allocator belongs to another runtime
-// (a framework's caching allocator) that must not be bypassed.  For them,
-// hydro_rhs_noalloc evaluates a uniform batch with the same tile kernel as
-// hydro_rhs_ex, but its only scratch memory -- the table of sub-grid
-// descriptors the kernel reads -- lives in the file-scope device array below,
-// whose storage exists from module load until process exit on every GPU that
-// loads the library.  Nothing is allocated on the host heap or the device.
+// Some callers cannot call cudaMalloc at all: real-time loops where a device
+// allocation (which may synchronise the whole device) is not allowed, or
+// hosts whose device memory belongs to another allocator (a framework's
+// caching allocator) that must not be bypassed.  For them, hydro_rhs_noalloc
+// evaluates a uniform batch with a register-load tile kernel of the same
+// per-cell arithmetic as hydro_rhs_ex's, but its only scratch memory -- the
+// table of sub-grid descriptors the kernel reads -- lives in the file-scope
+// device array below, whose storage exists from module load until process
+// exit on every GPU that loads the library.  Nothing is allocated on the
+// host heap or the device.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -87,6 +87,13 @@ std::mutex g_namu;
 
 constexpr int kThreads = 256;
 constexpr int kLch = 32;
+// the launch needs this much dynamic shared memory with F = HYDRO_MAX_FIELDS
+// (the layout does not grow with F); a kernel change that outgrows the
+// opt-in limit of sm_100-class GPUs (227 KiB per CTA, less the kernels'
+// static shared memory) fails here, at build time
+static_assert(hydro_dev::smem_layout_bytes<0>(kLch) <= 226 * 1024 &&
+                  hydro_dev::smem_layout_bytes<1>(kLch) <= 226 * 1024,
+              "shared memory of the allocation-free launch");
 
 void* noalloc_func(hydro_precision_t prec) {
   return prec == HYDRO_FP64 ? (void*)&hydro_dev::rhs_uniform_kernel<0, kThreads, 1>
@@ -105,11 +112,15 @@ int noalloc_setup(int dev, NoallocDev** out) {
     if ((e = cudaDeviceGetAttribute(&D.n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
       return hydro_host::cuda_fail(e, "cudaDeviceGetAttribute");
+    // the same limit as the other entry points' kernels (hydro_api.cu:
+    // the opt-in maximum less 1 KiB for the kernels' static shared memory)
+    const int limit = optin - 1024;
     for (int m = 0; m < 2; m++) {
       hydro_precision_t prec = (hydro_precision_t)m;
       int smem = hydro_host::smem_bytes(prec, HYDRO_MAX_FIELDS, kLch);
+      if (smem > limit) return HYDRO_EINVAL;  // a GPU with less shared memory than sm_100
       if ((e = cudaFuncSetAttribute(noalloc_func(prec), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    optin - 1024)) != cudaSuccess)
+                                    limit)) != cudaSuccess)
         return hydro_host::cuda_fail(e, "cudaFuncSetAttribute");
       if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&D.occ[m], noalloc_func(prec), kThreads,
                                                              smem)) != cudaSuccess)

@@ -25,3 +25,19 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """Write the worst parity ratios of the GPU checks (tests/gpu_helpers.py)
+    to the JSON file named by HYDRO_PARITY_REPORT, if set."""
+    path = os.environ.get("HYDRO_PARITY_REPORT")
+    if not path:
+        return
+    mod = sys.modules.get("tests.gpu_helpers")
+    if mod is None:
+        return
+    import json
+
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    with open(path, "w") as f:
+        json.dump(dict(sorted(mod.WORST.items())), f, indent=1)

@@ -93,3 +93,12 @@ def test_time_step_entry_points_check_arguments_before_the_device(lib):
                                      0) == hydro.HYDRO_EINVAL
     assert lib.hydro_forest_stage_dt(None, P, P, 0.0, 1.0, P, 0.1, 5.0 / 3.0, P * 2, P, 0, None,
                                      0) == hydro.HYDRO_EINVAL
+
+
+def test_fp64_probe_checks_arguments_before_the_device(lib):
+    """hydro_probe_fp64 refuses bad arguments without touching a GPU."""
+    n = ctypes.c_double(0.0)
+    assert lib.hydro_probe_fp64(0, 100, None, ctypes.byref(n)) == hydro.HYDRO_EINVAL
+    assert lib.hydro_probe_fp64(65, 100, None, ctypes.byref(n)) == hydro.HYDRO_EINVAL
+    assert lib.hydro_probe_fp64(4, 0, None, ctypes.byref(n)) == hydro.HYDRO_EINVAL
+    assert lib.hydro_probe_fp64(4, 100, None, None) == hydro.HYDRO_EINVAL
