@@ -682,7 +682,8 @@ def oracle_sample_parity(blocks_host, dx, gpu):
     CPU-baseline sample (each sub-grid whole): binary64 form against the
     oracle's binary64 mode under the 1e-12 gate of the parity tests, the
     mixed form's normwise error against the binary64 oracle (per sub-grid and
-    field, max|gpu - oracle| / max|oracle|, worst over the sample) and against
+    field, max|gpu - oracle| / max(max|oracle|, amax max|U_f| / dx), worst
+    over the sample) and against
     the oracle's mixed mode in binary32 ulps of the flux-divergence scale."""
     import oracle
 
@@ -697,7 +698,10 @@ def oracle_sample_parity(blocks_host, dx, gpu):
     floor = ram[:, None] * umax / dx
     fp64 = (np.abs(gpu["fp64"] - r0).max(axis=2) / np.maximum(np.maximum(np.abs(r0).max(axis=2), floor),
                                                                1e-300)).max()
-    mx = (np.abs(gpu["mixed"] - r0).max(axis=2) / np.maximum(np.abs(r0).max(axis=2), 1e-300)).max()
+    # normwise with the parity tests' flux-divergence floor (exact zeros of
+    # uniform regions must not divide by zero)
+    mx = (np.abs(gpu["mixed"] - r0).max(axis=2) / np.maximum(np.maximum(np.abs(r0).max(axis=2), floor),
+                                                              1e-300)).max()
     S32 = 2.0 * ram1[:, None] * (umax + np.where((np.arange(nf) >= 1) & (np.arange(nf) <= 4), umax[:, 4:5], 0.0))
     ulps = (np.abs(gpu["mixed"] - r1).max(axis=2) / (2.0 ** -24 * S32 / dx)).max()
     return {"subgrids": n, "oracle_flags": int(fl.any()),

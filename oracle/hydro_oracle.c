@@ -24,8 +24,10 @@
  *
  * Evaluation order is fixed and written out; compile with
  *   -O2 -ffp-contract=off
- * so that no multiply-add is fused.  The mixed mode (mode 1) runs steps 2-3
- * in IEEE binary32 on binary32-rounded primitives and step 4 in binary64.
+ * so that no multiply-add is fused.  The mixed mode (mode 1) forms the
+ * primitives in binary32 from the binary32-rounded conserved values (the
+ * internal energy and the dual-energy switch stay binary64; see
+ * primitives_mixed), runs steps 2-3 in IEEE binary32 and step 4 in binary64.
  *
  * Layout: U[f][k][j][i] with i (x) fastest; a block has interior nx*ny*nz
  * cells and `ghost` >= 3 ghost layers on every side (only the innermost 3 are
@@ -107,6 +109,31 @@ static int primitives(const double* u, int nf, double gamma, double* w) {
   int bad = !(rho > 0.0) || !(p > 0.0);
   for (int f = 0; f < nf; f++)
     if (!isfinite(u[f]) || !isfinite(w[f])) bad = 1;
+  return bad;
+}
+
+/* Step 1 of the mixed mode (declared reading): the conserved values are
+ * rounded to binary32 (C's conversion: to nearest, ties to even); rho,
+ * v = s/rho, phi = tau/rho and X_k = rho_k/rho are formed from them in
+ * binary32 (one binary32 division each); the internal energy and the
+ * dual-energy switch are those of `primitives` on the binary64 inputs, and
+ * p = (gamma-1) e is rounded to binary32.  w receives the binary32 values
+ * (exactly, as doubles).  Returns 1 if nonphysical. */
+static int primitives_mixed(const double* u, int nf, double gamma, double* w) {
+  double w64[ORA_MAXF];
+  int bad = primitives(u, nf, gamma, w64); /* e, the switch and p in binary64 */
+  float q[ORA_MAXF];
+  for (int f = 0; f < nf; f++) q[f] = (float)u[f];
+  float rho = q[0];
+  w[0] = rho;
+  w[1] = q[1] / rho;
+  w[2] = q[2] / rho;
+  w[3] = q[3] / rho;
+  w[4] = (float)w64[4];
+  w[5] = q[5] / rho;
+  for (int f = 6; f < nf; f++) w[f] = q[f] / rho;
+  for (int f = 0; f < nf; f++)
+    if (!isfinite(w[f])) bad = 1;
   return bad;
 }
 
@@ -424,7 +451,8 @@ int ora_rhs_block(const double* U, int nx, int ny, int nz, int ghost, int nf, do
   int flags = 0;
   size_t ncell = (size_t)g.gx * g.gy * g.gz;
 
-  /* step 1 over the star region; W[f][cell] in the same indexing as U */
+  /* step 1 over the star region; W[f][cell] in the same indexing as U (in
+   * mode 1 the binary32 primitives, held exactly as doubles) */
   double* W = (double*)calloc((size_t)nf * ncell, sizeof(double));
   for (int k = -3; k < nz + 3; k++)
     for (int j = -3; j < ny + 3; j++)
@@ -432,7 +460,7 @@ int ora_rhs_block(const double* U, int nx, int ny, int nz, int ghost, int nf, do
         if (!(q26 ? in_read26(&g, i, j, k) : in_star(&g, i, j, k))) continue;
         double u[ORA_MAXF], w[ORA_MAXF];
         for (int f = 0; f < nf; f++) u[f] = U[at(&g, f, i, j, k)];
-        flags |= primitives(u, nf, gamma, w) ? ORA_NONPHYS : 0;
+        flags |= (mode == 1 ? primitives_mixed(u, nf, gamma, w) : primitives(u, nf, gamma, w)) ? ORA_NONPHYS : 0;
         for (int f = 0; f < nf; f++) W[at(&g, f, i, j, k)] = w[f];
       }
 

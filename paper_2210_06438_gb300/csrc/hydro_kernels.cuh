@@ -30,9 +30,10 @@
 // scalings by powers of two run on the integer pipe on the bit patterns, and
 // the flux is written in an algebraically reduced form (see kt_hydro64).
 //
-// MODE 1 (mixed) converts the binary64 inputs to binary32 with integer
-// operations, forms primitives in binary32 (the dual-energy decision and the
-// internal energy near it are recomputed in binary64), reconstructs and
+// MODE 1 (mixed) rounds the binary64 inputs to binary32 (to nearest even,
+// mostly with integer operations), forms primitives in binary32 (the
+// dual-energy decision and the internal energy near it are evaluated in
+// binary64, as the binary64 form does), reconstructs and
 // fluxes in binary32, and carries the flux differences and their sum as exact
 // binary32 pairs (error-free transformations, Knuth's TwoSum), so that the
 // binary64 result telescopes across faces like the binary64 form.
@@ -110,17 +111,28 @@ __device__ __forceinline__ void cell_of(int s, int& x, int& y, int& z) {
   }
 }
 
-// slot of position c (0..LL-1, cell c-3) of line l along direction d
-__device__ __forceinline__ int line_slot(int d, int l, int c) {
-  int a = l % TE, b = l / TE;
-  if (d == 0) return slot_of(c - 3, a, b);
-  if (d == 1) return slot_of(a, c - 3, b);
-  return slot_of(a, b, c - 3);
+// The binary32/binary64 primitives of the read region (W) use a padded
+// copy of that layout, so that the reconstruction's line reads meet no
+// shared-memory bank conflicts along x and y (and 2-way ones on the interior
+// part of the z lines): interior rows of pitch WP = 15 elements instead of
+// 14, and y ghost slabs of z pitch WYZ = 56 instead of 48.  Sixteen lines of
+// a half warp then read sixteen distinct 8-byte banks (odd row pitch along
+// x; rows 8 apart land 8 banks apart along y).  The staging buffer and 1/rho
+// keep the dense slots; wslot maps a dense slot to its W slot.
+constexpr int WP = LL + 1;                 // interior row pitch in W
+constexpr int WYZ = 6 * TE + TE;           // z pitch of the y slabs in W
+constexpr int WXROWS = TE * TE * WP;       // 960
+constexpr int WYSLAB = TE * WYZ;           // 448
+constexpr int WSTAR = WXROWS + WYSLAB + 6 * TE * TE;  // 1792 slots per field in W
+__host__ __device__ __forceinline__ int wslot(int s) {
+  if (s < XROWS) return s + s / LL;                     // row s/14 gains one slot per row
+  if (s < XROWS + YSLAB) return s + (WXROWS - XROWS) + TE * ((s - XROWS) / (6 * TE));
+  return s + (WXROWS - XROWS) + (WYSLAB - YSLAB);
 }
 
-// Addressing of line l along direction d in the read-region layout: three
-// segments (3 low ghosts, TE interior cells, 3 high ghosts), each with a
-// base slot and a constant stride.
+// Addressing of line l along direction d in W: three segments (3 low
+// ghosts, TE interior cells, 3 high ghosts), each with a base slot and a
+// constant stride.
 struct LineAddr {
   int lo, in, hi, sg, si;
   __device__ __forceinline__ int at(int c) const {
@@ -130,13 +142,13 @@ struct LineAddr {
 __device__ __forceinline__ LineAddr line_addr(int d, int l) {
   int a = l % TE, b = l / TE;
   if (d == 0) {
-    int base = (b * TE + a) * LL;
+    int base = (b * TE + a) * WP;
     return {base, base + 3, base + 3 + TE, 1, 1};
   }
   if (d == 1)
-    return {XROWS + b * 6 * TE + a, b * TE * LL + a + 3, XROWS + b * 6 * TE + 3 * TE + a, TE, LL};
-  return {XROWS + YSLAB + b * TE + a, b * LL + a + 3, XROWS + YSLAB + 3 * TE * TE + b * TE + a,
-          TE * TE, TE * LL};
+    return {WXROWS + b * WYZ + a, b * TE * WP + a + 3, WXROWS + b * WYZ + 3 * TE + a, TE, WP};
+  return {WXROWS + WYSLAB + b * TE + a, b * WP + a + 3, WXROWS + WYSLAB + 3 * TE * TE + b * TE + a,
+          TE * TE, TE * WP};
 }
 
 // --------------------------------------------------- periodic domains --
@@ -430,16 +442,49 @@ __device__ __forceinline__ double kt_hydro64(const double* wl, const double* wr,
 }
 
 // ====================================================== binary32 (mixed) ==
-// binary64 -> binary32 on the integer pipe: the top 24 significant bits,
-// rounded to nearest with ties away from zero (the binary64 to binary32
-// instruction runs on the slow binary64 pipe of this GPU).  Magnitudes below
-// the smallest normal binary32 (including zero) become signed zero; inputs
-// must stay below 2^128 in magnitude.
+// binary64 -> binary32, rounded to nearest with ties to even: the IEEE
+// conversion, bit for bit.  d2f_fast converts magnitudes in the binary32
+// normal range below the top binade, [2^-126, 2^127), on the integer pipe
+// (the conversion instruction runs on the slow binary64 pipe of this GPU):
+// the funnel shift takes the low 9 bits of the binary64 exponent and the top
+// 23 fraction bits; adding 128 to that 9-bit exponent field (mod 512)
+// rebiases it to binary32 for every exponent of the range; the 29 dropped
+// bits round the result (up when above one half, or exactly one half with an
+// odd result; a carry out of the fraction steps the exponent), and zero.  For
+// values outside that range its result is meaningless and `oor` (an unsigned
+// maximum over the values of a cell) becomes >= D2F_OOR, so that the caller
+// converts that cell again with the instruction (d2f_slow): results below
+// the normal range, the top binade (which may round to infinity) and
+// non-finite values.  d2f_fast_pos takes the same path for positive values
+// only (zero and negative ones count as out of range).
+constexpr unsigned D2F_OOR = 253u << 20;
+__device__ __forceinline__ float d2f_fast(double d, unsigned& oor) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned ahi = hi & 0x7fffffffu;
+  // zero (or a magnitude below 2^-1042): signed zero, exactly as the
+  // conversion rounds it -- momenta of gas at rest are zero
+  const bool z = ahi == 0u;
+  oor = max(oor, z ? 0u : ahi - (897u << 20));
+  unsigned t = __funnelshift_l(lo, ahi, 3);
+  const bool up = ((lo & 0x1fffffffu) | (t & 1u)) > 0x10000000u;
+  t += (128u << 23) + (up ? 1u : 0u);
+  return __uint_as_float((z ? 0u : t) | (hi & 0x80000000u));
+}
+__device__ __forceinline__ float d2f_fast_pos(double d, unsigned& oor) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  oor = max(oor, hi - (897u << 20));
+  unsigned t = __funnelshift_l(lo, hi, 3);
+  const bool up = ((lo & 0x1fffffffu) | (t & 1u)) > 0x10000000u;
+  return __uint_as_float(t + (128u << 23) + (up ? 1u : 0u));
+}
+// Not inlined, so that the compiler cannot evaluate it speculatively (it has
+// no side effects) in the common case that does not need it.
+static __device__ __noinline__ float d2f_slow(double d) { return __double2float_rn(d); }
+// one value, any magnitude
 __device__ __forceinline__ float d2f_int(double d) {
-  unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-  unsigned sg = hi & 0x80000000u, ahi = hi & 0x7fffffffu;
-  unsigned mag = __funnelshift_l(lo, ahi - (896u << 20), 3) + ((lo >> 28) & 1u);
-  return __uint_as_float(ahi < (897u << 20) ? sg : (mag | sg));
+  unsigned oor = 0;
+  const float f = d2f_fast(d, oor);
+  return oor >= D2F_OOR ? d2f_slow(d) : f;
 }
 // binary32 -> binary64 (exact), on the integer pipe; zero and subnormal
 // binary32 values give signed zero.
@@ -469,28 +514,46 @@ __device__ __forceinline__ float tau_pow32(float tau, float gamma, bool g53) {
 }
 
 // ------------------------------------------------------ step A1, mixed --
+// The mixed form's primitives (declared reading): the conserved values are
+// rounded to binary32 (d2f_int, the IEEE conversion); rho, v = s/rho and
+// phi = tau/rho are formed in binary32 from them (reciprocal with one Newton
+// step, then products: within ~1.5 ulp of the quotients); the internal
+// energy and the dual-energy switch are those of the binary64 form, on the
+// binary64 inputs, and p = (gamma - 1) e rounded to binary32.  Where the
+// binary32 estimate e32 = E - |s|^2/(2 rho) settles the branch with room to
+// spare -- e32 >= E/2 (not switched; e32 within ~4 ulp of e) or
+// e32 <= eta E/2 (switched; tau^gamma in binary32, within ~3 ulp) -- the
+// binary32 values are used; in between, e and the branch are evaluated in
+// binary64 in the reference order of operations.
 // u: the binary64 hydro inputs of one cell (fields 0-5); writes binary32
-// primitives (rho, vx, vy, vz, p, phi) and r = 1/rho.  Where e_int is within a
-// factor 4 of E (where binary32 cancellation would cost more than ~20 ulp) or
-// near the switch, it is recomputed in binary64 in the reference order.
+// primitives (rho, vx, vy, vz, p, phi) and r = 1/rho.
 __device__ __forceinline__ bool prim_mixed(const double* u, double gamma, float gamf, float gm1f,
                                            bool g53, float* w, float& r) {
-  float rho = d2f_int(u[0]);
-  float s1 = d2f_int(u[1]), s2 = d2f_int(u[2]), s3 = d2f_int(u[3]);
-  float E = d2f_int(u[4]), tau = d2f_int(u[5]);
+  unsigned oor = 0;
+  float rho = d2f_fast_pos(u[0], oor);
+  float s1 = d2f_fast(u[1], oor), s2 = d2f_fast(u[2], oor), s3 = d2f_fast(u[3], oor);
+  float E = d2f_fast_pos(u[4], oor), tau = d2f_fast_pos(u[5], oor);
+  if (oor >= D2F_OOR) {  // rare: a value outside the fast conversion's range
+    rho = d2f_slow(u[0]);
+    s1 = d2f_slow(u[1]);
+    s2 = d2f_slow(u[2]);
+    s3 = d2f_slow(u[3]);
+    E = d2f_slow(u[4]);
+    tau = d2f_slow(u[5]);
+  }
   r = rcp32(rho);
   float ssq = fmaf(s3, s3, fmaf(s2, s2, s1 * s1));
   float eint = fmaf(-0.5f * ssq, r, E);
-  float thr = (float)ETA * E;
   float p;
-  if (eint > 0.5f * thr && eint < 0.25f * E) {  // near the switch, or too inexact in binary32
+  if (eint >= 0.5f * E) {
+    p = gm1f * eint;
+  } else if (eint <= (float)(0.5 * ETA) * E) {
+    p = gm1f * tau_pow32(tau, gamf, g53);
+  } else {
     double ss = __dadd_rn(__dadd_rn(__dmul_rn(u[1], u[1]), __dmul_rn(u[2], u[2])), __dmul_rn(u[3], u[3]));
     double ex = __dsub_rn(u[4], __ddiv_rn(__dmul_rn(0.5, ss), u[0]));
     double e = ex < __dmul_rn(ETA, u[4]) ? tau_pow64(u[5], gamma, g53) : ex;
-    p = __double2float_rn((gamma - 1.0) * e);
-  } else {
-    float e = eint <= 0.5f * thr ? tau_pow32(tau, gamf, g53) : eint;
-    p = gm1f * e;
+    p = d2f_int(__dmul_rn(gamma - 1.0, e));
   }
   w[0] = rho;
   w[1] = s1 * r;
@@ -498,9 +561,13 @@ __device__ __forceinline__ bool prim_mixed(const double* u, double gamma, float 
   w[3] = s3 * r;
   w[4] = p;
   w[5] = tau * r;
-  bool bad = !(rho > 0.0f) || !(p > 0.0f) || !isfinite(p);
+  // nonphysical: rho <= 0, p <= 0 or a non-finite value.  A non-finite input
+  // (or one beyond the binary32 range) leaves a non-finite primitive, so the
+  // binary32 primitives alone decide it, as the binary32 quotients do in the
+  // reference definition of the mixed form.
+  bool bad = !(rho > 0.0f) || !(p > 0.0f);
 #pragma unroll
-  for (int f = 0; f < 6; f++) bad |= !dfinite(u[f]);
+  for (int f = 0; f < 6; f++) bad |= !isfinite(w[f]);
   return bad;
 }
 
@@ -516,33 +583,45 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // ------------------------------------------------------ step A2, mixed --
 // ppm_line64's steps in binary32 on a pair of fields, in half-slope form:
 // with dm = q - q_-1 and dp = q_+1 - q, half the monotonised central slope is
-//   h = sign(dm + dp) min(|dm + dp|/4, |dm|, |dp|)  if dm, dp have one sign,
-//   h = 0 otherwise,
-// and the face between cells c-1 and c is (q_c-1 + q_c)/2 - (h_c - h_c-1)/3.
-// The same-sign tests run on products (a product of two differences that
-// underflows reads as "not the same sign", which changes results by less
-// than those differences).  The parabola limiter in clamp form: with
-// up = q+ - q and dn = q - q- of one sign, q+ = q + 2dn where |up| > 2|dn|
-// and q- = q - 2up where |dn| > 2|up| (CW84 eq. 1.10); a cell with
-// up dn <= 0 is flattened.
-// min(|a|, |b|) with the sign of a (min.xorsign.abs with |b|)
-__device__ __forceinline__ float min_signed(float a, float b) {
+//   h = minmod((dm + dp)/4, dm, dp)
+// (sign times the smallest magnitude if all three have one sign, else 0), and
+// the face between cells c-1 and c is (q_c-1 + q_c)/2 - (h_c - h_c-1)/3.
+// The parabola limiter in clamp form: with up = q+ - q and dn = q - q-,
+//   q- = q - minmod(dn, 2 up),  q+ = q + minmod(up, 2 dn)
+// which is CW84 eq. 1.10 exactly: where up, dn have one sign, q- = q - 2up
+// where |dn| > 2|up| (D m > D^2/6) and q+ = q + 2dn where |up| > 2|dn|
+// (D m < -D^2/6); where they do not (an extremum), both minmods are 0 and
+// the cell is flattened.
+//
+// minmod(a, b) in three instructions: min.xorsign.abs(a, b) is
+// min(|a|, |b|) with the sign bit sign(a) xor sign(b), i.e. positive exactly
+// when a and b have one sign; clamped at 0 it is |minmod(a, b)|, and
+// min.xorsign.abs(a, that) gives it a's sign.
+__device__ __forceinline__ float minxs(float a, float b) {  // min(|a|, |b|), sign(a) xor sign(b)
   float r;
-  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(fabsf(b)));
+  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
   return r;
 }
-__device__ __forceinline__ float hslope1(float dm, float dp, float s4, float pr) {
-  float m = fminf(fminf(fabsf(s4), fabsf(dm)), fabsf(dp));
-  return pr > 0.0f ? copysignf(m, s4) : 0.0f;
+__device__ __forceinline__ float minmod(float a, float b) { return minxs(a, fmaxf(minxs(a, b), 0.0f)); }
+__device__ __forceinline__ float2 minmod2(float2 a, float2 b) {
+  return make_float2(minmod(a.x, b.x), minmod(a.y, b.y));
 }
+// half slope: minmod((dm + dp)/4, minmod(dm, dp)) -- if dm, dp have one sign
+// their sum has it too
 __device__ __forceinline__ float2 hslope32x2(float2 dm, float2 dp) {
-  float2 s4 = mul2(add2(dm, dp), f2(0.25f));
-  float2 pr = mul2(dm, dp);
-  return make_float2(hslope1(dm.x, dp.x, s4.x, pr.x), hslope1(dm.y, dp.y, s4.y, pr.y));
+  return minmod2(mul2(add2(dm, dp), f2(0.25f)), minmod2(dm, dp));
 }
-__device__ __forceinline__ void limit1(float q, float lo, float hi, float up, float dn, float e, float uu,
-                                       float du, float lc, float hc, float& L, float& H) {
-  const bool ext = !(e > 0.0f);
+// Scalar forms for the single-cell reconstructions of the 26-point variant:
+// the half slope of a cell with differences dm, dp (s4 = (dm + dp)/4), and
+// the limited states from the face values lo, hi (up = hi - q, dn = q - lo,
+// uu = 2 up, du = 2 dn, lc = q - uu, hc = q + du): an unclamped face keeps
+// its value exactly.
+__device__ __forceinline__ float hslope1(float dm, float dp, float s4) {
+  return minmod(s4, minmod(dm, dp));
+}
+__device__ __forceinline__ void limit1(float q, float lo, float hi, float up, float dn, float uu, float du,
+                                       float lc, float hc, float& L, float& H) {
+  const bool ext = !(minxs(up, dn) > 0.0f);  // up, dn not of one sign (or one of them 0)
   L = ext ? q : (fabsf(dn) > fabsf(uu) ? lc : lo);
   H = ext ? q : (fabsf(up) > fabsf(du) ? hc : hi);
 }
@@ -565,24 +644,9 @@ __device__ __forceinline__ void ppm_line32x2(const float2* w, const LineAddr& la
     // up of cell c-1: dq/2 - (h_c - h_c-1)/3
     float2 up = fma2(sub2(h_prev, h), f2(1.0f / 3.0f), mul2(dm, f2(0.5f)));
     if (c >= 3) {  // states of cell c-1
-      float2 e = mul2(up, dn);
-      float2 uu = add2(up, up), du = add2(dn, dn);
-      // the offsets after clamping: with up, dn of one sign, the smaller of
-      // |dn| and 2|up| with the sign of dn, the smaller of |up| and 2|dn| with
-      // the sign of up (one instruction each)
-      float2 a, b;
-      a.x = min_signed(dn.x, uu.x);
-      a.y = min_signed(dn.y, uu.y);
-      b.x = min_signed(up.x, du.x);
-      b.y = min_signed(up.y, du.y);
-      float2 L = sub2(qm, a), H = add2(qm, b);
-      L.x = e.x > 0.0f ? L.x : qm.x;
-      L.y = e.y > 0.0f ? L.y : qm.y;
-      H.x = e.x > 0.0f ? H.x : qm.x;
-      H.y = e.y > 0.0f ? H.y : qm.y;
-      int j = c - 4;  // cell index of c-1
-      if (j >= 0) right[j] = L;
-      if (j + 1 <= TE) left[j + 1] = H;
+      const int j = c - 4;  // cell index of c-1
+      if (j >= 0) right[j] = sub2(qm, minmod2(dn, add2(up, up)));
+      if (j + 1 <= TE) left[j + 1] = add2(qm, minmod2(up, add2(dn, dn)));
     }
     dn = sub2(dm, up);  // dn of cell c
     h_prev = h;
@@ -731,6 +795,25 @@ template <int MODE> struct Prec;
 template <> struct Prec<0> { typedef double R; typedef double V; typedef double Acc; static constexpr int PACK = 1; };
 template <> struct Prec<1> { typedef float R; typedef float2 V; typedef P2 Acc; static constexpr int PACK = 2; };
 
+// The per-face factors (g_l, g_r) of the species fluxes as one vector access
+// (conflict-free in shared memory, unlike two strided scalar ones).
+__device__ __forceinline__ void store_pair(float* g, float a, float b) {
+  *reinterpret_cast<float2*>(g) = make_float2(a, b);
+}
+__device__ __forceinline__ void store_pair(double* g, double a, double b) {
+  *reinterpret_cast<double2*>(g) = make_double2(a, b);
+}
+__device__ __forceinline__ void load_pair(const float* g, float& a, float& b) {
+  const float2 v = *reinterpret_cast<const float2*>(g);
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void load_pair(const double* g, double& a, double& b) {
+  const double2 v = *reinterpret_cast<const double2*>(g);
+  a = v.x;
+  b = v.y;
+}
+
 // Source of the tile descriptors: a prepared work list in global memory.
 struct TileList {
   const Tile* __restrict__ tiles;
@@ -741,7 +824,7 @@ constexpr int NGRP = 6;  // fields per group: hydro (rho, vx, vy, vz, p, phi) or
 
 // Shared memory of one CTA.  V = R (binary64) or a pair of binary32 values
 // (mixed form: fields 2k and 2k+1 of a group share one 8-byte element):
-//   W  [NGRP/PACK][STAR] V   primitives of the read region: the hydro group,
+//   W  [NGRP/PACK][WSTAR] V  primitives of the read region (padded slots): the hydro group,
 //                            then (after the hydro pass) the species
 //   RR [STAR] R              1/rho of every read cell
 //   GG [3][NLN][NFC][2] R    per face the factors g_l, g_r of the species fluxes
@@ -749,7 +832,7 @@ constexpr int NGRP = 6;  // fields per group: hydro (rho, vx, vy, vz, p, phi) or
 template <int MODE>
 __host__ __device__ constexpr size_t smem_layout_bytes(int lch) {
   return (MODE == 0 ? 8 : 4) *
-         ((size_t)NGRP * STAR + STAR + 3 * NLN * NFC * 2 + 2 * (size_t)NGRP * lch * NFC);
+         ((size_t)NGRP * WSTAR + STAR + 3 * NLN * NFC * 2 + 2 * (size_t)NGRP * lch * NFC);
 }
 
 // ------------------------------------------------------------ forests --
@@ -907,7 +990,7 @@ __device__ __forceinline__ void group_pass(
       for (int task = tid; task < lch * ng; task += NT) {
         int ll = task % lch, j = task / lch;
         LineAddr la = line_addr(d, l0 + ll);
-        const V* w = W + j * STAR;
+        const V* w = W + j * WSTAR;
         if constexpr (MODE == 0) {
           ppm_line64(w, la, QS + j * fs + ll * NFC, QR + j * fs + ll * NFC);
         } else {
@@ -932,8 +1015,7 @@ __device__ __forceinline__ void group_pass(
           R a, gl, gr;
           if constexpr (MODE == 0) a = kt_hydro64(wl, wr, d, gamma, inv_gm1, knp, fo, fs, gl, gr);
           else a = kt_hydro32(wl, wr, d, gamma, inv_gm1, knp, fo, fs, gl, gr);
-          g[0] = gl;
-          g[1] = gr;
+          store_pair(g, gl, gr);  // one 8- or 16-byte store
           bool fvalid = (l % TE) < e_a && (l / TE) < e_b && i <= e_d;
           if constexpr (MODE == 0) {
             if (fvalid) amax = dmaxp(amax, a);
@@ -941,7 +1023,8 @@ __device__ __forceinline__ void group_pass(
             if (fvalid) amax = fmaxf(amax, a);
           }
         } else {
-          R gl = g[0], gr = g[1];
+          R gl, gr;
+          load_pair(g, gl, gr);
 #pragma unroll
           for (int j = 0; j < NS; j++)
             if (j < ng) {
@@ -1069,7 +1152,7 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
   constexpr int NS = NGRP / PK;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* W = reinterpret_cast<V*>(smem_raw);
-  R* RR = reinterpret_cast<R*>(W + NS * STAR);
+  R* RR = reinterpret_cast<R*>(W + NS * WSTAR);
   R* GG = RR + STAR;
   V* QS = reinterpret_cast<V*>(GG + 3 * NLN * NFC * 2);
   __shared__ double red[NT / 32];
@@ -1155,10 +1238,10 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
         }
         if constexpr (MODE == 0) {
 #pragma unroll
-          for (int f = 0; f < 6; f++) W[f * STAR + s] = w[f];
+          for (int f = 0; f < 6; f++) W[f * WSTAR + wslot(s)] = w[f];
         } else {
 #pragma unroll
-          for (int j = 0; j < 3; j++) W[j * STAR + s] = make_float2(w[2 * j], w[2 * j + 1]);
+          for (int j = 0; j < 3; j++) W[j * WSTAR + wslot(s)] = make_float2(w[2 * j], w[2 * j + 1]);
         }
         RR[s] = r;
       }
@@ -1209,22 +1292,37 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
           if (k >= SPT || s >= STAR) continue;
           R r = RR[s];
           R x[MAXF - 6];
+          unsigned oor = 0;
 #pragma unroll
           for (int f = 0; f < MAXF - 6; f++) {
             x[f] = R(0);
             if (f < nsp && off[kk] >= 0) {
-              bad |= !dfinite(v[kk][f]);
-              if constexpr (MODE == 0) x[f] = v[kk][f] * r; else x[f] = d2f_int(v[kk][f]) * r;
+              if constexpr (MODE == 0) {
+                bad |= !dfinite(v[kk][f]);
+                x[f] = v[kk][f] * r;
+              } else {
+                x[f] = d2f_fast_pos(v[kk][f], oor) * r;
+              }
             }
+          }
+          if constexpr (MODE == 1) {
+            if (oor >= D2F_OOR) {  // rare: convert the cell's species again
+#pragma unroll
+              for (int f = 0; f < MAXF - 6; f++)
+                if (f < nsp && off[kk] >= 0) x[f] = d2f_slow(v[kk][f]) * r;
+            }
+#pragma unroll
+            for (int f = 0; f < MAXF - 6; f++)  // a non-finite input leaves a non-finite quotient
+              if (f < nsp) bad |= !isfinite(x[f]);
           }
           if constexpr (MODE == 0) {
 #pragma unroll
             for (int f = 0; f < MAXF - 6; f++)
-              if (f < nsp) W[f * STAR + s] = x[f];
+              if (f < nsp) W[f * WSTAR + wslot(s)] = x[f];
           } else {
 #pragma unroll
             for (int j = 0; j < 3; j++)
-              if (2 * j < nsp) W[j * STAR + s] = make_float2(x[2 * j], 2 * j + 1 < MAXF - 6 ? x[2 * j + 1] : 0.0f);
+              if (2 * j < nsp) W[j * WSTAR + wslot(s)] = make_float2(x[2 * j], 2 * j + 1 < MAXF - 6 ? x[2 * j + 1] : 0.0f);
           }
         }
       }
@@ -1291,14 +1389,14 @@ rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
 //   flux  3 rounds (one per direction) of 64 lines x 9 faces = 576 faces
 //   A4    one interior cell per thread (threads 0..511)
 // Shared memory (bytes): S  [6][STAR] binary64 staging      79872
-//                        W  [3][STAR] float2 primitives     39936
+//                        W  [3][WSTAR] float2 primitives    43008
 //                        RR [STAR] float 1/rho               6656
 //                        GG [3][NLN][NFC][2] float          13824
 //                        QS [3][2][3][NLN][NFC] float2      82944
 constexpr int PNT = 3 * NLN * 3;  // 576
 constexpr int PSPT = (STAR + PNT - 1) / PNT;  // read-region slots per thread: 3
 __host__ __device__ constexpr size_t pipe_smem_bytes() {
-  return (size_t)6 * STAR * 8 + 3 * STAR * 8 + STAR * 4 + 3 * NLN * NFC * 2 * 4 + 3 * 2 * 3 * NLN * NFC * 8;
+  return (size_t)6 * STAR * 8 + 3 * WSTAR * 8 + STAR * 4 + 3 * NLN * NFC * 2 * 4 + 3 * 2 * 3 * NLN * NFC * 8;
 }
 
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
@@ -1312,12 +1410,14 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // tile-local (x, y, z) packed as three signed bytes.
 struct SlotXYZ {
   int p[PSPT];
+  int w[PSPT];  // the slot's index in W
   __device__ __forceinline__ void init(int tid) {
 #pragma unroll
     for (int k = 0; k < PSPT; k++) {
       int s = tid + k * PNT, x = 0, y = 0, z = 0;
       if (s < STAR) cell_of(s, x, y, z);
       p[k] = (x & 0xff) | ((y & 0xff) << 8) | ((z & 0xff) << 16);
+      w[k] = wslot(s < STAR ? s : 0);
     }
   }
   __device__ __forceinline__ void get(int k, int& x, int& y, int& z) const {
@@ -1390,7 +1490,7 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* S = reinterpret_cast<double*>(smem_raw);
   float2* W = reinterpret_cast<float2*>(S + 6 * STAR);
-  float* RR = reinterpret_cast<float*>(W + 3 * STAR);
+  float* RR = reinterpret_cast<float*>(W + 3 * WSTAR);
   float* GG = RR + STAR;
   float2* QS = reinterpret_cast<float2*>(GG + 3 * NLN * NFC * 2);
   __shared__ double red[PNT / 32];
@@ -1437,7 +1537,7 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
         r = 1.0f;
       }
 #pragma unroll
-      for (int j = 0; j < 3; j++) W[j * STAR + s] = make_float2(w[2 * j], w[2 * j + 1]);
+      for (int j = 0; j < 3; j++) W[j * WSTAR + sx.w[k]] = make_float2(w[2 * j], w[2 * j + 1]);
       RR[s] = r;
     }
     bad = __syncthreads_or(bad);
@@ -1451,7 +1551,7 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
     {
       const int d = tid / (3 * NLN), rem = tid - d * 3 * NLN, j = rem / NLN, l = rem - j * NLN;
       LineAddr la = line_addr(d, l);
-      ppm_line32x2(W + j * STAR, la, qs(d, 0, j) + l * NFC, qs(d, 1, j) + l * NFC);
+      ppm_line32x2(W + j * WSTAR, la, qs(d, 0, j) + l * NFC, qs(d, 1, j) + l * NFC);
     }
     __syncthreads();
     // ---- A3 hydro: one direction per round, 576 faces each
@@ -1470,8 +1570,7 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
         float gl, gr;
         float a = kt_hydro32(wl, wr, d, gamma, inv_gm1, knp, fo, FS, gl, gr);
         float* g = GG + ((d * NLN + l) * NFC + i) * 2;
-        g[0] = gl;
-        g[1] = gr;
+        store_pair(g, gl, gr);
         const int e_d = d == 0 ? ex : (d == 1 ? ey : ez);
         const int e_a = d == 0 ? ey : ex;
         const int e_b = d == 2 ? ey : ez;
@@ -1516,18 +1615,23 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
         bool valid = full || pipe_valid(x, y, z, ex, ey, ez);
         float r = RR[s];
         float xs[6];
+        unsigned oor = 0;
 #pragma unroll
         for (int f = 0; f < 6; f++) {
           xs[f] = 0.0f;
-          if (f < nsp && valid) {
-            double v = S[f * STAR + s];
-            bad |= !dfinite(v);
-            xs[f] = d2f_int(v) * r;
-          }
+          if (f < nsp && valid) xs[f] = d2f_fast_pos(S[f * STAR + s], oor) * r;
+        }
+        if (oor >= D2F_OOR) {  // rare: convert the cell's species again
+#pragma unroll
+          for (int f = 0; f < 6; f++)
+            if (f < nsp && valid) xs[f] = d2f_slow(S[f * STAR + s]) * r;
         }
 #pragma unroll
+        for (int f = 0; f < 6; f++)  // a non-finite input leaves a non-finite quotient
+          if (f < nsp) bad |= !isfinite(xs[f]);
+#pragma unroll
         for (int j = 0; j < 3; j++)
-          if (j < npair) W[j * STAR + s] = make_float2(xs[2 * j], xs[2 * j + 1]);
+          if (j < npair) W[j * WSTAR + sx.w[k]] = make_float2(xs[2 * j], xs[2 * j + 1]);
       }
       bad = __syncthreads_or(bad);
       if (tn < n_tiles) pipe_issue<DOM>(fetch, fetch(tn), sx, S, 0, 6);
@@ -1536,7 +1640,7 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
         const int d = tid / (3 * NLN), rem = tid - d * 3 * NLN, j = rem / NLN, l = rem - j * NLN;
         if (j < npair) {
           LineAddr la = line_addr(d, l);
-          ppm_line32x2(W + j * STAR, la, qs(d, 0, j) + l * NFC, qs(d, 1, j) + l * NFC);
+          ppm_line32x2(W + j * WSTAR, la, qs(d, 0, j) + l * NFC, qs(d, 1, j) + l * NFC);
         }
       }
       __syncthreads();
@@ -1548,7 +1652,8 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
           float2* fo = qs(d, 0, 0) + l * NFC + i;
           const float2* fr = qs(d, 1, 0) + l * NFC + i;
           const float* g = GG + ((d * NLN + l) * NFC + i) * 2;
-          const float gl = g[0], gr = g[1];
+          float gl, gr;
+          load_pair(g, gl, gr);
 #pragma unroll
           for (int j = 0; j < 3; j++)
             if (j < npair) fo[j * FS] = fma2(fo[j * FS], f2(gl), mul2(fr[j * FS], f2(gr)));

@@ -6,10 +6,15 @@ Binary64 form (the 1e-12 gate): per sub-grid and field,
   S_f = amax * max|U_f| / dx  (a flux-divergence scale, so that exact zeros of
   a uniform region do not divide by zero); amax within 1e-14 relative.
 
-Mixed form against the oracle's mixed mode: both take binary32 face fluxes,
-so they may differ by a few binary32 roundings of the flux magnitude:
-  max_i |gpu - oracle| <= 64 * 2^-24 * S32_f / dx,
-  S32_f = 2 amax (max|U_f| + [f in 1..4] max E)  (bound of |Fhat_f|).
+Mixed form against the oracle's mixed mode (the same definition: binary32
+primitives from the binary32-rounded conserved values, binary64 internal
+energy and switch, binary32 reconstruction and flux, binary64 divergence):
+both take binary32 face fluxes, which differ by the roundings of differently
+ordered (fused) operations and by the binary32 reciprocal, so a result may
+differ by a few binary32 ulps of the flux scale:
+  max_i |gpu - oracle| <= 8 * 2^-24 * S32_f / dx,
+  S32_f = 2 amax (max|U_f| + [f in 1..4] max E)  (a scale of |Fhat_f|);
+the largest ratio measured over the GPU tests is ~5.2 of these ulps.
 """
 from __future__ import annotations
 
@@ -131,7 +136,7 @@ def flux_bounds(U, amax, gamma=G53):
     return S
 
 
-def check_mixed(got, ref, got_amax, ref_amax, blocks, dxs, ulps=64):
+def check_mixed(got, ref, got_amax, ref_amax, blocks, dxs, ulps=8, label="mixed"):
     """Gate: |gpu - oracle| <= ulps * 2^-24 * S32_f / dx per (sub-grid, field).
     Records the worst ratio in binary32 ulps of that scale and of the tighter
     flux bound of flux_bounds."""
@@ -149,9 +154,9 @@ def check_mixed(got, ref, got_amax, ref_amax, blocks, dxs, ulps=64):
             worst_fb = max(worst_fb, err / (EPS32 * fb[f] / dxs[s]))
             assert err <= bound, ("sub-grid", s, "field", f, err, bound)
     rel = np.abs(got_amax - ref_amax) / np.maximum(ref_amax, 1e-300)
-    _record("mixed ulps of S32", worst * ulps)
-    _record("mixed ulps of flux bound", worst_fb)
-    _record("mixed amax rel", rel.max() if len(rel) else 0.0)
+    _record(label + " ulps of S32", worst * ulps)
+    _record(label + " ulps of flux bound", worst_fb)
+    _record(label + " amax rel", rel.max() if len(rel) else 0.0)
     assert rel.max() <= 1e-6, rel.max()
     return worst
 

@@ -60,12 +60,16 @@ def test_plain_aggregation_512_subgrids(prec, flags):
         gh.check_fp64(got, ref, gam, ram, blocks, dxs)
     else:
         gh.check_mixed(got, ref, gam, ram, blocks, dxs)
-        # against the binary64 oracle: the same flux-scaled binary32 bound, and a
-        # normwise cap on smooth data (the error grows with the cancellation in
-        # the flux differences, i.e. with resolution)
+        # against the binary64 oracle: the flux-scaled binary32 bound, and a
+        # normwise cap just above the scheme's own error here -- the oracle's
+        # mixed mode differs from its binary64 mode by 1.44e-5 normwise on this
+        # domain (the error grows with the cancellation in the flux
+        # differences, i.e. with resolution)
         ref64, ram64, _ = gh.oracle_ref(list(blocks), dxs, mode=0)
-        gh.check_mixed(got, ref64, gam, ram64, blocks, dxs)
-        assert gh.normwise_vs(got, ref64) <= 1e-4
+        gh.check_mixed(got, ref64, gam, ram64, blocks, dxs, ulps=16, label="mixed vs fp64")
+        nw = gh.normwise_vs(got, ref64)
+        gh._record("mixed vs fp64 normwise", nw)
+        assert nw <= 2e-5
     # periodic domain: the GPU result conserves every field on its own
     tot = np.sum([o.sum(axis=(1, 2, 3)) for o in got], axis=0)
     mag = np.sum([np.abs(o).sum(axis=(1, 2, 3)) for o in got], axis=0)
