@@ -111,28 +111,9 @@ __device__ __forceinline__ void cell_of(int s, int& x, int& y, int& z) {
   }
 }
 
-// The binary32/binary64 primitives of the read region (W) use a padded
-// copy of that layout, so that the reconstruction's line reads meet no
-// shared-memory bank conflicts along x and y (and 2-way ones on the interior
-// part of the z lines): interior rows of pitch WP = 15 elements instead of
-// 14, and y ghost slabs of z pitch WYZ = 56 instead of 48.  Sixteen lines of
-// a half warp then read sixteen distinct 8-byte banks (odd row pitch along
-// x; rows 8 apart land 8 banks apart along y).  The staging buffer and 1/rho
-// keep the dense slots; wslot maps a dense slot to its W slot.
-constexpr int WP = LL + 1;                 // interior row pitch in W
-constexpr int WYZ = 6 * TE + TE;           // z pitch of the y slabs in W
-constexpr int WXROWS = TE * TE * WP;       // 960
-constexpr int WYSLAB = TE * WYZ;           // 448
-constexpr int WSTAR = WXROWS + WYSLAB + 6 * TE * TE;  // 1792 slots per field in W
-__host__ __device__ __forceinline__ int wslot(int s) {
-  if (s < XROWS) return s + s / LL;                     // row s/14 gains one slot per row
-  if (s < XROWS + YSLAB) return s + (WXROWS - XROWS) + TE * ((s - XROWS) / (6 * TE));
-  return s + (WXROWS - XROWS) + (WYSLAB - YSLAB);
-}
-
-// Addressing of line l along direction d in W: three segments (3 low
-// ghosts, TE interior cells, 3 high ghosts), each with a base slot and a
-// constant stride.
+// Addressing of line l along direction d in the read-region layout: three
+// segments (3 low ghosts, TE interior cells, 3 high ghosts), each with a
+// base slot and a constant stride.
 struct LineAddr {
   int lo, in, hi, sg, si;
   __device__ __forceinline__ int at(int c) const {
@@ -142,13 +123,13 @@ struct LineAddr {
 __device__ __forceinline__ LineAddr line_addr(int d, int l) {
   int a = l % TE, b = l / TE;
   if (d == 0) {
-    int base = (b * TE + a) * WP;
+    int base = (b * TE + a) * LL;
     return {base, base + 3, base + 3 + TE, 1, 1};
   }
   if (d == 1)
-    return {WXROWS + b * WYZ + a, b * TE * WP + a + 3, WXROWS + b * WYZ + 3 * TE + a, TE, WP};
-  return {WXROWS + WYSLAB + b * TE + a, b * WP + a + 3, WXROWS + WYSLAB + 3 * TE * TE + b * TE + a,
-          TE * TE, TE * WP};
+    return {XROWS + b * 6 * TE + a, b * TE * LL + a + 3, XROWS + b * 6 * TE + 3 * TE + a, TE, LL};
+  return {XROWS + YSLAB + b * TE + a, b * LL + a + 3, XROWS + YSLAB + 3 * TE * TE + b * TE + a,
+          TE * TE, TE * LL};
 }
 
 // --------------------------------------------------- periodic domains --
@@ -503,14 +484,18 @@ __device__ __forceinline__ float rcp32(float x) {  // seed + one Newton step
   return fmaf(fmaf(-x, y, 1.0f), y, y);
 }
 
-// tau^gamma in binary32 (gamma = 5/3: seed + one Halley step on w^3 = tau^2)
+// tau^gamma in binary32: for gamma = 5/3 and tau in (1e-18, 1e18),
+// tau * w with w^3 = tau^2 (seed exp2(2/3 log2 tau), one Halley step);
+// otherwise exp2(gamma log2 tau).  Both are evaluated and one is selected,
+// so that the code has no branch.
 __device__ __forceinline__ float tau_pow32(float tau, float gamma, bool g53) {
-  if (!g53 || !(tau > 1e-18f && tau < 1e18f)) return exp2f(gamma * __log2f(tau));
-  float w = exp2f((2.0f / 3.0f) * __log2f(tau));
-  float A = tau * tau;
-  float w3 = w * w * w;
+  const float lt = __log2f(tau);
+  const float gen = exp2f(gamma * lt);
+  float w = exp2f((2.0f / 3.0f) * lt);
+  const float A = tau * tau;
+  const float w3 = w * w * w;
   w = w * fmaf(2.0f, A, w3) * rcp32(fmaf(2.0f, w3, A));
-  return tau * w;
+  return (g53 && tau > 1e-18f && tau < 1e18f) ? tau * w : gen;
 }
 
 // ------------------------------------------------------ step A1, mixed --
@@ -527,13 +512,38 @@ __device__ __forceinline__ float tau_pow32(float tau, float gamma, bool g53) {
 // binary64 in the reference order of operations.
 // u: the binary64 hydro inputs of one cell (fields 0-5); writes binary32
 // primitives (rho, vx, vy, vz, p, phi) and r = 1/rho.
-__device__ __forceinline__ bool prim_mixed(const double* u, double gamma, float gamf, float gm1f,
-                                           bool g53, float* w, float& r) {
+// The common path, without branches: every value in the fast conversion's
+// range and the binary32 estimate of e settling the branch.  Returns true
+// where that does not hold, and the cell takes prim_mixed_slow.
+__device__ __forceinline__ bool prim_mixed_fast(const double* u, float gamf, float gm1f, bool g53, float* w,
+                                                float& r) {
+  unsigned oor = 0;
+  const float rho = d2f_fast_pos(u[0], oor);
+  const float s1 = d2f_fast(u[1], oor), s2 = d2f_fast(u[2], oor), s3 = d2f_fast(u[3], oor);
+  const float E = d2f_fast_pos(u[4], oor), tau = d2f_fast_pos(u[5], oor);
+  r = rcp32(rho);
+  const float ssq = fmaf(s3, s3, fmaf(s2, s2, s1 * s1));
+  const float eint = fmaf(-0.5f * ssq, r, E);
+  const bool kin = eint >= 0.5f * E;                          // not switched
+  const bool sw = eint <= (float)(0.5 * ETA) * E;             // switched
+  const float ptau = gm1f * tau_pow32(tau, gamf, g53);
+  w[0] = rho;
+  w[1] = s1 * r;
+  w[2] = s2 * r;
+  w[3] = s3 * r;
+  w[4] = kin ? gm1f * eint : ptau;
+  w[5] = tau * r;
+  return oor >= D2F_OOR || !(kin || sw);
+}
+// The careful path: values outside the fast conversion's range converted
+// with the instruction, and e and the branch in binary64 inside the window.
+__device__ __forceinline__ void prim_mixed_slow(const double* u, double gamma, float gamf, float gm1f, bool g53,
+                                                float* w, float& r) {
   unsigned oor = 0;
   float rho = d2f_fast_pos(u[0], oor);
   float s1 = d2f_fast(u[1], oor), s2 = d2f_fast(u[2], oor), s3 = d2f_fast(u[3], oor);
   float E = d2f_fast_pos(u[4], oor), tau = d2f_fast_pos(u[5], oor);
-  if (oor >= D2F_OOR) {  // rare: a value outside the fast conversion's range
+  if (oor >= D2F_OOR) {
     rho = d2f_slow(u[0]);
     s1 = d2f_slow(u[1]);
     s2 = d2f_slow(u[2]);
@@ -561,14 +571,21 @@ __device__ __forceinline__ bool prim_mixed(const double* u, double gamma, float 
   w[3] = s3 * r;
   w[4] = p;
   w[5] = tau * r;
-  // nonphysical: rho <= 0, p <= 0 or a non-finite value.  A non-finite input
-  // (or one beyond the binary32 range) leaves a non-finite primitive, so the
-  // binary32 primitives alone decide it, as the binary32 quotients do in the
-  // reference definition of the mixed form.
-  bool bad = !(rho > 0.0f) || !(p > 0.0f);
+}
+// nonphysical: rho <= 0, p <= 0 or a non-finite value.  A non-finite input
+// (or one beyond the binary32 range) leaves a non-finite primitive, so the
+// binary32 primitives alone decide it, as the binary32 quotients do in the
+// reference definition of the mixed form.
+__device__ __forceinline__ bool prim_mixed_bad(const float* w) {
+  bool bad = !(w[0] > 0.0f) || !(w[4] > 0.0f);
 #pragma unroll
   for (int f = 0; f < 6; f++) bad |= !isfinite(w[f]);
   return bad;
+}
+__device__ __forceinline__ bool prim_mixed(const double* u, double gamma, float gamf, float gm1f,
+                                           bool g53, float* w, float& r) {
+  if (prim_mixed_fast(u, gamf, gm1f, g53, w, r)) prim_mixed_slow(u, gamma, gamf, gm1f, g53, w, r);
+  return prim_mixed_bad(w);
 }
 
 // -------------------------------------------- packed binary32 arithmetic --
@@ -824,7 +841,7 @@ constexpr int NGRP = 6;  // fields per group: hydro (rho, vx, vy, vz, p, phi) or
 
 // Shared memory of one CTA.  V = R (binary64) or a pair of binary32 values
 // (mixed form: fields 2k and 2k+1 of a group share one 8-byte element):
-//   W  [NGRP/PACK][WSTAR] V  primitives of the read region (padded slots): the hydro group,
+//   W  [NGRP/PACK][STAR] V   primitives of the read region: the hydro group,
 //                            then (after the hydro pass) the species
 //   RR [STAR] R              1/rho of every read cell
 //   GG [3][NLN][NFC][2] R    per face the factors g_l, g_r of the species fluxes
@@ -832,7 +849,7 @@ constexpr int NGRP = 6;  // fields per group: hydro (rho, vx, vy, vz, p, phi) or
 template <int MODE>
 __host__ __device__ constexpr size_t smem_layout_bytes(int lch) {
   return (MODE == 0 ? 8 : 4) *
-         ((size_t)NGRP * WSTAR + STAR + 3 * NLN * NFC * 2 + 2 * (size_t)NGRP * lch * NFC);
+         ((size_t)NGRP * STAR + STAR + 3 * NLN * NFC * 2 + 2 * (size_t)NGRP * lch * NFC);
 }
 
 // ------------------------------------------------------------ forests --
@@ -990,7 +1007,7 @@ __device__ __forceinline__ void group_pass(
       for (int task = tid; task < lch * ng; task += NT) {
         int ll = task % lch, j = task / lch;
         LineAddr la = line_addr(d, l0 + ll);
-        const V* w = W + j * WSTAR;
+        const V* w = W + j * STAR;
         if constexpr (MODE == 0) {
           ppm_line64(w, la, QS + j * fs + ll * NFC, QR + j * fs + ll * NFC);
         } else {
@@ -1152,7 +1169,7 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
   constexpr int NS = NGRP / PK;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* W = reinterpret_cast<V*>(smem_raw);
-  R* RR = reinterpret_cast<R*>(W + NS * WSTAR);
+  R* RR = reinterpret_cast<R*>(W + NS * STAR);
   R* GG = RR + STAR;
   V* QS = reinterpret_cast<V*>(GG + 3 * NLN * NFC * 2);
   __shared__ double red[NT / 32];
@@ -1238,10 +1255,10 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
         }
         if constexpr (MODE == 0) {
 #pragma unroll
-          for (int f = 0; f < 6; f++) W[f * WSTAR + wslot(s)] = w[f];
+          for (int f = 0; f < 6; f++) W[f * STAR + s] = w[f];
         } else {
 #pragma unroll
-          for (int j = 0; j < 3; j++) W[j * WSTAR + wslot(s)] = make_float2(w[2 * j], w[2 * j + 1]);
+          for (int j = 0; j < 3; j++) W[j * STAR + s] = make_float2(w[2 * j], w[2 * j + 1]);
         }
         RR[s] = r;
       }
@@ -1318,11 +1335,11 @@ __device__ __forceinline__ void tile_loop(const Fetch& fetch, int n_tiles, int l
           if constexpr (MODE == 0) {
 #pragma unroll
             for (int f = 0; f < MAXF - 6; f++)
-              if (f < nsp) W[f * WSTAR + wslot(s)] = x[f];
+              if (f < nsp) W[f * STAR + s] = x[f];
           } else {
 #pragma unroll
             for (int j = 0; j < 3; j++)
-              if (2 * j < nsp) W[j * WSTAR + wslot(s)] = make_float2(x[2 * j], 2 * j + 1 < MAXF - 6 ? x[2 * j + 1] : 0.0f);
+              if (2 * j < nsp) W[j * STAR + s] = make_float2(x[2 * j], 2 * j + 1 < MAXF - 6 ? x[2 * j + 1] : 0.0f);
           }
         }
       }
@@ -1383,41 +1400,147 @@ rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
 // (cp.async, global -> shared, no registers held) into a staging buffer, one
 // field group ahead: the species of tile t arrive while its hydro group is
 // reconstructed and fluxed, and the hydro group of the CTA's next tile while
-// its species are.  One CTA of PNT threads per SM; the three directions are
-// reconstructed together, so every phase divides evenly over the threads:
+// its species are.  Full tiles of ghosted blocks whose rows start 16-byte
+// aligned move in 16-byte copies: the interior rows with their x ghosts
+// (7 per row) and every ghost-slab row as the aligned span x = -1 .. TE
+// (5 per row; the 32-byte sectors the cells x = 0 .. TE-1 occupy in any
+// case); other tiles (partial, periodic domains, forests, misaligned
+// blocks) use one 8-byte copy per cell.  One CTA of PNT threads per SM; the
+// three directions are reconstructed together, so every phase divides
+// evenly over the threads:
 //   PPM   3 directions x 64 lines x 3 field pairs = 576 tasks
 //   flux  3 rounds (one per direction) of 64 lines x 9 faces = 576 faces
 //   A4    one interior cell per thread (threads 0..511)
-// Shared memory (bytes): S  [6][STAR] binary64 staging      79872
-//                        W  [3][WSTAR] float2 primitives    43008
-//                        RR [STAR] float 1/rho               6656
+// Shared memory (bytes): S  [6][SSTAR] binary64 staging     89088
+//                        W  [3][STAR] float2 primitives     39936
 //                        GG [3][NLN][NFC][2] float          13824
 //                        QS [3][2][3][NLN][NFC] float2      82944
+// Staging layout of one field: the interior rows [z][y][LL] as in the read
+// region (XROWS), then the y-ghost rows [z][yg][SROW] and the z-ghost rows
+// [zg][y][SROW], each holding x = -1 .. TE.
 constexpr int PNT = 3 * NLN * 3;  // 576
 constexpr int PSPT = (STAR + PNT - 1) / PNT;  // read-region slots per thread: 3
+constexpr int SROW = TE + 2;                  // a staged ghost-slab row
+constexpr int SSTAR = XROWS + 2 * 6 * TE * SROW;  // 1856 staged values per field
 __host__ __device__ constexpr size_t pipe_smem_bytes() {
-  return (size_t)6 * STAR * 8 + 3 * WSTAR * 8 + STAR * 4 + 3 * NLN * NFC * 2 * 4 + 3 * 2 * 3 * NLN * NFC * 8;
+  return (size_t)6 * SSTAR * 8 + 3 * STAR * 8 + 3 * NLN * NFC * 2 * 4 + 3 * 2 * 3 * NLN * NFC * 8;
+}
+// staging slot of read-region slot s
+__host__ __device__ __forceinline__ int sslot(int s) {
+  if (s < XROWS) return s;
+  const int t = s - XROWS;  // ghost-slab cell: row t / TE, x = t % TE
+  return XROWS + (t / TE) * SROW + (t % TE) + 1;
 }
 
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Fetch tile t's descriptor into shared memory (one thread): a work list's
+// entry by asynchronous copies (complete at the thread's next wait), other
+// tile sources by computing it.
+template <class Fetch>
+__device__ __forceinline__ void prefetch_desc(const Fetch& fetch, int t, Tile* dst) {
+  *dst = fetch(t);
+}
+__device__ __forceinline__ void prefetch_desc(const TileList& fetch, int t, Tile* dst) {
+  const char* src = reinterpret_cast<const char*>(fetch.tiles + t);
+#pragma unroll
+  for (int i = 0; i < 4; i++) cp_async16(reinterpret_cast<char*>(dst) + 16 * i, src + 16 * i);
+  cp_async_commit();
+}
+
+__device__ __forceinline__ void cp_async16cg(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// 16-byte copies: a full tile of a ghosted block whose rows start 16-byte
+// aligned (G even, odd ghost width, block 16-byte aligned), so that the
+// interior rows (from x = -3) and the ghost-slab rows (from x = -1) do.
+template <int DOM>
+__device__ __forceinline__ bool chunk_ok(const Tile& tile) {
+  if constexpr (DOM != 0) {
+    return false;
+  } else {
+    const int gh = (tile.G - tile.N) >> 1;
+    return tile.N - tile.ox >= TE && tile.N - tile.oy >= TE && tile.N - tile.oz >= TE && (tile.G & 1) == 0 &&
+           (gh & 1) == 1 && (reinterpret_cast<uintptr_t>(tile.U) & 15) == 0;
+  }
+}
+// The 16-byte chunks of one field's staging: 7 per interior row (64 rows),
+// 5 per ghost-slab row (96 rows); every thread takes chunks tid and
+// tid + PNT.  A chunk is (z, y, x0) of its first cell, x0 in {-3, -1} + 2k,
+// and its staging slot.
+constexpr int NCHUNK = TE * TE * (LL / 2) + 2 * 6 * TE * (SROW / 2);  // 928
+constexpr int PCPT = (NCHUNK + PNT - 1) / PNT;                          // chunks per thread: 2
+struct ChunkGeom {
+  int zyx[PCPT];  // z, y, x0 as signed bytes; 0x7f7f7f7f: none
+  int st[PCPT];   // staging slot of the first double
+  __device__ __forceinline__ void init(int tid) {
+#pragma unroll
+    for (int k = 0; k < PCPT; k++) {
+      const int c = tid + k * PNT;
+      int z = 0, y = 0, x0 = 0, slot = 0;
+      if (c < TE * TE * (LL / 2)) {
+        const int row = c / (LL / 2), q = c % (LL / 2);
+        z = row / TE;
+        y = row % TE;
+        x0 = -3 + 2 * q;
+        slot = row * LL + 2 * q;
+      } else if (c < NCHUNK) {
+        const int c2 = c - TE * TE * (LL / 2), r = c2 / (SROW / 2), q = c2 % (SROW / 2);
+        if (r < 6 * TE) {
+          z = r / 6;
+          const int yg = r % 6;
+          y = yg < 3 ? yg - 3 : yg + TE - 3;
+        } else {
+          const int r2 = r - 6 * TE, zg = r2 / TE;
+          y = r2 % TE;
+          z = zg < 3 ? zg - 3 : zg + TE - 3;
+        }
+        x0 = -1 + 2 * q;
+        slot = XROWS + r * SROW + 2 * q;
+      }
+      zyx[k] = c < NCHUNK ? ((z & 0xff) | ((y & 0xff) << 8) | ((x0 & 0xff) << 16)) : 0x7f7f7f7f;
+      st[k] = slot;
+    }
+  }
+};
+// Issue the 16-byte copies of fields f0 .. f0+nf-1 (chunk_ok tiles).
+__device__ __forceinline__ void chunk_issue(const Tile& tile, const ChunkGeom& cg, double* S, int f0, int nf) {
+  const int G = tile.G, gh = (G - tile.N) >> 1;
+  const long long plane = (long long)G * G * G;
+  const double* base = tile.U + (long long)f0 * plane +
+                       ((long long)(tile.oz + gh) * G + (tile.oy + gh)) * G + (tile.ox + gh);
+#pragma unroll
+  for (int k = 0; k < PCPT; k++) {
+    if (cg.zyx[k] == 0x7f7f7f7f) continue;
+    const int z = (int)(signed char)(cg.zyx[k] & 0xff), y = (int)(signed char)((cg.zyx[k] >> 8) & 0xff),
+              x0 = (int)(signed char)((cg.zyx[k] >> 16) & 0xff);
+    const double* src = base + ((long long)z * G + y) * G + x0;
+#pragma unroll
+    for (int f = 0; f < 6; f++)
+      if (f < nf) cp_async16cg(S + f * SSTAR + cg.st[k], src + f * plane);
+  }
+}
 
 // Read-region geometry of one thread's slots, computed once per kernel:
-// tile-local (x, y, z) packed as three signed bytes.
+// tile-local (x, y, z) packed as three signed bytes, and the staging slot.
 struct SlotXYZ {
   int p[PSPT];
-  int w[PSPT];  // the slot's index in W
+  int ss[PSPT];
   __device__ __forceinline__ void init(int tid) {
 #pragma unroll
     for (int k = 0; k < PSPT; k++) {
       int s = tid + k * PNT, x = 0, y = 0, z = 0;
       if (s < STAR) cell_of(s, x, y, z);
       p[k] = (x & 0xff) | ((y & 0xff) << 8) | ((z & 0xff) << 16);
-      w[k] = wslot(s < STAR ? s : 0);
+      ss[k] = sslot(s < STAR ? s : 0);
     }
   }
   __device__ __forceinline__ void get(int k, int& x, int& y, int& z) const {
@@ -1446,11 +1569,17 @@ __device__ __forceinline__ int pipe_offset(const Tile& tile, const DomainPos& dp
   }
 }
 
-// Issue the copies of fields f0 .. f0+nf-1 of the tile's read region into S
-// (DOM as in tile_loop; a forest locates cells through fetch.loc).
+// Issue the copies of fields f0 .. f0+nf-1 of the tile's read region into S:
+// 16-byte copies where chunk_ok, else one 8-byte copy per cell (DOM as in
+// tile_loop; a forest locates cells through fetch.loc).
 template <int DOM, class Fetch>
-__device__ __forceinline__ void pipe_issue(const Fetch& fetch, const Tile& tile, const SlotXYZ& sx, double* S,
-                                           int f0, int nf) {
+__device__ __forceinline__ void pipe_issue(const Fetch& fetch, const Tile& tile, const SlotXYZ& sx,
+                                           const ChunkGeom& cg, double* S, int f0, int nf) {
+  if (chunk_ok<DOM>(tile)) {
+    chunk_issue(tile, cg, S, f0, nf);
+    cp_async_commit();
+    return;
+  }
   const int N = tile.N;
   const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
   const long long plane = DOM ? (long long)N * N * N : (long long)tile.G * tile.G * tile.G;
@@ -1476,11 +1605,10 @@ __device__ __forceinline__ void pipe_issue(const Fetch& fetch, const Tile& tile,
     }
 #pragma unroll
     for (int f = 0; f < 6; f++)
-      if (f < nf) cp_async8(S + f * STAR + s, src + f * plane);
+      if (f < nf) cp_async8(S + f * SSTAR + sx.ss[k], src + f * plane);
   }
   cp_async_commit();
 }
-
 template <class Fetch, int DOM>
 __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, double* __restrict__ out,
                                                double* __restrict__ amax_out, Status* __restrict__ status,
@@ -1489,9 +1617,8 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
   typedef P2 Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* S = reinterpret_cast<double*>(smem_raw);
-  float2* W = reinterpret_cast<float2*>(S + 6 * STAR);
-  float* RR = reinterpret_cast<float*>(W + 3 * WSTAR);
-  float* GG = RR + STAR;
+  float2* W = reinterpret_cast<float2*>(S + 6 * SSTAR);
+  float* GG = reinterpret_cast<float*>(W + 3 * STAR);
   float2* QS = reinterpret_cast<float2*>(GG + 3 * NLN * NFC * 2);
   __shared__ double red[PNT / 32];
   const int tid = threadIdx.x;
@@ -1504,46 +1631,76 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
   auto qs = [&](int d, int side, int j) { return QS + ((d * 2 + side) * 3 + j) * FS; };
   SlotXYZ sx;
   sx.init(tid);
+  ChunkGeom cg;
+  cg.init(tid);
+  // Tile descriptors, double-buffered in shared memory: thread 0 fetches the
+  // next tile's while the current one is converted, so that its latency is
+  // hidden before the next tile's copies are issued.
+  __shared__ Tile tsm[2];
 
   int t = blockIdx.x;
-  if (t < n_tiles) pipe_issue<DOM>(fetch, fetch(t), sx, S, 0, 6);
-  for (; t < n_tiles; t += gridDim.x) {
-    const Tile tile = fetch(t);
+  if (tid == 0 && t < n_tiles) tsm[0] = fetch(t);
+  __syncthreads();
+  if (t < n_tiles) pipe_issue<DOM>(fetch, tsm[0], sx, cg, S, 0, 6);
+  for (int it = 0; t < n_tiles; t += gridDim.x, it ^= 1) {
+    const Tile tile = tsm[it];
     const int F = tile.F, N = tile.N, nsp = F - 6;
     const int ex = min(TE, N - tile.ox), ey = min(TE, N - tile.oy), ez = min(TE, N - tile.oz);
     const bool full = ex == TE && ey == TE && ez == TE;
     const int tn = t + (int)gridDim.x;
 
-    // ---- A0/A1 hydro: staged binary64 (rho, s, E, tau) -> binary32 primitives
+    // ---- A0/A1 hydro: staged binary64 (rho, s, E, tau) -> binary32 primitives.
+    // The common path of every slot first (straight-line code, so that the
+    // slots' long latency chains interleave), then the careful path for the
+    // few cells that need it.
     cp_async_wait_all();
     __syncthreads();
+    if (tid == 0 && tn < n_tiles) prefetch_desc(fetch, tn, &tsm[it ^ 1]);
     bool bad = false;
+    {
+      float w[PSPT][6], r[PSPT];
+      bool need[PSPT], valid[PSPT];
 #pragma unroll
-    for (int k = 0; k < PSPT; k++) {
-      int s = tid + k * PNT;
-      if (s >= STAR) continue;
-      int x, y, z;
-      sx.get(k, x, y, z);
-      bool valid = full || pipe_valid(x, y, z, ex, ey, ez);
-      float w[6], r;
-      if (valid) {
-        double u[6];
+      for (int k = 0; k < PSPT; k++) {
+        const int s = tid + k * PNT;
+        int x, y, z;
+        sx.get(k, x, y, z);
+        valid[k] = s < STAR && (full || pipe_valid(x, y, z, ex, ey, ez));
+        need[k] = false;
+        if (valid[k]) {
+          double u[6];
 #pragma unroll
-        for (int f = 0; f < 6; f++) u[f] = S[f * STAR + s];
-        bad |= prim_mixed(u, gamma_d, gamma, gm1f, g53, w, r);
-      } else {
+          for (int f = 0; f < 6; f++) u[f] = S[f * SSTAR + sx.ss[k]];
+          need[k] = prim_mixed_fast(u, gamma, gm1f, g53, w[k], r[k]);
+        } else {
 #pragma unroll
-        for (int f = 0; f < 6; f++) w[f] = (f == 0 || f == 4) ? 1.0f : 0.0f;
-        r = 1.0f;
+          for (int f = 0; f < 6; f++) w[k][f] = (f == 0 || f == 4) ? 1.0f : 0.0f;
+          r[k] = 1.0f;
+        }
       }
 #pragma unroll
-      for (int j = 0; j < 3; j++) W[j * WSTAR + sx.w[k]] = make_float2(w[2 * j], w[2 * j + 1]);
-      RR[s] = r;
+      for (int k = 0; k < PSPT; k++) {
+        if (need[k]) {
+          double u[6];
+#pragma unroll
+          for (int f = 0; f < 6; f++) u[f] = S[f * SSTAR + sx.ss[k]];
+          prim_mixed_slow(u, gamma_d, gamma, gm1f, g53, w[k], r[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < PSPT; k++) {
+        const int s = tid + k * PNT;
+        if (s >= STAR) continue;
+        if (valid[k]) bad |= prim_mixed_bad(w[k]);
+#pragma unroll
+        for (int j = 0; j < 3; j++) W[j * STAR + s] = make_float2(w[k][2 * j], w[k][2 * j + 1]);
+      }
     }
+    if (tid == 0) cp_async_wait_all();  // the next tile's descriptor
     bad = __syncthreads_or(bad);
     // the staging buffer is free: species of this tile, or the next tile
-    if (nsp > 0) pipe_issue<DOM>(fetch, tile, sx, S, 6, nsp);
-    else if (tn < n_tiles) pipe_issue<DOM>(fetch, fetch(tn), sx, S, 0, 6);
+    if (nsp > 0) pipe_issue<DOM>(fetch, tile, sx, cg, S, 6, nsp);
+    else if (tn < n_tiles) pipe_issue<DOM>(fetch, tsm[it ^ 1], sx, cg, S, 0, 6);
 
     float amax = 0.0f;
     Acc acc[1][3];
@@ -1551,7 +1708,7 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
     {
       const int d = tid / (3 * NLN), rem = tid - d * 3 * NLN, j = rem / NLN, l = rem - j * NLN;
       LineAddr la = line_addr(d, l);
-      ppm_line32x2(W + j * WSTAR, la, qs(d, 0, j) + l * NFC, qs(d, 1, j) + l * NFC);
+      ppm_line32x2(W + j * STAR, la, qs(d, 0, j) + l * NFC, qs(d, 1, j) + l * NFC);
     }
     __syncthreads();
     // ---- A3 hydro: one direction per round, 576 faces each
@@ -1603,44 +1760,57 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
 
     if (nsp > 0) {
       const int npair = (nsp + 1) / 2;
-      // ---- A0/A1 species: X_k = rho_k / rho
+      // ---- A0/A1 species: X_k = rho_k / rho (every slot first, then the
+      // rare cells with a value outside the fast conversion's range); 1/rho
+      // is formed again from the staged rho, bit for bit the hydro pass's
       cp_async_wait_all();
       __syncthreads();
+      {
+        float xs[PSPT][6], rs[PSPT];
+        unsigned oor[PSPT];
+        bool valid[PSPT];
 #pragma unroll
-      for (int k = 0; k < PSPT; k++) {
-        int s = tid + k * PNT;
-        if (s >= STAR) continue;
-        int x, y, z;
-        sx.get(k, x, y, z);
-        bool valid = full || pipe_valid(x, y, z, ex, ey, ez);
-        float r = RR[s];
-        float xs[6];
-        unsigned oor = 0;
+        for (int k = 0; k < PSPT; k++) {
+          const int s = tid + k * PNT;
+          int x, y, z;
+          sx.get(k, x, y, z);
+          valid[k] = s < STAR && (full || pipe_valid(x, y, z, ex, ey, ez));
+          rs[k] = s < STAR ? rcp32(W[s].x) : 0.0f;
+          oor[k] = 0;
 #pragma unroll
-        for (int f = 0; f < 6; f++) {
-          xs[f] = 0.0f;
-          if (f < nsp && valid) xs[f] = d2f_fast_pos(S[f * STAR + s], oor) * r;
-        }
-        if (oor >= D2F_OOR) {  // rare: convert the cell's species again
-#pragma unroll
-          for (int f = 0; f < 6; f++)
-            if (f < nsp && valid) xs[f] = d2f_slow(S[f * STAR + s]) * r;
+          for (int f = 0; f < 6; f++) {
+            xs[k][f] = 0.0f;
+            if (f < nsp && valid[k]) xs[k][f] = d2f_fast_pos(S[f * SSTAR + sx.ss[k]], oor[k]) * rs[k];
+          }
         }
 #pragma unroll
-        for (int f = 0; f < 6; f++)  // a non-finite input leaves a non-finite quotient
-          if (f < nsp) bad |= !isfinite(xs[f]);
+        for (int k = 0; k < PSPT; k++) {
+          if (oor[k] >= D2F_OOR) {
 #pragma unroll
-        for (int j = 0; j < 3; j++)
-          if (j < npair) W[j * WSTAR + sx.w[k]] = make_float2(xs[2 * j], xs[2 * j + 1]);
+            for (int f = 0; f < 6; f++)
+              if (f < nsp) xs[k][f] = d2f_slow(S[f * SSTAR + sx.ss[k]]) * rs[k];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < PSPT; k++) {
+          const int s = tid + k * PNT;
+          if (s >= STAR) continue;
+#pragma unroll
+          for (int f = 0; f < 6; f++)  // a non-finite input leaves a non-finite quotient
+            if (f < nsp) bad |= !isfinite(xs[k][f]);
+#pragma unroll
+          for (int j = 0; j < 3; j++)
+            if (j < npair) W[j * STAR + s] = make_float2(xs[k][2 * j], xs[k][2 * j + 1]);
+        }
       }
       bad = __syncthreads_or(bad);
-      if (tn < n_tiles) pipe_issue<DOM>(fetch, fetch(tn), sx, S, 0, 6);
+      if (tn < n_tiles) pipe_issue<DOM>(fetch, tsm[it ^ 1], sx, cg, S, 0, 6);
       // ---- A2 species
       {
         const int d = tid / (3 * NLN), rem = tid - d * 3 * NLN, j = rem / NLN, l = rem - j * NLN;
         if (j < npair) {
           LineAddr la = line_addr(d, l);
-          ppm_line32x2(W + j * WSTAR, la, qs(d, 0, j) + l * NFC, qs(d, 1, j) + l * NFC);
+          ppm_line32x2(W + j * STAR, la, qs(d, 0, j) + l * NFC, qs(d, 1, j) + l * NFC);
         }
       }
       __syncthreads();
