@@ -484,18 +484,19 @@ __device__ __forceinline__ float rcp32(float x) {  // seed + one Newton step
   return fmaf(fmaf(-x, y, 1.0f), y, y);
 }
 
-// tau^gamma in binary32: for gamma = 5/3 and tau in (1e-18, 1e18),
-// tau * w with w^3 = tau^2 (seed exp2(2/3 log2 tau), one Halley step);
-// otherwise exp2(gamma log2 tau).  Both are evaluated and one is selected,
-// so that the code has no branch.
-__device__ __forceinline__ float tau_pow32(float tau, float gamma, bool g53) {
-  const float lt = __log2f(tau);
-  const float gen = exp2f(gamma * lt);
-  float w = exp2f((2.0f / 3.0f) * lt);
+// tau^(5/3) in binary32 for tau in (1e-18, 1e18): tau * w with w^3 = tau^2
+// (seed exp2(2/3 log2 tau), one Halley step).
+__device__ __forceinline__ float tau53_32(float tau) {
+  float w = exp2f((2.0f / 3.0f) * __log2f(tau));
   const float A = tau * tau;
   const float w3 = w * w * w;
   w = w * fmaf(2.0f, A, w3) * rcp32(fmaf(2.0f, w3, A));
-  return (g53 && tau > 1e-18f && tau < 1e18f) ? tau * w : gen;
+  return tau * w;
+}
+__device__ __forceinline__ bool tau53_ok(float tau) { return tau > 1e-18f && tau < 1e18f; }
+// tau^gamma in binary32: tau53_32 where it applies, else exp2(gamma log2 tau)
+__device__ __forceinline__ float tau_pow32(float tau, float gamma, bool g53) {
+  return (g53 && tau53_ok(tau)) ? tau53_32(tau) : exp2f(gamma * __log2f(tau));
 }
 
 // ------------------------------------------------------ step A1, mixed --
@@ -525,8 +526,10 @@ __device__ __forceinline__ bool prim_mixed_fast(const double* u, float gamf, flo
   const float ssq = fmaf(s3, s3, fmaf(s2, s2, s1 * s1));
   const float eint = fmaf(-0.5f * ssq, r, E);
   const bool kin = eint >= 0.5f * E;                          // not switched
-  const bool sw = eint <= (float)(0.5 * ETA) * E;             // switched
-  const float ptau = gm1f * tau_pow32(tau, gamf, g53);
+  // switched, with tau^(5/3) in its range (other gamma, or tau out of range,
+  // take the careful path)
+  const bool sw = eint <= (float)(0.5 * ETA) * E && g53 && tau53_ok(tau);
+  const float ptau = gm1f * tau53_32(tau);
   w[0] = rho;
   w[1] = s1 * r;
   w[2] = s2 * r;
@@ -600,45 +603,33 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // ------------------------------------------------------ step A2, mixed --
 // ppm_line64's steps in binary32 on a pair of fields, in half-slope form:
 // with dm = q - q_-1 and dp = q_+1 - q, half the monotonised central slope is
-//   h = minmod((dm + dp)/4, dm, dp)
-// (sign times the smallest magnitude if all three have one sign, else 0), and
-// the face between cells c-1 and c is (q_c-1 + q_c)/2 - (h_c - h_c-1)/3.
-// The parabola limiter in clamp form: with up = q+ - q and dn = q - q-,
-//   q- = q - minmod(dn, 2 up),  q+ = q + minmod(up, 2 dn)
-// which is CW84 eq. 1.10 exactly: where up, dn have one sign, q- = q - 2up
-// where |dn| > 2|up| (D m > D^2/6) and q+ = q + 2dn where |up| > 2|dn|
-// (D m < -D^2/6); where they do not (an extremum), both minmods are 0 and
-// the cell is flattened.
-//
-// minmod(a, b) in three instructions: min.xorsign.abs(a, b) is
-// min(|a|, |b|) with the sign bit sign(a) xor sign(b), i.e. positive exactly
-// when a and b have one sign; clamped at 0 it is |minmod(a, b)|, and
-// min.xorsign.abs(a, that) gives it a's sign.
-__device__ __forceinline__ float minxs(float a, float b) {  // min(|a|, |b|), sign(a) xor sign(b)
+//   h = sign(dm + dp) min(|dm + dp|/4, |dm|, |dp|)  if dm, dp have one sign,
+//   h = 0 otherwise,
+// and the face between cells c-1 and c is (q_c-1 + q_c)/2 - (h_c - h_c-1)/3.
+// The same-sign tests run on products (a product of two differences that
+// underflows reads as "not the same sign", which changes results by less
+// than those differences).  The parabola limiter in clamp form: with
+// up = q+ - q and dn = q - q- of one sign, q+ = q + 2dn where |up| > 2|dn|
+// and q- = q - 2up where |dn| > 2|up| (CW84 eq. 1.10); a cell with
+// up dn <= 0 is flattened.
+// min(|a|, |b|) with the sign of a (min.xorsign.abs with |b|)
+__device__ __forceinline__ float min_signed(float a, float b) {
   float r;
-  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(fabsf(b)));
   return r;
 }
-__device__ __forceinline__ float minmod(float a, float b) { return minxs(a, fmaxf(minxs(a, b), 0.0f)); }
-__device__ __forceinline__ float2 minmod2(float2 a, float2 b) {
-  return make_float2(minmod(a.x, b.x), minmod(a.y, b.y));
+__device__ __forceinline__ float hslope1(float dm, float dp, float s4, float pr) {
+  float m = fminf(fminf(fabsf(s4), fabsf(dm)), fabsf(dp));
+  return pr > 0.0f ? copysignf(m, s4) : 0.0f;
 }
-// half slope: minmod((dm + dp)/4, minmod(dm, dp)) -- if dm, dp have one sign
-// their sum has it too
 __device__ __forceinline__ float2 hslope32x2(float2 dm, float2 dp) {
-  return minmod2(mul2(add2(dm, dp), f2(0.25f)), minmod2(dm, dp));
+  float2 s4 = mul2(add2(dm, dp), f2(0.25f));
+  float2 pr = mul2(dm, dp);
+  return make_float2(hslope1(dm.x, dp.x, s4.x, pr.x), hslope1(dm.y, dp.y, s4.y, pr.y));
 }
-// Scalar forms for the single-cell reconstructions of the 26-point variant:
-// the half slope of a cell with differences dm, dp (s4 = (dm + dp)/4), and
-// the limited states from the face values lo, hi (up = hi - q, dn = q - lo,
-// uu = 2 up, du = 2 dn, lc = q - uu, hc = q + du): an unclamped face keeps
-// its value exactly.
-__device__ __forceinline__ float hslope1(float dm, float dp, float s4) {
-  return minmod(s4, minmod(dm, dp));
-}
-__device__ __forceinline__ void limit1(float q, float lo, float hi, float up, float dn, float uu, float du,
-                                       float lc, float hc, float& L, float& H) {
-  const bool ext = !(minxs(up, dn) > 0.0f);  // up, dn not of one sign (or one of them 0)
+__device__ __forceinline__ void limit1(float q, float lo, float hi, float up, float dn, float e, float uu,
+                                       float du, float lc, float hc, float& L, float& H) {
+  const bool ext = !(e > 0.0f);
   L = ext ? q : (fabsf(dn) > fabsf(uu) ? lc : lo);
   H = ext ? q : (fabsf(up) > fabsf(du) ? hc : hi);
 }
@@ -661,9 +652,24 @@ __device__ __forceinline__ void ppm_line32x2(const float2* w, const LineAddr& la
     // up of cell c-1: dq/2 - (h_c - h_c-1)/3
     float2 up = fma2(sub2(h_prev, h), f2(1.0f / 3.0f), mul2(dm, f2(0.5f)));
     if (c >= 3) {  // states of cell c-1
-      const int j = c - 4;  // cell index of c-1
-      if (j >= 0) right[j] = sub2(qm, minmod2(dn, add2(up, up)));
-      if (j + 1 <= TE) left[j + 1] = add2(qm, minmod2(up, add2(dn, dn)));
+      float2 e = mul2(up, dn);
+      float2 uu = add2(up, up), du = add2(dn, dn);
+      // the offsets after clamping: with up, dn of one sign, the smaller of
+      // |dn| and 2|up| with the sign of dn, the smaller of |up| and 2|dn| with
+      // the sign of up (one instruction each)
+      float2 a, b;
+      a.x = min_signed(dn.x, uu.x);
+      a.y = min_signed(dn.y, uu.y);
+      b.x = min_signed(up.x, du.x);
+      b.y = min_signed(up.y, du.y);
+      float2 L = sub2(qm, a), H = add2(qm, b);
+      L.x = e.x > 0.0f ? L.x : qm.x;
+      L.y = e.y > 0.0f ? L.y : qm.y;
+      H.x = e.x > 0.0f ? H.x : qm.x;
+      H.y = e.y > 0.0f ? H.y : qm.y;
+      int j = c - 4;  // cell index of c-1
+      if (j >= 0) right[j] = L;
+      if (j + 1 <= TE) left[j + 1] = H;
     }
     dn = sub2(dm, up);  // dn of cell c
     h_prev = h;

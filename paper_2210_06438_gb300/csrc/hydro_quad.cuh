@@ -74,15 +74,15 @@ __device__ __forceinline__ void ppm5_64(const double* q, double& lo, double& hi)
 // The same for binary32, in ppm_line32x2's half-slope and clamp form.
 __device__ __forceinline__ void ppm5_32(const float* q, float& lo, float& hi) {
   float d0 = q[1] - q[0], d1 = q[2] - q[1], d2 = q[3] - q[2], d3 = q[4] - q[3];
-  float h1 = hslope1(d0, d1, (d0 + d1) * 0.25f);
-  float h2 = hslope1(d1, d2, (d1 + d2) * 0.25f);
-  float h3 = hslope1(d2, d3, (d2 + d3) * 0.25f);
+  float h1 = hslope1(d0, d1, (d0 + d1) * 0.25f, d0 * d1);
+  float h2 = hslope1(d1, d2, (d1 + d2) * 0.25f, d1 * d2);
+  float h3 = hslope1(d2, d3, (d2 + d3) * 0.25f, d2 * d3);
   const float qc = q[2];
   float l = fmaf(h1 - h2, 1.0f / 3.0f, (q[1] + q[2]) * 0.5f);
   float h = fmaf(h2 - h3, 1.0f / 3.0f, (q[2] + q[3]) * 0.5f);
   float up = h - qc, dn = qc - l;
   float uu = up + up, du = dn + dn;
-  limit1(qc, l, h, up, dn, uu, du, qc - uu, qc + du, lo, hi);
+  limit1(qc, l, h, up, dn, up * dn, uu, du, qc - uu, qc + du, lo, hi);
 }
 
 template <int MODE>
