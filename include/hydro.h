@@ -36,9 +36,13 @@
  *   - Return value: HYDRO_OK (0) or a negative status below.  No entry point
  *     aborts the process or traps the GPU; device-side problems are recorded
  *     in a per-device status word read back by hydro_status().
- *   - Thread safety: calls from several host threads are serialised by a
- *     library lock; a plan or server handle may be used by one thread at a
- *     time.
+ *   - Thread safety: entry points may be called from several host threads
+ *     at once, also for different devices: each device's context has its
+ *     own lock for set-up and the status word, and the direct calls
+ *     (hydro_rhs, hydro_rhs_ex, hydro_rhs_per_subgrid) each take one of four
+ *     work-list slots with its own lock, so that up to four of them build
+ *     their work lists and wait for their slots concurrently.  A plan,
+ *     server or forest handle may be used by one thread at a time.
  */
 #ifndef HYDRO_H_
 #define HYDRO_H_

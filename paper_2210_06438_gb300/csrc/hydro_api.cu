@@ -21,7 +21,6 @@ using hydro_dev::Status;
 namespace hydro_host {
 
 thread_local std::string g_last_cuda_error = "no CUDA error";
-std::mutex g_lock;
 
 int cuda_fail(cudaError_t e, const char* what) {
   char buf[256];
@@ -31,7 +30,13 @@ int cuda_fail(cudaError_t e, const char* what) {
 }
 
 // ------------------------------------------------------------ device ctx --
+// One per device.  `mu` guards the one-time set-up, the ring cursor and the
+// status word; each ring slot has its own lock, held by the call that fills
+// the slot's work list until its launch is recorded, so that calls from
+// several host threads (or on several devices) build their work lists and
+// wait for their slots concurrently.
 struct DeviceCtx {
+  std::mutex mu;
   bool ready = false;
   int device = -1;
   int n_sm = 0;
@@ -39,9 +44,11 @@ struct DeviceCtx {
   Status* status = nullptr;  // sticky status word (device)
   // ring of work-list slots for the non-plan entry points
   static constexpr int RING = 4;
+  std::mutex slot_mu[RING];
   Tile* dev_tiles[RING] = {};
   Tile* host_tiles[RING] = {};  // pinned staging
   size_t cap[RING] = {};
+  std::vector<int64_t> first[RING];  // per-sub-grid first tile (hydro_rhs_per_subgrid)
   cudaEvent_t done[RING] = {};
   int next = 0;
 };
@@ -56,6 +63,7 @@ int ctx_get(DeviceCtx** out) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= 64) return HYDRO_EINVAL;
   DeviceCtx& c = g_ctx[dev];
+  std::lock_guard<std::mutex> g(c.mu);
   if (!c.ready) {
     c.device = dev;
     if ((e = cudaDeviceGetAttribute(&c.n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
@@ -64,12 +72,12 @@ int ctx_get(DeviceCtx** out) {
         cudaSuccess)
       return cuda_fail(e, "cudaDeviceGetAttribute(smem)");
     c.smem_optin -= 1024;  // room for the kernels' static shared memory
-    if ((e = cudaMalloc(&c.status, sizeof(Status))) != cudaSuccess) return HYDRO_ENOMEM;
+    if (!c.status && (e = cudaMalloc(&c.status, sizeof(Status))) != cudaSuccess) return HYDRO_ENOMEM;
     if ((e = cudaMemcpy(c.status, &kStatusClear, sizeof(Status), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
       return cuda_fail(e, "cudaMemcpy(status)");
     for (int i = 0; i < DeviceCtx::RING; i++)
-      if ((e = cudaEventCreateWithFlags(&c.done[i], cudaEventDisableTiming)) != cudaSuccess)
+      if (!c.done[i] && (e = cudaEventCreateWithFlags(&c.done[i], cudaEventDisableTiming)) != cudaSuccess)
         return cuda_fail(e, "cudaEventCreate");
     if ((e = kernels_init(c.smem_optin)) != cudaSuccess) return cuda_fail(e, "kernel attributes");
     c.ready = true;
@@ -134,66 +142,99 @@ void fill_tile(Tile& t, const hydro_subgrid_t& d, int ghost, int64_t out_off, in
   t.flags = (short)((multi ? 1 : 0) | (pow2 ? 2 : 0));
 }
 
-// Work list: one Tile per 8^3 tile, in descriptor order or (sort_by_cost)
-// the largest field counts first.  The fields of a sub-grid's tiles are
-// filled once and copied per tile.
-void build_tiles(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, std::vector<Tile>& tiles,
-                 std::vector<int64_t>* first_tile, bool sort_by_cost, int* Fmax, bool* any_multi) {
-  std::vector<int64_t> off(n + 1, 0);
-  int64_t n_tiles = 0;
+// Size of a batch's work list: tiles, whether any sub-grid spans several
+// tiles, the largest field count and whether all sub-grids have one.
+void count_tiles(const hydro_subgrid_t* sg, int64_t n, int64_t* n_tiles, bool* any_multi, int* Fmax,
+                 bool* uniform_F) {
+  int64_t nt = 0;
+  bool multi = false, uni = true;
+  int fm = 6;
   for (int64_t s = 0; s < n; s++) {
-    off[s + 1] = off[s] + (int64_t)sg[s].n_fields * sg[s].N * sg[s].N * sg[s].N;
-    const int64_t nt = (sg[s].N + hydro_dev::TE - 1) / hydro_dev::TE;
-    n_tiles += nt * nt * nt;
+    const int64_t e = (sg[s].N + hydro_dev::TE - 1) / hydro_dev::TE;
+    nt += e * e * e;
+    multi |= e > 1;
+    fm = std::max(fm, (int)sg[s].n_fields);
+    uni &= sg[s].n_fields == sg[0].n_fields;
   }
-  std::vector<int64_t> order;
-  if (sort_by_cost) {  // largest field count first: the longest tiles start first
+  *n_tiles = nt;
+  *any_multi = multi;
+  *Fmax = fm;
+  *uniform_F = uni;
+}
+
+// Work list: one Tile per 8^3 tile written to `tiles` (room for the count of
+// count_tiles), in descriptor order or (sort_by_cost) the largest field
+// counts first, so that the longest tiles start first.  The fields of a
+// sub-grid's tiles are filled once and copied per tile.  first_tile, if
+// given (n + 1 entries), receives each sub-grid's first tile.
+void fill_tiles(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, Tile* tiles, int64_t* first_tile,
+                bool sort_by_cost) {
+  std::vector<int64_t> off, order;
+  if (sort_by_cost) {
+    off.assign(n + 1, 0);
+    for (int64_t s = 0; s < n; s++) off[s + 1] = off[s] + (int64_t)sg[s].n_fields * sg[s].N * sg[s].N * sg[s].N;
     order.resize(n);
     for (int64_t s = 0; s < n; s++) order[s] = s;
     std::stable_sort(order.begin(), order.end(),
                      [&](int64_t a, int64_t b) { return sg[a].n_fields > sg[b].n_fields; });
   }
-  tiles.clear();
-  tiles.reserve((size_t)n_tiles);
-  if (first_tile) first_tile->assign(n + 1, 0);
-  *Fmax = 6;
-  *any_multi = false;
+  int64_t k_out = 0, run = 0;  // run: output offset in descriptor order
+  double last_dx = -1.0, inv_dx = 0.0;
+  short pow2 = 0;
   for (int64_t k = 0; k < n; k++) {
     const int64_t s = sort_by_cost ? order[k] : k;
     const hydro_subgrid_t& d = sg[s];
     const int nt = (d.N + hydro_dev::TE - 1) / hydro_dev::TE;
-    const bool multi = nt > 1;
-    *any_multi |= multi;
-    *Fmax = std::max(*Fmax, (int)d.n_fields);
-    if (first_tile) (*first_tile)[s] = (int64_t)tiles.size();
-    Tile t;
-    fill_tile(t, d, ghost, off[s], s, (int)s, 0, 0, 0, multi);
+    if (first_tile) first_tile[s] = k_out;
+    if (d.dx != last_dx) {  // 1/dx and the power-of-two test once per run of equal widths
+      last_dx = d.dx;
+      inv_dx = 1.0 / d.dx;
+      int ex2;
+      pow2 = (std::frexp(d.dx, &ex2) == 0.5 && ex2 > -120 && ex2 < 120) ? 2 : 0;
+    }
+    Tile t{d.U, sort_by_cost ? off[s] : run, s, inv_dx, (int)s, d.N, d.n_fields, d.N + 2 * ghost,
+           0, 0, 0, (short)((nt > 1 ? 1 : 0) | pow2), {0, 0}};
+    run += (int64_t)d.n_fields * d.N * d.N * d.N;
     for (int tz = 0; tz < nt; tz++)
       for (int ty = 0; ty < nt; ty++)
         for (int tx = 0; tx < nt; tx++) {
           t.ox = (short)(tx * hydro_dev::TE);
           t.oy = (short)(ty * hydro_dev::TE);
           t.oz = (short)(tz * hydro_dev::TE);
-          tiles.push_back(t);
+          tiles[k_out++] = t;
         }
   }
-  if (first_tile) (*first_tile)[n] = (int64_t)tiles.size();
+  if (first_tile) first_tile[n] = k_out;
 }
 
-// Copy a work list into the next ring slot, ordered after the slot's last
-// use.  Returns the device pointer in *dev.
-int stage_tiles(DeviceCtx* c, const std::vector<Tile>& tiles, cudaStream_t st, Tile** dev,
-                int* slot_out) {
-  int slot = c->next;
-  c->next = (c->next + 1) % DeviceCtx::RING;
+// The same into a vector (plans build their work list once).
+void build_tiles(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, std::vector<Tile>& tiles,
+                 std::vector<int64_t>* first_tile, bool sort_by_cost, int* Fmax, bool* any_multi) {
+  int64_t nt;
+  bool uni;
+  count_tiles(sg, n, &nt, any_multi, Fmax, &uni);
+  tiles.resize((size_t)nt);
+  if (first_tile) first_tile->assign(n + 1, 0);
+  fill_tiles(sg, n, ghost, tiles.data(), first_tile ? first_tile->data() : nullptr, sort_by_cost && !uni);
+}
+
+// Take the next ring slot for a work list of `need` tiles: its lock is held
+// in *lk until the caller has recorded the slot's event after its launch;
+// the slot's previous launch has finished (its host and device buffers are
+// free) and they have room for `need` tiles.
+int acquire_slot(DeviceCtx* c, int64_t need, int* slot_out, std::unique_lock<std::mutex>* lk) {
+  int slot;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    slot = c->next;
+    c->next = (c->next + 1) % DeviceCtx::RING;
+  }
+  *lk = std::unique_lock<std::mutex>(c->slot_mu[slot]);
   cudaError_t e;
-  // the previous launch that read this slot must be done before the host
-  // staging buffer and the device copy are overwritten
   if ((e = cudaEventSynchronize(c->done[slot])) != cudaSuccess)
     return cuda_fail(e, "cudaEventSynchronize(ring)");
-  size_t need = std::max<size_t>(tiles.size(), 1);
-  if (need > c->cap[slot]) {
-    size_t cap = std::max<size_t>(need, 1024);
+  if ((size_t)std::max<int64_t>(need, 1) > c->cap[slot]) {
+    size_t cap = std::max<size_t>((size_t)need, 1024);
     if (c->dev_tiles[slot]) cudaFree(c->dev_tiles[slot]);
     if (c->host_tiles[slot]) cudaFreeHost(c->host_tiles[slot]);
     c->dev_tiles[slot] = nullptr;
@@ -203,13 +244,6 @@ int stage_tiles(DeviceCtx* c, const std::vector<Tile>& tiles, cudaStream_t st, T
     if (cudaMallocHost(&c->host_tiles[slot], cap * sizeof(Tile)) != cudaSuccess) return HYDRO_ENOMEM;
     c->cap[slot] = cap;
   }
-  if (!tiles.empty()) {
-    memcpy(c->host_tiles[slot], tiles.data(), tiles.size() * sizeof(Tile));
-    if ((e = cudaMemcpyAsync(c->dev_tiles[slot], c->host_tiles[slot], tiles.size() * sizeof(Tile),
-                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
-      return cuda_fail(e, "cudaMemcpyAsync(work list)");
-  }
-  *dev = c->dev_tiles[slot];
   *slot_out = slot;
   return HYDRO_OK;
 }
@@ -257,24 +291,29 @@ int hydro_rhs_ex(const hydro_subgrid_t* sg, int64_t n, int32_t N, int32_t ghost,
   if (prec != HYDRO_FP64 && prec != HYDRO_FP32_FLUX_FP64_ACC) return HYDRO_EINVAL;
   if (n == 0) return HYDRO_OK;
   if (!out || !amax) return HYDRO_EINVAL;
-  std::lock_guard<std::mutex> g(g_lock);
   DeviceCtx* c;
   if ((rc = ctx_get(&c))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  std::vector<Tile> tiles;
+  int64_t nt;
   int Fmax;
-  bool multi;
-  build_tiles(sg, n, ghost, tiles, nullptr, true, &Fmax, &multi);
-  Tile* dt;
+  bool multi, uniF;
+  count_tiles(sg, n, &nt, &multi, &Fmax, &uniF);
+  if (nt > 0x7fffffffLL) return HYDRO_EINVAL;
   int slot;
-  if ((rc = stage_tiles(c, tiles, st, &dt, &slot))) return rc;
+  std::unique_lock<std::mutex> lk;
+  if ((rc = acquire_slot(c, nt, &slot, &lk))) return rc;
+  fill_tiles(sg, n, ghost, c->host_tiles[slot], nullptr, !uniF);  // a batch of one field count needs no sort
   cudaError_t e;
+  Tile* dt = c->dev_tiles[slot];
+  if ((e = cudaMemcpyAsync(dt, c->host_tiles[slot], (size_t)nt * sizeof(Tile), cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync(work list)");
   if (multi && (e = cudaMemsetAsync(amax, 0, n * sizeof(double), st)) != cudaSuccess)
     return cuda_fail(e, "cudaMemsetAsync(amax)");
-  LaunchCfg cfg = default_cfg(prec, Fmax, c->n_sm, c->smem_optin, (int64_t)tiles.size(),
-                              !(flags & HYDRO_F_REGISTER_LOADS), (flags & HYDRO_F_QUAD26) != 0);
-  if ((e = launch_tiles(cfg, prec, dt, (int)tiles.size(), Fmax, out, amax, c->status, gamma,
-                        !(flags & HYDRO_F_NO_STATUS), st, (flags & HYDRO_F_KNP) ? 1 : 0)) != cudaSuccess)
+  LaunchCfg cfg = default_cfg(prec, Fmax, c->n_sm, c->smem_optin, nt, !(flags & HYDRO_F_REGISTER_LOADS),
+                              (flags & HYDRO_F_QUAD26) != 0);
+  if ((e = launch_tiles(cfg, prec, dt, (int)nt, Fmax, out, amax, c->status, gamma, !(flags & HYDRO_F_NO_STATUS),
+                        st, (flags & HYDRO_F_KNP) ? 1 : 0)) != cudaSuccess)
     return cuda_fail(e, "launch");
   if ((e = cudaEventRecord(c->done[slot], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   return HYDRO_OK;
@@ -294,19 +333,25 @@ int hydro_rhs_per_subgrid(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, d
   if (n_streams < 1 || !streams) return HYDRO_EINVAL;
   if (n == 0) return HYDRO_OK;
   if (!out || !amax) return HYDRO_EINVAL;
-  std::lock_guard<std::mutex> g(g_lock);
   DeviceCtx* c;
   if ((rc = ctx_get(&c))) return rc;
-  std::vector<Tile> tiles;
-  std::vector<int64_t> first;
+  int64_t nt;
   int Fmax;
-  bool multi;
-  build_tiles(sg, n, ghost, tiles, &first, false, &Fmax, &multi);
+  bool multi, uniF;
+  count_tiles(sg, n, &nt, &multi, &Fmax, &uniF);
+  if (nt > 0x7fffffffLL) return HYDRO_EINVAL;
   cudaStream_t s0 = (cudaStream_t)streams[0];
-  Tile* dt;
   int slot;
-  if ((rc = stage_tiles(c, tiles, s0, &dt, &slot))) return rc;
+  std::unique_lock<std::mutex> lk;
+  if ((rc = acquire_slot(c, nt, &slot, &lk))) return rc;
+  std::vector<int64_t>& first = c->first[slot];
+  first.assign(n + 1, 0);
+  fill_tiles(sg, n, ghost, c->host_tiles[slot], first.data(), false);
+  Tile* dt = c->dev_tiles[slot];
   cudaError_t e;
+  if ((e = cudaMemcpyAsync(dt, c->host_tiles[slot], (size_t)nt * sizeof(Tile), cudaMemcpyHostToDevice, s0)) !=
+      cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync(work list)");
   // every stream starts after the work list is on the device
   cudaEvent_t ready = c->done[slot];
   if ((e = cudaEventRecord(ready, s0)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
@@ -315,13 +360,13 @@ int hydro_rhs_per_subgrid(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, d
       return cuda_fail(e, "cudaStreamWaitEvent");
   for (int64_t s = 0; s < n; s++) {
     cudaStream_t st = (cudaStream_t)streams[s % n_streams];
-    int nt = (int)(first[s + 1] - first[s]);
+    const int nts = (int)(first[s + 1] - first[s]);
     int F = sg[s].n_fields;
-    if (nt > 1 && (e = cudaMemsetAsync(amax + s, 0, sizeof(double), st)) != cudaSuccess)
+    if (nts > 1 && (e = cudaMemsetAsync(amax + s, 0, sizeof(double), st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemsetAsync(amax)");
-    LaunchCfg cfg = default_cfg(prec, F, c->n_sm, c->smem_optin, nt);
-    cfg.grid = nt;
-    if ((e = launch_tiles(cfg, prec, dt + first[s], nt, F, out, amax, c->status, gamma, 1, st)) !=
+    LaunchCfg cfg = default_cfg(prec, F, c->n_sm, c->smem_optin, nts);
+    cfg.grid = nts;
+    if ((e = launch_tiles(cfg, prec, dt + first[s], nts, F, out, amax, c->status, gamma, 1, st)) !=
         cudaSuccess)
       return cuda_fail(e, "launch");
   }
@@ -336,10 +381,10 @@ int hydro_rhs_per_subgrid(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, d
 }
 
 int hydro_status(void* stream, int64_t* first_bad) {
-  std::lock_guard<std::mutex> g(g_lock);
   DeviceCtx* c;
   int rc;
   if ((rc = ctx_get(&c))) return rc;
+  std::lock_guard<std::mutex> g(c->mu);
   cudaError_t e;
   if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess)
     return cuda_fail(e, "cudaStreamSynchronize");

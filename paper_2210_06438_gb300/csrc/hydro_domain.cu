@@ -108,10 +108,7 @@ int domain_launch(const double* U, const double* U0, double alpha, double beta, 
   if (rc) return rc;
   hydro_dev::Status* status;
   int n_sm, optin;
-  {
-    std::lock_guard<std::mutex> g(hydro_host::g_lock);
-    if ((rc = hydro_host::ctx_status_ptr(&status, &n_sm, &optin))) return rc;
-  }
+  if ((rc = hydro_host::ctx_status_ptr(&status, &n_sm, &optin))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int tpe = (N + hydro_dev::TE - 1) / hydro_dev::TE;
   const long long n_tiles = (long long)nb * nb * nb * tpe * tpe * tpe;

@@ -512,10 +512,7 @@ int forest_launch(hydro_forest* fo, const double* U, const double* U0, double al
   if (rc) return rc;
   hydro_dev::Status* status;
   int n_sm, optin;
-  {
-    std::lock_guard<std::mutex> g(hydro_host::g_lock);
-    if ((rc = hydro_host::ctx_status_ptr(&status, &n_sm, &optin))) return rc;
-  }
+  if ((rc = hydro_host::ctx_status_ptr(&status, &n_sm, &optin))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int N = fo->N, F = fo->F;
   const int tpe = (N + hydro_dev::TE - 1) / hydro_dev::TE;

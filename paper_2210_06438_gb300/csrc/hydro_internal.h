@@ -53,7 +53,6 @@ cudaError_t launch_tiles(const LaunchCfg& cfg, hydro_precision_t prec, const hyd
 void kernel_node(const LaunchCfg& cfg, hydro_precision_t prec, void** func);
 
 extern thread_local std::string g_last_cuda_error;
-extern std::mutex g_lock;
 int cuda_fail(cudaError_t e, const char* what);
 
 }  // namespace hydro_host

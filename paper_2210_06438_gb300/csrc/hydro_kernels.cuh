@@ -242,41 +242,63 @@ __device__ __forceinline__ double rsqrt64(double z) {
   return y * t;
 }
 
-// tau^gamma.  For gamma = 5/3: tau^(5/3) = tau * w with w^3 = tau^2, w seeded
-// in binary32 (log2/exp2) and refined by one Halley step (cubic convergence),
-// then ~1 ulp.  Other gamma, or tau outside [1e-30, 1e30]: pow().
+// binary64 <-> binary32 on the integer pipe for positive normal values well
+// inside the binary32 range: truncation to binary32 (a seed), and the exact
+// widening.
+__device__ __forceinline__ float d2f_trunc_pos(double d) {
+  return __uint_as_float(__funnelshift_l((unsigned)__double2loint(d), (unsigned)__double2hiint(d), 3) +
+                         (128u << 23));
+}
+__device__ __forceinline__ double f2d_pos(float f) {
+  const unsigned a = __float_as_uint(f);
+  return __hiloint2double((int)((a >> 3) + (896u << 20)), (int)(a << 29));
+}
+
+// tau^gamma.  For gamma = 5/3: tau^(5/3) = tau^2 z with z = tau^(-1/3), seeded
+// in binary32 (log2/exp2, relative error ~2^-22) and refined by one
+// third-order step without division: with e = 1 - tau z^3,
+// z' = z (1 - e)^(-1/3) ~ z (1 + e/3 + 2 e^2/9) (the series' next term,
+// 14 e^3/81, is below 2^-60); ~2 ulp in all.  Other gamma, or tau outside
+// [1e-30, 1e30]: pow().
 __device__ __forceinline__ double tau_pow64(double tau, double gamma, bool g53) {
   if (!g53 || !(tau > 1e-30 && tau < 1e30)) return pow(tau, gamma);
-  float tf = __double2float_rn(tau);
-  double w = (double)exp2f((2.0f / 3.0f) * __log2f(tf));
-  double A = tau * tau;
-  double w3 = w * w * w;
-  w = w * fma(2.0, A, w3) * rcp64(fma(2.0, w3, A));
-  return tau * w;
+  double z = f2d_pos(exp2f((-1.0f / 3.0f) * __log2f(d2f_trunc_pos(tau))));
+  const double z3 = z * z * z;
+  const double e = fma(-tau, z3, 1.0);
+  z = fma(z, e * fma(e, 2.0 / 9.0, 1.0 / 3.0), z);
+  return tau * (tau * z);
 }
 
 // ---------------------------------------------------- step A1, binary64 --
 // Conserved -> primitive (rho, v, p, phi = tau/rho; the species X_k =
 // rho_k/rho are formed by the caller with the returned r = 1/rho).
 // The dual-energy branch is decided on e_int = E - |s|^2/(2 rho) against
-// eta*E.  A fast estimate (reciprocal, fused operations) decides it when it
-// is far from the threshold; inside [eta/2, 20 eta]*E the quantities are
-// recomputed with correctly rounded operations in the reference order, so the
-// branch is taken exactly as the reference definition takes it.
+// eta*E.  Far from the threshold a fast estimate (reciprocal, fused
+// operations) decides it from the binary exponents alone (integer pipe):
+// with k = expo(e_int) - expo(E), both positive and normal,
+// 2^(k-1) < e_int/E < 2^(k+1), so k <= -12 means e_int < 2^-11 E < eta E
+// (switched) and k >= -4 means e_int > 2^-5 E > eta E (not switched).  In
+// between, and for values that are not positive and normal, e_int and the
+// branch are recomputed with correctly rounded operations in the reference
+// order, so the branch is taken exactly as the reference definition takes it.
 __device__ __forceinline__ bool prim64(const double* u, double gamma, bool g53, double* w,
                                        double& r) {
   double rho = u[0], E = u[4], tau = u[5];
   r = rcp64(rho);
   double ssq = fma(u[3], u[3], fma(u[2], u[2], u[1] * u[1]));
   double eint = fma(-dhalf(ssq), r, E);
-  double thr = ETA * E;
+  const int xe = hiw(eint) >> 20, xE = hiw(E) >> 20;  // biased exponents; negative values give < 0
+  const bool normal = xe > 0 && xe < 0x7ff && xE > 0 && xE < 0x7ff;
+  const int k = xe - xE;
   double e;
-  if (dgt(eint, dhalf(thr)) && dgt(20.0 * thr, eint)) {  // near the switch: exact path
+  if (normal && k <= -12) {
+    e = tau_pow64(tau, gamma, g53);
+  } else if (normal && k >= -4) {
+    e = eint;
+  } else {  // near the switch: the reference order
     double ss = __dadd_rn(__dadd_rn(__dmul_rn(u[1], u[1]), __dmul_rn(u[2], u[2])), __dmul_rn(u[3], u[3]));
     double ex = __dsub_rn(E, __ddiv_rn(__dmul_rn(0.5, ss), rho));
     e = ex < __dmul_rn(ETA, E) ? tau_pow64(tau, gamma, g53) : ex;
-  } else {
-    e = dgt(thr, eint) ? tau_pow64(tau, gamma, g53) : eint;
   }
   double p = (gamma - 1.0) * e;
   w[0] = rho;

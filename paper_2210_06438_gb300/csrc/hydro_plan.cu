@@ -150,7 +150,6 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
   if (rc) return rc;
   if (n < 1) return HYDRO_EINVAL;
   if (prec != HYDRO_FP64 && prec != HYDRO_FP32_FLUX_FP64_ACC) return HYDRO_EINVAL;
-  std::lock_guard<std::mutex> g(g_lock);
   Status* status;
   int n_sm, smem_optin;
   if ((rc = ctx_status_ptr(&status, &n_sm, &smem_optin))) return rc;
@@ -269,7 +268,6 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
 
 int hydro_plan_execute(hydro_plan_t* p, double* out, double* amax, void* stream) {
   if (!p || !out || !amax) return HYDRO_EINVAL;
-  std::lock_guard<std::mutex> g(g_lock);
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   bool changed = out != p->a_out || amax != p->a_amax;
@@ -304,7 +302,6 @@ int hydro_plan_info(const hydro_plan_t* p, hydro_plan_info_t* info) {
 
 int hydro_plan_destroy(hydro_plan_t* p) {
   if (!p) return HYDRO_EINVAL;
-  std::lock_guard<std::mutex> g(g_lock);
   plan_free(p);
   return HYDRO_OK;
 }

@@ -277,7 +277,6 @@ int hydro_server_create(const hydro_server_cfg_t* cfg, hydro_server_t** out) {
   memset(&S->st, 0, sizeof S->st);
   S->slots.resize(cfg->n_streams);
   if (cfg->dry_run_ns <= 0) {
-    std::lock_guard<std::mutex> g(g_lock);
     int rc = ctx_status_ptr(&S->status, &S->n_sm, &S->smem_optin);
     if (rc) {
       delete S;
