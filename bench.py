@@ -1320,9 +1320,10 @@ def run_profile(args):
     if args.profile.startswith("forest"):
         return run_profile_forest(args)
     batch = polytrope_batch(n=args.domain)
-    prec = hydro.FP64 if args.profile == "fp64" else hydro.FP32_FLUX_FP64_ACC
+    prec = hydro.FP64 if args.profile.startswith("fp64") else hydro.FP32_FLUX_FP64_ACC
+    flags = hydro.PLAN_QUAD26 if args.profile.endswith("quad26") else 0
     plan = hydro.Plan(batch.desc, ghost=3, gamma=GAMMA, prec=prec, autotune=True, stream=stream,
-                      n=batch.n)
+                      n=batch.n, flags=flags)
     info = plan.info()
     out = torch.empty(batch.out_doubles, dtype=torch.float64, device="cuda")
     amax = torch.empty(batch.n, dtype=torch.float64, device="cuda")
@@ -1356,8 +1357,8 @@ def main():
                     help="skip the smaller workloads (one sub-grid, 512 sub-grids, the uneven batch)")
     ap.add_argument("--rate", type=float, default=20000.0, help="serving arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
-    ap.add_argument("--profile", choices=["fp64", "mixed", "forest64", "forestmx", "forest64_quad26",
-                                          "forestmx_quad26"], default=None,
+    ap.add_argument("--profile", choices=["fp64", "mixed", "fp64_quad26", "mixed_quad26", "forest64",
+                                          "forestmx", "forest64_quad26", "forestmx_quad26"], default=None,
                     help="short run of one form for ncu (no JSON bench line)")
     args = ap.parse_args()
     if args.profile:

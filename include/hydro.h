@@ -133,6 +133,15 @@ int hydro_rhs_per_subgrid(const hydro_subgrid_t* subgrids, int64_t n_subgrids, i
                           double gamma, double* out_dUdt, double* out_amax,
                           hydro_precision_t prec, void* const* streams, int32_t n_streams);
 
+/* hydro_rhs_per_subgrid with flags: HYDRO_F_KNP, HYDRO_F_QUAD26 (each launch
+ * then runs the 26-point kernel), HYDRO_F_REGISTER_LOADS, HYDRO_F_NO_STATUS,
+ * as for hydro_rhs_ex; the results equal hydro_rhs_ex's with the same flags
+ * bit for bit.  HYDRO_EINVAL for other flag bits. */
+int hydro_rhs_per_subgrid_ex(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t ghost,
+                             double gamma, double* out_dUdt, double* out_amax,
+                             hydro_precision_t prec, void* const* streams, int32_t n_streams,
+                             uint32_t flags);
+
 /* ---------------------------------------------------------------------------
  * Plans: a fixed batch (the descriptors, hence the input pointers, are bound
  * at creation) whose work list is built, sorted and uploaded once, whose
@@ -222,7 +231,7 @@ typedef struct {
   int32_t per_task;       /* 1: never aggregate; one launch per task (the comparison form) */
   int64_t dry_run_ns;     /* > 0: no GPU work at all; a launch "completes" this many ns after
                              it starts (host-only testing of admission, order and timeouts) */
-  uint32_t flags;         /* HYDRO_F_KNP or 0 */
+  uint32_t flags;         /* HYDRO_F_KNP, HYDRO_F_QUAD26 (the 26-point variant), or 0 */
 } hydro_server_cfg_t;
 
 typedef struct {

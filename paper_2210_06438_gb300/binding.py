@@ -129,6 +129,8 @@ def load(build_if_missing: bool = False):
         "hydro_rhs_ex": (ctypes.c_int, [SG, i64, i32, i32, i32, dbl, P, P, ctypes.c_int, P, u32]),
         "hydro_rhs_per_subgrid": (ctypes.c_int, [SG, i64, i32, dbl, P, P, ctypes.c_int,
                                                  ctypes.POINTER(P), i32]),
+        "hydro_rhs_per_subgrid_ex": (ctypes.c_int, [SG, i64, i32, dbl, P, P, ctypes.c_int,
+                                                 ctypes.POINTER(P), i32, u32]),
         "hydro_plan_create": (ctypes.c_int, [SG, i64, i32, dbl, ctypes.c_int, u32, P,
                                              ctypes.POINTER(P)]),
         "hydro_plan_execute": (ctypes.c_int, [P, P, P, P]),
@@ -351,13 +353,13 @@ def courant(amax, n_rows, row_stride, n, clock, cfl, t_end, dx=None, dx_uniform=
 
 
 def rhs_per_subgrid(desc, out, amax, streams: Iterable, ghost=3, gamma=5.0 / 3.0, prec=FP64,
-                    n=None):
-    """The per-sub-grid launch form (hydro_rhs_per_subgrid) over a stream pool."""
+                    n=None, flags=0):
+    """The per-sub-grid launch form (hydro_rhs_per_subgrid_ex) over a stream pool."""
     n = len(desc) if n is None else n
     st = [_stream(s) for s in streams]
     arr = (ctypes.c_void_p * len(st))(*st)
-    _check(load().hydro_rhs_per_subgrid(desc, n, ghost, float(gamma), _ptr(out), _ptr(amax),
-                                        int(prec), arr, len(st)), "hydro_rhs_per_subgrid")
+    _check(load().hydro_rhs_per_subgrid_ex(desc, n, ghost, float(gamma), _ptr(out), _ptr(amax),
+                                           int(prec), arr, len(st), int(flags)), "hydro_rhs_per_subgrid_ex")
 
 
 def status(stream=None):
@@ -409,10 +411,10 @@ class Server:
 
     def __init__(self, budget_bytes=40 << 30, max_batch=4096, n_streams=4, ghost=3,
                  queue_capacity=1 << 20, gamma=5.0 / 3.0, prec=FP64, per_task=False,
-                 dry_run_ns=0, knp=False):
+                 dry_run_ns=0, knp=False, flags=0):
         cfg = ServerCfg(int(budget_bytes), int(max_batch), int(n_streams), int(ghost),
                         int(queue_capacity), float(gamma), int(prec), 1 if per_task else 0,
-                        int(dry_run_ns), F_KNP if knp else 0)
+                        int(dry_run_ns), int(flags) | (F_KNP if knp else 0))
         h = ctypes.c_void_p()
         _check(load().hydro_server_create(ctypes.byref(cfg), ctypes.byref(h)), "hydro_server_create")
         self._h = h

@@ -327,6 +327,14 @@ int hydro_rhs(const hydro_subgrid_t* sg, int64_t n, int32_t N, int32_t ghost, in
 int hydro_rhs_per_subgrid(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, double gamma,
                           double* out, double* amax, hydro_precision_t prec, void* const* streams,
                           int32_t n_streams) {
+  return hydro_rhs_per_subgrid_ex(sg, n, ghost, gamma, out, amax, prec, streams, n_streams, 0u);
+}
+
+int hydro_rhs_per_subgrid_ex(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, double gamma,
+                             double* out, double* amax, hydro_precision_t prec, void* const* streams,
+                             int32_t n_streams, uint32_t flags) {
+  if (flags & ~(uint32_t)(HYDRO_F_NO_STATUS | HYDRO_F_KNP | HYDRO_F_QUAD26 | HYDRO_F_REGISTER_LOADS))
+    return HYDRO_EINVAL;
   int rc = validate(sg, n, 0, ghost, 0, gamma);
   if (rc) return rc;
   if (prec != HYDRO_FP64 && prec != HYDRO_FP32_FLUX_FP64_ACC) return HYDRO_EINVAL;
@@ -364,9 +372,11 @@ int hydro_rhs_per_subgrid(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, d
     int F = sg[s].n_fields;
     if (nts > 1 && (e = cudaMemsetAsync(amax + s, 0, sizeof(double), st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemsetAsync(amax)");
-    LaunchCfg cfg = default_cfg(prec, F, c->n_sm, c->smem_optin, nts);
+    LaunchCfg cfg = default_cfg(prec, F, c->n_sm, c->smem_optin, nts, !(flags & HYDRO_F_REGISTER_LOADS),
+                                (flags & HYDRO_F_QUAD26) != 0);
     cfg.grid = nts;
-    if ((e = launch_tiles(cfg, prec, dt + first[s], nts, F, out, amax, c->status, gamma, 1, st)) !=
+    if ((e = launch_tiles(cfg, prec, dt + first[s], nts, F, out, amax, c->status, gamma,
+                          !(flags & HYDRO_F_NO_STATUS), st, (flags & HYDRO_F_KNP) ? 1 : 0)) !=
         cudaSuccess)
       return cuda_fail(e, "launch");
   }

@@ -167,7 +167,8 @@ static int launch_batch(hydro_server* S, Slot& s, const std::vector<int64_t>& id
   if ((e = cudaMemcpyAsync(s.dev_tiles, s.host_tiles, k * sizeof(Tile), cudaMemcpyHostToDevice,
                            s.stream)) != cudaSuccess)
     return cuda_fail(e, "cudaMemcpyAsync(work list)");
-  LaunchCfg c = default_cfg(S->cfg.prec, Fmax, S->n_sm, S->smem_optin, (int64_t)k);
+  LaunchCfg c = default_cfg(S->cfg.prec, Fmax, S->n_sm, S->smem_optin, (int64_t)k, true,
+                            (S->cfg.flags & HYDRO_F_QUAD26) != 0);
   if ((e = launch_tiles(c, S->cfg.prec, s.dev_tiles, (int)k, Fmax, obase, abase, S->status,
                         S->cfg.gamma, 1, s.stream, (S->cfg.flags & HYDRO_F_KNP) ? 1 : 0)) != cudaSuccess)
     return cuda_fail(e, "launch");
@@ -270,7 +271,8 @@ int hydro_server_create(const hydro_server_cfg_t* cfg, hydro_server_t** out) {
   *out = nullptr;
   if (cfg->budget_bytes <= 0 || cfg->max_batch < 1 || cfg->n_streams < 1 || cfg->n_streams > 1024 ||
       cfg->ghost < 3 || cfg->queue_capacity < 1 || !(cfg->gamma > 1.0) ||
-      (cfg->prec != HYDRO_FP64 && cfg->prec != HYDRO_FP32_FLUX_FP64_ACC))
+      (cfg->prec != HYDRO_FP64 && cfg->prec != HYDRO_FP32_FLUX_FP64_ACC) ||
+      (cfg->flags & ~(uint32_t)(HYDRO_F_KNP | HYDRO_F_QUAD26)))
     return HYDRO_EINVAL;
   hydro_server* S = new hydro_server();
   S->cfg = *cfg;

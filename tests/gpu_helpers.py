@@ -60,6 +60,8 @@ def run_gpu(dev_blocks, dxs, prec=hydro.FP64, ghost=3, gamma=G53, form="rhs", st
     if form == "rhs":
         hydro.rhs(desc, out, amax, ghost=ghost, gamma=gamma, prec=prec, n=n, flags=flags)
     elif form == "per_subgrid":
+        for st in streams or []:  # side streams do not order themselves after the fills above
+            st.wait_stream(torch.cuda.current_stream())
         hydro.rhs_per_subgrid(desc, out, amax, streams or [None], ghost=ghost, gamma=gamma,
                               prec=prec, n=n)
     elif form == "plan":

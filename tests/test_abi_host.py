@@ -102,3 +102,12 @@ def test_fp64_probe_checks_arguments_before_the_device(lib):
     assert lib.hydro_probe_fp64(65, 100, None, ctypes.byref(n)) == hydro.HYDRO_EINVAL
     assert lib.hydro_probe_fp64(4, 0, None, ctypes.byref(n)) == hydro.HYDRO_EINVAL
     assert lib.hydro_probe_fp64(4, 100, None, None) == hydro.HYDRO_EINVAL
+
+
+def test_per_subgrid_and_server_flags_are_checked(lib):
+    """Unknown flag bits are refused before any device work."""
+    d = hydro.descriptors([(8, 0.1, 8, 6)])
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.hydro_rhs_per_subgrid_ex(d, 1, 3, 5.0 / 3.0, 64, 64, 0, arr, 1, 1 << 10) == hydro.HYDRO_EINVAL
+    with pytest.raises(hydro.HydroError):
+        hydro.Server(dry_run_ns=1000, flags=hydro.F_REGISTER_LOADS)

@@ -44,9 +44,10 @@ def test_direct_calls_from_several_threads(prec):
             _, n, N, F = specs[i]
             outs = []
             for rep in range(12):
-                out = torch.full((hydro.output_doubles(desc, n),), float("nan"), dtype=torch.float64,
-                                 device="cuda")
-                am = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+                with torch.cuda.stream(streams[i]):  # the fills run on the call's own stream
+                    out = torch.full((hydro.output_doubles(desc, n),), float("nan"), dtype=torch.float64,
+                                     device="cuda")
+                    am = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
                 if rep % 3 == 2:
                     hydro.rhs_per_subgrid(desc, out, am, [streams[i]], prec=prec, n=n)
                 else:

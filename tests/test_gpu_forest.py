@@ -175,6 +175,7 @@ def test_forest_rk3_step_in_a_cuda_graph():
     W1, W2, W3 = torch.empty_like(U), torch.empty_like(U), torch.empty_like(U)
     am = torch.empty((3, len(lv)), dtype=torch.float64, device="cuda")
     st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())  # after the copies above
 
     def step(out):
         fo.stage(U, U, 0.0, 1.0, 1e-4, dx0, W1, am[0], stream=st)

@@ -3,6 +3,7 @@ against the oracle's QUAD26 mode, in both precision forms, with partial
 tiles, the one-sided flux, plans and conservation."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 import paper_2210_06438_gb300 as hydro
@@ -80,3 +81,26 @@ def test_periodic_conservation():
         tot = np.sum([o.sum(axis=(1, 2, 3)) for o in got], axis=0)
         mag = np.sum([np.abs(o).sum(axis=(1, 2, 3)) for o in got], axis=0)
         assert np.all(np.abs(tot) <= 1e-13 * mag)
+
+
+@pytest.mark.parametrize("flags", [hydro.F_QUAD26, hydro.F_QUAD26 | hydro.F_KNP, hydro.F_KNP])
+@pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
+def test_per_subgrid_form_with_flags_gives_the_aggregated_bits(prec, flags):
+    """hydro_rhs_per_subgrid_ex: one launch per sub-grid over a stream pool
+    runs the flux variant of its flags with the aggregated form's bits."""
+    blocks = [torch.from_numpy(synth.iid_block(synth.rng_for(808, s), N, F)).cuda()
+              for s, (N, F) in enumerate([(8, 11), (16, 6), (5, 8), (8, 7), (12, 11)])]
+    desc = hydro.descriptors([(b, 0.2, b.shape[1] - 6, b.shape[0]) for b in blocks])
+    n = len(blocks)
+    nout = hydro.output_doubles(desc, n)
+    ref = torch.empty(nout, dtype=torch.float64, device="cuda")
+    ram = torch.empty(n, dtype=torch.float64, device="cuda")
+    hydro.rhs(desc, ref, ram, prec=prec, n=n, flags=flags)
+    out = torch.full((nout,), float("nan"), dtype=torch.float64, device="cuda")
+    am = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    pool = [torch.cuda.Stream() for _ in range(3)]
+    for st in pool:  # the pool's streams do not order themselves after the fills above
+        st.wait_stream(torch.cuda.current_stream())
+    hydro.rhs_per_subgrid(desc, out, am, pool, prec=prec, n=n, flags=flags)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref) and torch.equal(am, ram)

@@ -25,8 +25,9 @@ def _pool(n=24, seed=31):
     return blocks, meta
 
 
+@pytest.mark.parametrize("flags", [0, hydro.F_QUAD26, hydro.F_KNP])
 @pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
-def test_results_are_identical_alone_and_in_the_mix(prec):
+def test_results_are_identical_alone_and_in_the_mix(prec, flags):
     blocks, meta = _pool()
     rng = np.random.default_rng(3)
     tasks = []
@@ -38,7 +39,7 @@ def test_results_are_identical_alone_and_in_the_mix(prec):
         nout = hydro.output_doubles(desc, k)
         tasks.append((desc, k, torch.full((nout,), float("nan"), dtype=torch.float64, device="cuda"),
                       torch.full((k,), float("nan"), dtype=torch.float64, device="cuda")))
-    srv = hydro.Server(n_streams=3, max_batch=12, prec=prec)
+    srv = hydro.Server(n_streams=3, max_batch=12, prec=prec, flags=flags)
     tickets = []
     for i, (desc, k, out, am) in enumerate(tasks):
         rc, t = srv.submit(desc, out, am, n=k)
@@ -56,7 +57,7 @@ def test_results_are_identical_alone_and_in_the_mix(prec):
     for desc, k, out, am in tasks:
         ref = torch.empty_like(out)
         ram = torch.empty_like(am)
-        hydro.rhs(desc, ref, ram, prec=prec, n=k)
+        hydro.rhs(desc, ref, ram, prec=prec, n=k, flags=flags)
         torch.cuda.synchronize()
         assert torch.equal(out, ref) and torch.equal(am, ram)
 
