@@ -337,6 +337,11 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
               if (f - 6 >= nsp) break;
               const double* base = tile.U + f * plane;
               R ql[5], qr[5], lo, hi;
+              // all ten loads first; the mixed form converts them on the
+              // integer pipe and takes the conversion instruction (a call
+              // the loads could not be scheduled across) only for the rare
+              // stencil with a value outside the fast path's range
+              double ul[5], ur[5];
 #pragma unroll
               for (int m = 0; m < 5; m++) {
                 int ol, orr;
@@ -355,14 +360,33 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
                   ol = gl0 + (m - 2) * gsl;
                   orr = gr0 + (m - 2) * gsr;
                 }
-                const double ul = __ldg(base + ol), ur = __ldg(base + orr);
-                const R rl = RR[il + (m - 2) * sl], rr = RR[ir + (m - 2) * sr];
-                if constexpr (MODE == 0) {
-                  ql[m] = ul * rl;
-                  qr[m] = ur * rr;
-                } else {
-                  ql[m] = d2f_int(ul) * rl;
-                  qr[m] = d2f_int(ur) * rr;
+                ul[m] = __ldg(base + ol);
+                ur[m] = __ldg(base + orr);
+              }
+              if constexpr (MODE == 0) {
+#pragma unroll
+                for (int m = 0; m < 5; m++) {
+                  ql[m] = ul[m] * RR[il + (m - 2) * sl];
+                  qr[m] = ur[m] * RR[ir + (m - 2) * sr];
+                }
+              } else {
+                unsigned oor = 0;  // species densities: positive (zero and below take the slow path)
+#pragma unroll
+                for (int m = 0; m < 5; m++) {
+                  ql[m] = d2f_fast_pos(ul[m], oor);
+                  qr[m] = d2f_fast_pos(ur[m], oor);
+                }
+                if (oor >= D2F_OOR) {
+#pragma unroll
+                  for (int m = 0; m < 5; m++) {
+                    ql[m] = d2f_slow(ul[m]);
+                    qr[m] = d2f_slow(ur[m]);
+                  }
+                }
+#pragma unroll
+                for (int m = 0; m < 5; m++) {
+                  ql[m] *= RR[il + (m - 2) * sl];
+                  qr[m] *= RR[ir + (m - 2) * sr];
                 }
               }
               if constexpr (MODE == 0) {
