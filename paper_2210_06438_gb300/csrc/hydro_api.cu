@@ -14,9 +14,21 @@
 #include "hydro.h"
 #include "hydro_internal.h"
 #include "hydro_kernels.cuh"
+#include "hydro_uniform.cuh"
 
 using hydro_dev::Tile;
 using hydro_dev::Status;
+
+namespace hydro_dev {
+
+// The work list of a uniform batch, built on the device from its sub-grid
+// descriptors (24 bytes each instead of 64 per tile from the host).
+__global__ void __launch_bounds__(256) expand_uniform_kernel(UniformDesc u, int n_tiles, Tile* __restrict__ tiles) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_tiles) tiles[t] = u(t);
+}
+
+}  // namespace hydro_dev
 
 namespace hydro_host {
 
@@ -143,11 +155,12 @@ void fill_tile(Tile& t, const hydro_subgrid_t& d, int ghost, int64_t out_off, in
 }
 
 // Size of a batch's work list: tiles, whether any sub-grid spans several
-// tiles, the largest field count and whether all sub-grids have one.
+// tiles, the largest field count, whether all sub-grids have one, and
+// (uniform_N, if given) whether they all have one edge N.
 void count_tiles(const hydro_subgrid_t* sg, int64_t n, int64_t* n_tiles, bool* any_multi, int* Fmax,
-                 bool* uniform_F) {
+                 bool* uniform_F, bool* uniform_N = nullptr) {
   int64_t nt = 0;
-  bool multi = false, uni = true;
+  bool multi = false, uni = true, uniN = true;
   int fm = 6;
   for (int64_t s = 0; s < n; s++) {
     const int64_t e = (sg[s].N + hydro_dev::TE - 1) / hydro_dev::TE;
@@ -155,11 +168,13 @@ void count_tiles(const hydro_subgrid_t* sg, int64_t n, int64_t* n_tiles, bool* a
     multi |= e > 1;
     fm = std::max(fm, (int)sg[s].n_fields);
     uni &= sg[s].n_fields == sg[0].n_fields;
+    uniN &= sg[s].N == sg[0].N;
   }
   *n_tiles = nt;
   *any_multi = multi;
   *Fmax = fm;
   *uniform_F = uni;
+  if (uniform_N) *uniform_N = uniN;
 }
 
 // Work list: one Tile per 8^3 tile written to `tiles` (room for the count of
@@ -296,18 +311,36 @@ int hydro_rhs_ex(const hydro_subgrid_t* sg, int64_t n, int32_t N, int32_t ghost,
   cudaStream_t st = (cudaStream_t)stream;
   int64_t nt;
   int Fmax;
-  bool multi, uniF;
-  count_tiles(sg, n, &nt, &multi, &Fmax, &uniF);
+  bool multi, uniF, uniN;
+  count_tiles(sg, n, &nt, &multi, &Fmax, &uniF, &uniN);
   if (nt > 0x7fffffffLL) return HYDRO_EINVAL;
+  // A batch of one N and one field count sends its descriptors and builds
+  // the work list on the device (descriptor order, as the host would);
+  // others send the work list, sorted by cost when the field counts differ.
+  const bool uniform = uniN && uniF;
+  const int64_t desc_slots = uniform ? (n * (int64_t)sizeof(hydro_subgrid_t) + sizeof(Tile) - 1) / sizeof(Tile) : 0;
   int slot;
   std::unique_lock<std::mutex> lk;
-  if ((rc = acquire_slot(c, nt, &slot, &lk))) return rc;
-  fill_tiles(sg, n, ghost, c->host_tiles[slot], nullptr, !uniF);  // a batch of one field count needs no sort
+  if ((rc = acquire_slot(c, nt + desc_slots, &slot, &lk))) return rc;
   cudaError_t e;
   Tile* dt = c->dev_tiles[slot];
-  if ((e = cudaMemcpyAsync(dt, c->host_tiles[slot], (size_t)nt * sizeof(Tile), cudaMemcpyHostToDevice, st)) !=
-      cudaSuccess)
-    return cuda_fail(e, "cudaMemcpyAsync(work list)");
+  if (uniform) {
+    // descriptors behind the work list in the slot's device buffer
+    hydro_subgrid_t* dd = reinterpret_cast<hydro_subgrid_t*>(dt + nt);
+    memcpy(c->host_tiles[slot], sg, (size_t)n * sizeof(hydro_subgrid_t));
+    if ((e = cudaMemcpyAsync(dd, c->host_tiles[slot], (size_t)n * sizeof(hydro_subgrid_t), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync(descriptors)");
+    const int N0 = sg[0].N, tpe = (N0 + hydro_dev::TE - 1) / hydro_dev::TE;
+    hydro_dev::UniformDesc u{dd, N0, sg[0].n_fields, N0 + 2 * ghost, tpe};
+    hydro_dev::expand_uniform_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(u, (int)nt, dt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "work-list launch");
+  } else {
+    fill_tiles(sg, n, ghost, c->host_tiles[slot], nullptr, !uniF);  // a batch of one field count needs no sort
+    if ((e = cudaMemcpyAsync(dt, c->host_tiles[slot], (size_t)nt * sizeof(Tile), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync(work list)");
+  }
   if (multi && (e = cudaMemsetAsync(amax, 0, n * sizeof(double), st)) != cudaSuccess)
     return cuda_fail(e, "cudaMemsetAsync(amax)");
   LaunchCfg cfg = default_cfg(prec, Fmax, c->n_sm, c->smem_optin, nt, !(flags & HYDRO_F_REGISTER_LOADS),

@@ -19,6 +19,7 @@
 #include "hydro.h"
 #include "hydro_internal.h"
 #include "hydro_kernels.cuh"
+#include "hydro_uniform.cuh"
 
 namespace hydro_dev {
 
@@ -27,38 +28,6 @@ namespace hydro_dev {
 // nothing in it has to start at zero.
 constexpr size_t kNoallocBytes = (size_t)HYDRO_NOALLOC_MAX_SUBGRIDS * sizeof(hydro_subgrid_t);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
-
-// Tile t of a uniform batch read from the descriptor table: sub-grid t / tps,
-// tile t % tps of it in x-fastest order.  Fills the same fields, with the same
-// arithmetic, as the host builds for hydro_rhs_ex.
-struct UniformDesc {
-  const hydro_subgrid_t* __restrict__ desc;
-  int N, F, G, tpe;  // tpe: tiles per edge
-  __device__ __forceinline__ Tile operator()(int t) const {
-    const int tps = tpe * tpe * tpe;
-    const int s = t / tps, k = t - s * tps;
-    const hydro_subgrid_t d = desc[s];
-    Tile tile;
-    tile.U = d.U;
-    tile.out_off = (long long)s * F * N * N * N;
-    tile.amax_off = s;
-    tile.inv_dx = 1.0 / d.dx;
-    tile.sub = s;
-    tile.N = N;
-    tile.F = F;
-    tile.G = G;
-    tile.ox = (short)((k % tpe) * TE);
-    tile.oy = (short)(((k / tpe) % tpe) * TE);
-    tile.oz = (short)((k / (tpe * tpe)) * TE);
-    // dx an exact power of two (frexp mantissa 1/2, exponent within +-120)
-    long long b = __double_as_longlong(d.dx);
-    int e2 = (int)((b >> 52) & 0x7ff) - 1022;
-    bool pow2 = (b & 0x000fffffffffffffLL) == 0 && ((b >> 52) & 0x7ff) != 0 && e2 > -120 && e2 < 120;
-    tile.flags = (short)((tps > 1 ? 1 : 0) | (pow2 ? 2 : 0));
-    tile.pad[0] = tile.pad[1] = 0;
-    return tile;
-  }
-};
 
 template <int MODE, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)

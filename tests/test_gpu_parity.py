@@ -217,6 +217,30 @@ def test_uniform_state_gives_exact_zero_on_gpu():
         assert np.all(got[0] == 0) and np.all(got[1] == 0)
 
 
+@pytest.mark.parametrize("N,F", [(8, 11), (12, 9), (16, 6), (5, 7)])
+@pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
+def test_uniform_batch_work_list_built_on_the_device(N, F, prec):
+    """hydro_rhs_ex builds the work list of a batch of one N and one field
+    count on the device from the descriptors; a plan builds it on the host.
+    Both lists must describe the same tiles: the results agree bit for bit
+    (widths that are powers of two and others, partial and several tiles)."""
+    n = 10
+    blocks = [synth.iid_block(synth.rng_for(515, s), N, F) for s in range(n)]
+    dxs = [1.0 / 64, 0.3, 2.0 ** -9, 1.0 / 3.0, 0.125] * 2
+    dev = gh.to_dev(blocks)
+    direct, dam = gh.run_gpu(dev, dxs, prec=prec)
+    plan, pam = gh.run_gpu(dev, dxs, prec=prec, form="plan")
+    for s in range(n):
+        assert np.array_equal(direct[s], plan[s]), s
+    assert np.array_equal(dam, pam)
+    want, want_am, fl = gh.oracle_ref(blocks, dxs, mode=0 if prec == hydro.FP64 else 1)
+    assert not fl.any()
+    if prec == hydro.FP64:
+        gh.check_fp64(direct, want, dam, want_am, blocks, dxs)
+    else:
+        gh.check_mixed(direct, want, dam, want_am, blocks, dxs)
+
+
 @pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
 def test_alone_in_batch_per_subgrid_and_plan_are_bitwise_equal(prec):
     leaves = synth.uneven_octree(n_subgrids=24)
