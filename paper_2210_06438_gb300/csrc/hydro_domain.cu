@@ -34,8 +34,8 @@ struct Shape {
 // 576 threads, mixed the pipelined kernel), then the 26-point kernels
 const Shape kShape[4] = {{576, 1, 64},
                          {hydro_host::kPipeThreads, 1, 64},
-                         {hydro_host::kQuadThreads, 1, 64},
-                         {hydro_host::kQuadThreads, 1, 64}};
+                         {hydro_dev::QuadShape<0>::NT, 1, 64},
+                         {hydro_dev::QuadShape<1>::NT, 1, 64}};
 const int kKind[4] = {hydro_host::kKindTiles, hydro_host::kKindPipe, hydro_host::kKindQuad,
                       hydro_host::kKindQuad};
 

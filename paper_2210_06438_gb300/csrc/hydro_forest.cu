@@ -269,8 +269,8 @@ namespace {
 // 2 mixed, register loads, 256 threads (HYDRO_F_REGISTER_LOADS); 3 and 4
 // the 26-point variant, binary64 and mixed.
 constexpr int kLch = 64, kNumKernels = 5;
-constexpr int kThreads[kNumKernels] = {576, hydro_host::kPipeThreads, 256, hydro_host::kQuadThreads,
-                                       hydro_host::kQuadThreads};
+constexpr int kThreads[kNumKernels] = {576, hydro_host::kPipeThreads, 256, hydro_dev::QuadShape<0>::NT,
+                                       hydro_dev::QuadShape<1>::NT};
 constexpr int kKinds[kNumKernels] = {hydro_host::kKindTiles, hydro_host::kKindPipe, hydro_host::kKindTiles,
                                      hydro_host::kKindQuad, hydro_host::kKindQuad};
 

@@ -20,7 +20,6 @@ namespace hydro_host {
 // kernel, the 26-point quadrature kernels.
 constexpr int kKindTiles = 0, kKindPipe = 1, kKindQuad = 2;
 constexpr int kPipeThreads = 576;  // threads of the pipelined mixed kernel
-constexpr int kQuadThreads = 192;  // threads of the 26-point quadrature kernels
 
 // Launch shape of the tile kernel.
 struct LaunchCfg {
@@ -38,6 +37,8 @@ struct LaunchCfg {
 cudaError_t kernels_init(int smem_optin);
 int smem_bytes(hydro_precision_t prec, int Fmax, int lch, int kind = kKindTiles);
 int occupancy(hydro_precision_t prec, const LaunchCfg& c);  // c.smem must be set
+// threads per CTA of the 26-point kernel of a precision
+int quad_threads(hydro_precision_t prec);
 int num_variants();
 void variant(int i, LaunchCfg* c);  // sets kind, threads, minb, kc
 bool variant_exists(hydro_precision_t prec, const LaunchCfg& c);

@@ -19,10 +19,9 @@ static const Variant kVariants[] = {
     {kKindTiles, 256, 1, 4}, {kKindTiles, 128, 1, 4}, {kKindTiles, 512, 1, 4}, {kKindTiles, 512, 1, 2},
     {kKindTiles, 384, 1, 4}, {kKindTiles, 384, 1, 2}, {kKindTiles, 192, 1, 4}, {kKindTiles, 256, 2, 2},
     {kKindTiles, 128, 2, 2}, {kKindTiles, 448, 1, 2}, {kKindTiles, 576, 1, 1},
-    {kKindPipe, kPipeThreads, 1, 0}, {kKindQuad, kQuadThreads, 1, 0}};
+    {kKindPipe, kPipeThreads, 1, 0}, {kKindQuad, 0, 1, 0}};  // 26-point: threads by precision
 static constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 static_assert(kPipeThreads == hydro_dev::PNT, "pipelined kernel block size");
-static_assert(kQuadThreads == hydro_dev::QNT, "26-point kernel block size");
 
 template <int MODE>
 static void* kfunc(const LaunchCfg& c) {
@@ -48,6 +47,10 @@ static void* kfunc(const LaunchCfg& c) {
 
 static void* pick(hydro_precision_t prec, const LaunchCfg& c) {
   return prec == HYDRO_FP64 ? kfunc<0>(c) : kfunc<1>(c);
+}
+
+int quad_threads(hydro_precision_t prec) {
+  return prec == HYDRO_FP64 ? hydro_dev::QuadShape<0>::NT : hydro_dev::QuadShape<1>::NT;
 }
 
 int num_variants() { return kNumVariants; }
@@ -102,7 +105,7 @@ LaunchCfg default_cfg(hydro_precision_t prec, int Fmax, int n_sm, int smem_optin
   LaunchCfg c;
   if (quad26) {
     c.kind = kKindQuad;
-    c.threads = kQuadThreads;
+    c.threads = quad_threads(prec);
     c.minb = 1;
     c.kc = 0;
     c.lch = 64;

@@ -215,6 +215,7 @@ int hydro_plan_create(const hydro_subgrid_t* sg, int64_t n, int32_t ghost, doubl
       for (int pf = 0; pf < 3; pf++) {  // L2 prefetch: off, row segments, planes
         LaunchCfg c;
         variant(vi, &c);
+        if (c.kind == kKindQuad) c.threads = quad_threads(prec);
         if (!variant_exists(prec, c)) continue;
         if ((c.kind == kKindQuad) != quad26) continue;  // one scheme per plan
         if (quad26 && (li != 2 || pf != 0)) continue;

@@ -11,18 +11,19 @@
 // e_d - o1 e_a - o2 e_b (lower end), and the face flux is Simpson's rule in
 // both tangential directions, sum_p c_p Fhat_p / 36, c_p = (1,4,1)x(1,4,1).
 //
-// One CTA per 8^3 tile (persistent over the tile list), QNT threads:
+// One CTA per 8^3 tile (persistent over the tile list, one CTA per SM):
 //   load   hydro primitives and 1/rho of the tile's read region (every cell
 //          with each coordinate in [-3, e+2] and at most one of them at -3 or
-//          e+2) into shared memory; species are read through the read-only
-//          cache and divided by rho on use;
-//   faces  per direction, each thread owns three of the 576 faces.  Binary64:
-//          the three are consecutive faces of one line, walked with the
-//          points in pairs (o, -o) so that each single-cell reconstruction
-//          gives a state at two points; the weighted point fluxes are summed
-//          in shared memory.  Mixed: every point's two states are
-//          reconstructed and the weighted fluxes summed in registers (fewer
-//          live values: two CTAs per SM without spills);
+//          e+2) into shared memory.  Species: binary64 reads them through the
+//          read-only cache and divides by rho on use; the mixed form stores
+//          X_k = rho_k/rho of the region in binary32 once per tile;
+//   faces  per direction.  Binary64 (192 threads): each thread owns three
+//          consecutive faces of one line, walked with the points in pairs
+//          (o, -o) so that each single-cell reconstruction gives a state at
+//          two points; the weighted point fluxes are summed in shared memory.
+//          Mixed: each thread owns 576 / HYDRO_QUAD_MIXED_THREADS faces,
+//          reconstructs both states of every point and sums the weighted
+//          fluxes in registers;
 //   A4     each thread owns up to three cells and accumulates x, y, z flux
 //          differences (binary64, or exact binary32 pairs in the mixed form).
 #pragma once
@@ -31,16 +32,28 @@
 
 namespace hydro_dev {
 
-constexpr int QNT = 192;                  // threads per CTA (3 faces per thread per direction)
 constexpr int QBLK = LL * LL * LL;        // 2744 cells of the ghosted 14^3 neighbourhood
 constexpr int QFACES = NLN * NFC;         // 576 faces per direction
-constexpr int QFPT = QFACES / QNT;        // faces per thread: 3
-constexpr int QCPT = (TE * TE * TE + QNT - 1) / QNT;  // cells per thread: 3
-static_assert(QFACES % QNT == 0, "faces divide evenly over the threads");
+#ifndef HYDRO_QUAD_MIXED_THREADS
+#define HYDRO_QUAD_MIXED_THREADS 576
+#endif
+// Threads per CTA: binary64 192 (3 faces per thread and direction, one CTA
+// per SM); mixed HYDRO_QUAD_MIXED_THREADS (faces per thread 576 / that).
+template <int MODE>
+struct QuadShape {
+  static constexpr int NT = MODE == 0 ? 192 : HYDRO_QUAD_MIXED_THREADS;
+  static constexpr int FPT = QFACES / NT;                    // faces per thread and direction
+  static constexpr int CPT = (TE * TE * TE + NT - 1) / NT;   // accumulated cells per thread
+  static_assert(QFACES % NT == 0 && NT % 32 == 0, "faces divide evenly over whole warps");
+};
 
+// Shared memory: hydro primitives and 1/rho of the neighbourhood, the face
+// fluxes of one direction, and (mixed form) the species X_k = rho_k/rho of
+// the neighbourhood, formed once per tile.
 template <int MODE>
 __host__ __device__ constexpr size_t quad_smem_bytes() {
-  return (MODE == 0 ? 8 : 4) * ((size_t)6 * QBLK + QBLK + (size_t)QFACES * MAXF);
+  return (MODE == 0 ? 8 : 4) *
+         ((size_t)6 * QBLK + QBLK + (size_t)QFACES * MAXF + (MODE == 0 ? 0 : (size_t)(MAXF - 6) * QBLK));
 }
 
 __device__ __forceinline__ int qidx(int x, int y, int z) { return ((z + 3) * LL + (y + 3)) * LL + (x + 3); }
@@ -117,10 +130,12 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
                                                                                   0.0, 0}) {
   typedef typename QuadPrec<MODE>::R R;
   typedef typename QuadPrec<MODE>::Acc Acc;
+  constexpr int QNT = QuadShape<MODE>::NT, QFPT = QuadShape<MODE>::FPT, QCPT = QuadShape<MODE>::CPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* P = reinterpret_cast<R*>(smem_raw);  // [6][QBLK] hydro primitives
   R* RR = P + 6 * QBLK;                    // [QBLK] 1/rho
   R* FF = RR + QBLK;                       // [MAXF][QFACES] face fluxes of one direction
+  R* XS = FF + MAXF * QFACES;              // mixed: [MAXF - 6][QBLK] species X_k
   __shared__ double red[QNT / 32];
   const int tid = threadIdx.x;
   const float gamf = (float)gamma_d, gm1f = (float)(gamma_d - 1.0);
@@ -160,14 +175,38 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
 #pragma unroll
         for (int f = 0; f < 6; f++) P[f * QBLK + s] = w[f];
         RR[s] = r;
+        for (int k = 0; k < nsp; k++) bad |= !dfinite(__ldg(src + (6 + k) * plane));
       } else {
         float w[6], r;
         bad |= prim_mixed(u, gamma_d, gamf, gm1f, g53, w, r);
 #pragma unroll
         for (int f = 0; f < 6; f++) P[f * QBLK + s] = w[f];
         RR[s] = r;
+        // species X_k = rho_k / rho in binary32 (rho_k converted, times the
+        // binary32 1/rho), once per cell and tile: positive densities on the
+        // integer pipe, the cell again with the conversion instruction if any
+        // value is outside that path's range
+        double us[MAXF - 6];
+        float xs[MAXF - 6];
+        unsigned oor = 0;
+#pragma unroll
+        for (int k = 0; k < MAXF - 6; k++)
+          if (k < nsp) {
+            us[k] = __ldg(src + (6 + k) * plane);
+            xs[k] = d2f_fast_pos(us[k], oor);
+          }
+        if (oor >= D2F_OOR) {
+#pragma unroll
+          for (int k = 0; k < MAXF - 6; k++)
+            if (k < nsp) xs[k] = d2f_slow(us[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < MAXF - 6; k++)
+          if (k < nsp) {
+            bad |= !dfinite(us[k]);
+            XS[k * QBLK + s] = xs[k] * r;
+          }
       }
-      for (int k = 0; k < nsp; k++) bad |= !dfinite(__ldg(src + (6 + k) * plane));
     }
     bad = __syncthreads_or(bad);
     if (bad && tid == 0 && write_status) {
@@ -283,11 +322,14 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
             }
           }
         }
+        // Simpson's 1/36 as a product with its rounded reciprocal (within an
+        // ulp of the quotient; a binary64 division costs ~9 operations of
+        // the pipe this kernel is bound by)
 #pragma unroll
         for (int k = 0; k < 3; k++)
 #pragma unroll
           for (int f = 0; f < MAXF; f++)
-            if (f < F) FF[f * QFACES + l * NFC + i0 + k] /= R(36);
+            if (f < F) FF[f * QFACES + l * NFC + i0 + k] *= 1.0 / 36.0;
       } else {
         // ---- A2/A3: the faces of this direction, 9 points each
 #pragma unroll 1
@@ -297,7 +339,6 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
           const bool fvalid = ca < e_a && cb < e_b && i <= e_d;
           // the low cell (i-1 along d) and the high cell (i)
           const int il = qidx(0, 0, 0) + (i - 1) * Sd + ca * Sa + cb * Sb, ir = il + Sd;
-          const int gl0 = ogl + (i - 1) * Gd + ca * Ga + cb * Gb, gr0 = gl0 + Gd;
           R fsum[MAXF];
 #pragma unroll
           for (int f = 0; f < MAXF; f++) fsum[f] = R(0);
@@ -309,7 +350,6 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
             // lines e_d + o1 e_a + o2 e_b through the low cell, e_d - o1 e_a - o2 e_b
             // through the high cell
             const int sl = Sd + o1 * Sa + o2 * Sb, sr = Sd - o1 * Sa - o2 * Sb;
-            const int gsl = Gd + o1 * Ga + o2 * Gb, gsr = Gd - o1 * Ga - o2 * Gb;
             R wl[MAXF], wr[MAXF];
 #pragma unroll
             for (int f = 0; f < 6; f++) {
@@ -319,87 +359,26 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
                 ql[m] = P[f * QBLK + il + (m - 2) * sl];
                 qr[m] = P[f * QBLK + ir + (m - 2) * sr];
               }
-              if constexpr (MODE == 0) {
-                ppm5_64(ql, lo, hi);
-                wl[f] = hi;
-                ppm5_64(qr, lo, hi);
-                wr[f] = lo;
-              } else {
-                ppm5_32(ql, lo, hi);
-                wl[f] = hi;
-                ppm5_32(qr, lo, hi);
-                wr[f] = lo;
-              }
+              ppm5_32(ql, lo, hi);
+              wl[f] = hi;
+              ppm5_32(qr, lo, hi);
+              wr[f] = lo;
             }
-            // species X_k = rho_k / rho on the stencil cells
+            // species X_k on the stencil cells, formed once per tile
 #pragma unroll
             for (int f = 6; f < MAXF; f++) {
               if (f - 6 >= nsp) break;
-              const double* base = tile.U + f * plane;
+              const R* xk = XS + (f - 6) * QBLK;
               R ql[5], qr[5], lo, hi;
-              // all ten loads first; the mixed form converts them on the
-              // integer pipe and takes the conversion instruction (a call
-              // the loads could not be scheduled across) only for the rare
-              // stencil with a value outside the fast path's range
-              double ul[5], ur[5];
 #pragma unroll
               for (int m = 0; m < 5; m++) {
-                int ol, orr;
-                if constexpr (DOMAIN) {
-                  // tile coordinates of the stencil cells (axis d, then a, b)
-                  const int cd = i - 1, vd = 1;
-                  const int lx = d == 0 ? cd + (m - 2) * vd : ca + (m - 2) * o1;
-                  const int ly = d == 1 ? cd + (m - 2) * vd : (d == 0 ? ca + (m - 2) * o1 : cb + (m - 2) * o2);
-                  const int lz = d == 2 ? cd + (m - 2) * vd : cb + (m - 2) * o2;
-                  const int rx = d == 0 ? cd + 1 + (m - 2) * vd : ca - (m - 2) * o1;
-                  const int ry = d == 1 ? cd + 1 + (m - 2) * vd : (d == 0 ? ca - (m - 2) * o1 : cb - (m - 2) * o2);
-                  const int rz = d == 2 ? cd + 1 + (m - 2) * vd : cb - (m - 2) * o2;
-                  ol = off_of(lx, ly, lz);
-                  orr = off_of(rx, ry, rz);
-                } else {
-                  ol = gl0 + (m - 2) * gsl;
-                  orr = gr0 + (m - 2) * gsr;
-                }
-                ul[m] = __ldg(base + ol);
-                ur[m] = __ldg(base + orr);
+                ql[m] = xk[il + (m - 2) * sl];
+                qr[m] = xk[ir + (m - 2) * sr];
               }
-              if constexpr (MODE == 0) {
-#pragma unroll
-                for (int m = 0; m < 5; m++) {
-                  ql[m] = ul[m] * RR[il + (m - 2) * sl];
-                  qr[m] = ur[m] * RR[ir + (m - 2) * sr];
-                }
-              } else {
-                unsigned oor = 0;  // species densities: positive (zero and below take the slow path)
-#pragma unroll
-                for (int m = 0; m < 5; m++) {
-                  ql[m] = d2f_fast_pos(ul[m], oor);
-                  qr[m] = d2f_fast_pos(ur[m], oor);
-                }
-                if (oor >= D2F_OOR) {
-#pragma unroll
-                  for (int m = 0; m < 5; m++) {
-                    ql[m] = d2f_slow(ul[m]);
-                    qr[m] = d2f_slow(ur[m]);
-                  }
-                }
-#pragma unroll
-                for (int m = 0; m < 5; m++) {
-                  ql[m] *= RR[il + (m - 2) * sl];
-                  qr[m] *= RR[ir + (m - 2) * sr];
-                }
-              }
-              if constexpr (MODE == 0) {
-                ppm5_64(ql, lo, hi);
-                wl[f] = hi;
-                ppm5_64(qr, lo, hi);
-                wr[f] = lo;
-              } else {
-                ppm5_32(ql, lo, hi);
-                wl[f] = hi;
-                ppm5_32(qr, lo, hi);
-                wr[f] = lo;
-              }
+              ppm5_32(ql, lo, hi);
+              wl[f] = hi;
+              ppm5_32(qr, lo, hi);
+              wr[f] = lo;
             }
             // central-upwind flux at the point
             R fh[MAXF], g_l, g_r, a;
@@ -518,10 +497,9 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
 }
 
 // Same arguments as rhs_tiles_kernel; lch and prefetch do not apply.  One
-// CTA per SM in binary64 (up to 255 registers per thread), two in the mixed
-// form (shared memory and registers of a sub-partition allow it).
+// CTA per SM (shared memory: binary64 204 KB, mixed 157 KB).
 template <int MODE>
-__global__ void __launch_bounds__(QNT, MODE == 0 ? 1 : 2)
+__global__ void __launch_bounds__(QuadShape<MODE>::NT, 1)
 rhs_quad_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch, double* __restrict__ out,
                 double* __restrict__ amax_out, Status* __restrict__ status, double gamma_d,
                 int write_status, int prefetch, int scheme) {
@@ -533,7 +511,7 @@ rhs_quad_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch, 
 
 // The 26-point variant of the domain form (rhs_domain_kernel's arguments).
 template <int MODE>
-__global__ void __launch_bounds__(QNT, MODE == 0 ? 1 : 2)
+__global__ void __launch_bounds__(QuadShape<MODE>::NT, 1)
 rhs_domain_quad_kernel(DomainTiles dom, int n_tiles, int lch, double* __restrict__ out,
                        double* __restrict__ amax_out, Status* __restrict__ status, double gamma_d,
                        int write_status, int scheme, StageArgs stage) {
@@ -579,7 +557,7 @@ struct ForestQuadTiles {
 };
 
 template <int MODE>
-__global__ void __launch_bounds__(QNT, MODE == 0 ? 1 : 2)
+__global__ void __launch_bounds__(QuadShape<MODE>::NT, 1)
 rhs_forest_quad_kernel(ForestQuadTiles ft, int n_tiles, int lch, double* __restrict__ out,
                        double* __restrict__ amax_out, Status* __restrict__ status, double gamma_d,
                        int write_status, int scheme, StageArgs stage) {
