@@ -97,6 +97,21 @@ __device__ __forceinline__ void ppm5_32(const float* q, float& lo, float& hi) {
   float uu = up + up, du = dn + dn;
   limit1(qc, l, h, up, dn, up * dn, uu, du, qc - uu, qc + du, lo, hi);
 }
+// ppm5_32 on two fields at once: the additions and products as packed
+// binary32 pairs (each lane rounded as the scalar instruction rounds it),
+// the slope and limiter selections per lane -- the same bits as two calls.
+__device__ __forceinline__ void ppm5_32x2(const float2* q, float2& lo, float2& hi) {
+  const float2 d0 = sub2(q[1], q[0]), d1 = sub2(q[2], q[1]), d2 = sub2(q[3], q[2]), d3 = sub2(q[4], q[3]);
+  const float2 h1 = hslope32x2(d0, d1), h2 = hslope32x2(d1, d2), h3 = hslope32x2(d2, d3);
+  const float2 qc = q[2];
+  const float2 l = fma2(sub2(h1, h2), f2(1.0f / 3.0f), mul2(add2(q[1], q[2]), f2(0.5f)));
+  const float2 h = fma2(sub2(h2, h3), f2(1.0f / 3.0f), mul2(add2(q[2], q[3]), f2(0.5f)));
+  const float2 up = sub2(h, qc), dn = sub2(qc, l);
+  const float2 uu = add2(up, up), du = add2(dn, dn);
+  const float2 e = mul2(up, dn), lc = sub2(qc, uu), hc = add2(qc, du);
+  limit1(qc.x, l.x, h.x, up.x, dn.x, e.x, uu.x, du.x, lc.x, hc.x, lo.x, hi.x);
+  limit1(qc.y, l.y, h.y, up.y, dn.y, e.y, uu.y, du.y, lc.y, hc.y, lo.y, hi.y);
+}
 
 template <int MODE>
 struct QuadPrec;
@@ -351,34 +366,44 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
             // through the high cell
             const int sl = Sd + o1 * Sa + o2 * Sb, sr = Sd - o1 * Sa - o2 * Sb;
             R wl[MAXF], wr[MAXF];
-#pragma unroll
-            for (int f = 0; f < 6; f++) {
-              R ql[5], qr[5], lo, hi;
+            // fields f, f + 1 of the 5-cell stencils of both sides, one
+            // packed reconstruction per side; a: the field's array
+            auto pair = [&](const R* a0, const R* a1, int f) {
+              float2 ql[5], qr[5], lo, hi;
 #pragma unroll
               for (int m = 0; m < 5; m++) {
-                ql[m] = P[f * QBLK + il + (m - 2) * sl];
-                qr[m] = P[f * QBLK + ir + (m - 2) * sr];
+                ql[m] = make_float2(a0[il + (m - 2) * sl], a1[il + (m - 2) * sl]);
+                qr[m] = make_float2(a0[ir + (m - 2) * sr], a1[ir + (m - 2) * sr]);
               }
-              ppm5_32(ql, lo, hi);
-              wl[f] = hi;
-              ppm5_32(qr, lo, hi);
-              wr[f] = lo;
-            }
-            // species X_k on the stencil cells, formed once per tile
+              ppm5_32x2(ql, lo, hi);
+              wl[f] = hi.x;
+              wl[f + 1] = hi.y;
+              ppm5_32x2(qr, lo, hi);
+              wr[f] = lo.x;
+              wr[f + 1] = lo.y;
+            };
 #pragma unroll
-            for (int f = 6; f < MAXF; f++) {
+            for (int f = 0; f < 6; f += 2) pair(P + f * QBLK, P + (f + 1) * QBLK, f);
+            // species X_k on the stencil cells, formed once per tile; an odd
+            // last species alone
+#pragma unroll
+            for (int f = 6; f < MAXF; f += 2) {
               if (f - 6 >= nsp) break;
               const R* xk = XS + (f - 6) * QBLK;
-              R ql[5], qr[5], lo, hi;
+              if (f + 1 < MAXF && f - 6 + 1 < nsp) {  // (f + 1 < MAXF: known when unrolled)
+                pair(xk, xk + QBLK, f);
+              } else {
+                R ql[5], qr[5], lo, hi;
 #pragma unroll
-              for (int m = 0; m < 5; m++) {
-                ql[m] = xk[il + (m - 2) * sl];
-                qr[m] = xk[ir + (m - 2) * sr];
+                for (int m = 0; m < 5; m++) {
+                  ql[m] = xk[il + (m - 2) * sl];
+                  qr[m] = xk[ir + (m - 2) * sr];
+                }
+                ppm5_32(ql, lo, hi);
+                wl[f] = hi;
+                ppm5_32(qr, lo, hi);
+                wr[f] = lo;
               }
-              ppm5_32(ql, lo, hi);
-              wl[f] = hi;
-              ppm5_32(qr, lo, hi);
-              wr[f] = lo;
             }
             // central-upwind flux at the point
             R fh[MAXF], g_l, g_r, a;
