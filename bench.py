@@ -1320,6 +1320,23 @@ def run_profile(args):
     if args.profile.startswith("forest"):
         return run_profile_forest(args)
     batch = polytrope_batch(n=args.domain)
+    if args.profile.startswith("domain"):
+        # the domain form: the same cells stored without ghosts, the ghost
+        # shells gathered in the kernel (one launch per call, no tuning)
+        prec = hydro.FP64 if args.profile == "domain64" else hydro.FP32_FLUX_FP64_ACC
+        dom = batch.blocks[:, :, 3:-3, 3:-3, 3:-3].contiguous()
+        del batch.blocks
+        dout = torch.empty_like(dom)
+        amax = torch.empty(batch.n, dtype=torch.float64, device="cuda")
+        nbd = args.domain // batch.N
+        ms = time_steps(lambda: hydro.domain_rhs(dom, nbd, batch.N, batch.nf, batch.dx, dout, amax, prec=prec,
+                                                 stream=stream), args.steps, args.warmup, stream)
+        rc, bad = hydro.status(stream)
+        print(json.dumps({"profile": args.profile, "domain": args.domain, "subgrids": batch.n, "ms": ms,
+                          "alg_bytes": batch.alg_bytes, "status": rc, "launches_before_timed": args.warmup,
+                          "kernel": "rhs_domain_kernel" if prec == hydro.FP64 else "rhs_domain_pipe"}),
+              flush=True)
+        return
     prec = hydro.FP64 if args.profile.startswith("fp64") else hydro.FP32_FLUX_FP64_ACC
     flags = hydro.PLAN_QUAD26 if args.profile.endswith("quad26") else 0
     plan = hydro.Plan(batch.desc, ghost=3, gamma=GAMMA, prec=prec, autotune=True, stream=stream,
@@ -1364,8 +1381,9 @@ def main():
                     help="skip the smaller workloads (one sub-grid, 512 sub-grids, the uneven batch)")
     ap.add_argument("--rate", type=float, default=20000.0, help="serving arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
-    ap.add_argument("--profile", choices=["fp64", "mixed", "fp64_quad26", "mixed_quad26", "forest64",
-                                          "forestmx", "forest64_quad26", "forestmx_quad26"], default=None,
+    ap.add_argument("--profile", choices=["fp64", "mixed", "fp64_quad26", "mixed_quad26", "domain64", "domainmx",
+                                          "forest64", "forestmx", "forest64_quad26", "forestmx_quad26"],
+                    default=None,
                     help="short run of one form for ncu (no JSON bench line)")
     args = ap.parse_args()
     if args.profile:
