@@ -1432,8 +1432,11 @@ rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
 // aligned move in 16-byte copies: the interior rows with their x ghosts
 // (7 per row) and every ghost-slab row as the aligned span x = -1 .. TE
 // (5 per row; the 32-byte sectors the cells x = 0 .. TE-1 occupy in any
-// case); other tiles (partial, periodic domains, forests, misaligned
-// blocks) use one 8-byte copy per cell.  One CTA of PNT threads per SM; the
+// case).  Full tiles of a ghost-free domain with even N move in 16-byte
+// copies too, each located in its periodic sub-grid (8 per interior row
+// x = -4 .. 11, 4 per ghost-slab row x = 0 .. TE-1; staged in the domain
+// layout below).  Other tiles (partial, forests, misaligned blocks) use one
+// 8-byte copy per cell.  One CTA of PNT threads per SM; the
 // three directions are reconstructed together, so every phase divides
 // evenly over the threads:
 //   PPM   3 directions x 64 lines x 3 field pairs = 576 tasks
@@ -1445,7 +1448,7 @@ rhs_tiles_kernel(const Tile* __restrict__ tiles, int n_tiles, int Fmax, int lch,
 //                        QS [3][2][3][NLN][NFC] float2      82944
 // Staging layout of one field: the interior rows [z][y][LL] as in the read
 // region (XROWS), then the y-ghost rows [z][yg][SROW] and the z-ghost rows
-// [zg][y][SROW], each holding x = -1 .. TE.
+// [zg][y][SROW], each holding x = -1 .. TE.  (Domain tiles: sslot_dom.)
 constexpr int PNT = 3 * NLN * 3;  // 576
 constexpr int PSPT = (STAR + PNT - 1) / PNT;  // read-region slots per thread: 3
 constexpr int SROW = TE + 2;                  // a staged ghost-slab row
@@ -1458,6 +1461,22 @@ __host__ __device__ __forceinline__ int sslot(int s) {
   if (s < XROWS) return s;
   const int t = s - XROWS;  // ghost-slab cell: row t / TE, x = t % TE
   return XROWS + (t / TE) * SROW + (t % TE) + 1;
+}
+// The domain form's staging layout (ghost-free storage, where a tile's row
+// x = 0..7 starts 16-byte aligned in its sub-grid when N is even): interior
+// rows of DROW values x = -4..11, then the ghost-slab rows of the 8 values
+// x = 0..7, so that every 2-cell chunk of an even x is 16-byte aligned in the
+// stored rows and in shared memory.  It fits in one field's SSTAR.
+constexpr int DROW = TE + 8;                           // 16
+constexpr int DSTAR = TE * TE * DROW + 2 * 6 * TE * TE;  // 1792
+static_assert(DSTAR <= SSTAR, "the domain staging layout fits a field's staging");
+__host__ __device__ __forceinline__ int sslot_dom(int s) {
+  if (s < XROWS) return (s / LL) * DROW + s % LL + 1;
+  return TE * TE * DROW + (s - XROWS);
+}
+template <int DOM>
+__host__ __device__ __forceinline__ int stage_slot(int s) {
+  return DOM == 1 ? sslot_dom(s) : sslot(s);
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -1492,36 +1511,50 @@ __device__ __forceinline__ void cp_async16cg(void* dst, const void* src) {
 // interior rows (from x = -3) and the ghost-slab rows (from x = -1) do.
 template <int DOM>
 __device__ __forceinline__ bool chunk_ok(const Tile& tile) {
-  if constexpr (DOM != 0) {
+  if constexpr (DOM == 2) {
     return false;
+  } else if constexpr (DOM == 1) {
+    // full tile of a domain with even N: every even-x chunk of 2 cells lies
+    // in one sub-grid row, 16-byte aligned
+    return tile.N - tile.ox >= TE && tile.N - tile.oy >= TE && tile.N - tile.oz >= TE && (tile.N & 1) == 0 &&
+           (reinterpret_cast<uintptr_t>(tile.U) & 15) == 0;
   } else {
     const int gh = (tile.G - tile.N) >> 1;
     return tile.N - tile.ox >= TE && tile.N - tile.oy >= TE && tile.N - tile.oz >= TE && (tile.G & 1) == 0 &&
            (gh & 1) == 1 && (reinterpret_cast<uintptr_t>(tile.U) & 15) == 0;
   }
 }
-// The 16-byte chunks of one field's staging: 7 per interior row (64 rows),
-// 5 per ghost-slab row (96 rows); every thread takes chunks tid and
-// tid + PNT.  A chunk is (z, y, x0) of its first cell, x0 in {-3, -1} + 2k,
-// and its staging slot.
+// The 16-byte chunks of one field's staging; every thread takes chunks tid
+// and tid + PNT.  A chunk is (z, y, x0) of its first cell and its staging
+// slot.  Ghosted blocks: 7 per interior row (64 rows, x0 in -3 + 2k), 5 per
+// ghost-slab row (96 rows, x0 in -1 + 2k).  Domain form: 8 per interior row
+// (x0 in -4 + 2k), 4 per ghost-slab row (x0 in 2k).
 constexpr int NCHUNK = TE * TE * (LL / 2) + 2 * 6 * TE * (SROW / 2);  // 928
+constexpr int NCHUNK_D = TE * TE * (DROW / 2) + 2 * 6 * TE * (TE / 2);  // 896
 constexpr int PCPT = (NCHUNK + PNT - 1) / PNT;                          // chunks per thread: 2
+static_assert(NCHUNK_D <= PCPT * PNT, "the domain chunks fit the same count per thread");
 struct ChunkGeom {
   int zyx[PCPT];  // z, y, x0 as signed bytes; 0x7f7f7f7f: none
   int st[PCPT];   // staging slot of the first double
+  template <int DOM>
   __device__ __forceinline__ void init(int tid) {
+    // chunks per interior row and per slab row, their first x, the slab rows' slot base and width
+    constexpr int CR = DOM == 1 ? DROW / 2 : LL / 2, CS = DOM == 1 ? TE / 2 : SROW / 2;
+    constexpr int X0R = DOM == 1 ? -4 : -3, X0S = DOM == 1 ? 0 : -1;
+    constexpr int RW = DOM == 1 ? DROW : LL, SBASE = DOM == 1 ? TE * TE * DROW : XROWS, SW = DOM == 1 ? TE : SROW;
+    constexpr int NC = TE * TE * CR + 2 * 6 * TE * CS;
 #pragma unroll
     for (int k = 0; k < PCPT; k++) {
       const int c = tid + k * PNT;
       int z = 0, y = 0, x0 = 0, slot = 0;
-      if (c < TE * TE * (LL / 2)) {
-        const int row = c / (LL / 2), q = c % (LL / 2);
+      if (c < TE * TE * CR) {
+        const int row = c / CR, q = c % CR;
         z = row / TE;
         y = row % TE;
-        x0 = -3 + 2 * q;
-        slot = row * LL + 2 * q;
-      } else if (c < NCHUNK) {
-        const int c2 = c - TE * TE * (LL / 2), r = c2 / (SROW / 2), q = c2 % (SROW / 2);
+        x0 = X0R + 2 * q;
+        slot = row * RW + 2 * q;
+      } else if (c < NC) {
+        const int c2 = c - TE * TE * CR, r = c2 / CS, q = c2 % CS;
         if (r < 6 * TE) {
           z = r / 6;
           const int yg = r % 6;
@@ -1531,14 +1564,33 @@ struct ChunkGeom {
           y = r2 % TE;
           z = zg < 3 ? zg - 3 : zg + TE - 3;
         }
-        x0 = -1 + 2 * q;
-        slot = XROWS + r * SROW + 2 * q;
+        x0 = X0S + 2 * q;
+        slot = SBASE + r * SW + 2 * q;
       }
-      zyx[k] = c < NCHUNK ? ((z & 0xff) | ((y & 0xff) << 8) | ((x0 & 0xff) << 16)) : 0x7f7f7f7f;
+      zyx[k] = c < NC ? ((z & 0xff) | ((y & 0xff) << 8) | ((x0 & 0xff) << 16)) : 0x7f7f7f7f;
       st[k] = slot;
     }
   }
 };
+// Issue the 16-byte copies of fields f0 .. f0+nf-1 of a domain tile
+// (chunk_ok<1>): each chunk located in its (periodic) sub-grid.
+__device__ __forceinline__ void chunk_issue_dom(const Tile& tile, const ChunkGeom& cg, double* S, int f0, int nf) {
+  const int N = tile.N;
+  const long long plane = (long long)N * N * N;
+  DomainPos dp;
+  dp.init(tile.sub, tile.pad[0], N, tile.F);
+  const double* base = tile.U + (long long)f0 * plane;
+#pragma unroll
+  for (int k = 0; k < PCPT; k++) {
+    if (cg.zyx[k] == 0x7f7f7f7f) continue;
+    const int z = (int)(signed char)(cg.zyx[k] & 0xff), y = (int)(signed char)((cg.zyx[k] >> 8) & 0xff),
+              x0 = (int)(signed char)((cg.zyx[k] >> 16) & 0xff);
+    const double* src = base + dp.off(tile.ox + x0, tile.oy + y, tile.oz + z);
+#pragma unroll
+    for (int f = 0; f < 6; f++)
+      if (f < nf) cp_async16cg(S + f * SSTAR + cg.st[k], src + f * plane);
+  }
+}
 // Issue the 16-byte copies of fields f0 .. f0+nf-1 (chunk_ok tiles).
 __device__ __forceinline__ void chunk_issue(const Tile& tile, const ChunkGeom& cg, double* S, int f0, int nf) {
   const int G = tile.G, gh = (G - tile.N) >> 1;
@@ -1562,13 +1614,14 @@ __device__ __forceinline__ void chunk_issue(const Tile& tile, const ChunkGeom& c
 struct SlotXYZ {
   int p[PSPT];
   int ss[PSPT];
+  template <int DOM>
   __device__ __forceinline__ void init(int tid) {
 #pragma unroll
     for (int k = 0; k < PSPT; k++) {
       int s = tid + k * PNT, x = 0, y = 0, z = 0;
       if (s < STAR) cell_of(s, x, y, z);
       p[k] = (x & 0xff) | ((y & 0xff) << 8) | ((z & 0xff) << 16);
-      ss[k] = sslot(s < STAR ? s : 0);
+      ss[k] = stage_slot<DOM>(s < STAR ? s : 0);
     }
   }
   __device__ __forceinline__ void get(int k, int& x, int& y, int& z) const {
@@ -1604,7 +1657,8 @@ template <int DOM, class Fetch>
 __device__ __forceinline__ void pipe_issue(const Fetch& fetch, const Tile& tile, const SlotXYZ& sx,
                                            const ChunkGeom& cg, double* S, int f0, int nf) {
   if (chunk_ok<DOM>(tile)) {
-    chunk_issue(tile, cg, S, f0, nf);
+    if constexpr (DOM == 1) chunk_issue_dom(tile, cg, S, f0, nf);
+    else chunk_issue(tile, cg, S, f0, nf);
     cp_async_commit();
     return;
   }
@@ -1658,9 +1712,9 @@ __device__ __forceinline__ void tile_loop_pipe(const Fetch& fetch, int n_tiles, 
   // QS block of (direction d, side 0 left / 1 right, pair j)
   auto qs = [&](int d, int side, int j) { return QS + ((d * 2 + side) * 3 + j) * FS; };
   SlotXYZ sx;
-  sx.init(tid);
+  sx.template init<DOM>(tid);
   ChunkGeom cg;
-  cg.init(tid);
+  cg.template init<DOM>(tid);
   // Tile descriptors, double-buffered in shared memory: thread 0 fetches the
   // next tile's while the current one is converted, so that its latency is
   // hidden before the next tile's copies are issued.

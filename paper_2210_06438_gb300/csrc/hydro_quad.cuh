@@ -346,7 +346,7 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
           for (int f = 0; f < MAXF; f++)
             if (f < F) FF[f * QFACES + l * NFC + i0 + k] *= 1.0 / 36.0;
       } else {
-        // ---- A2/A3: the faces of this direction, 9 points each
+        // ---- A2/A3 (mixed form): the faces of this direction, 9 points each
 #pragma unroll 1
         for (int k = 0; k < QFPT; k++) {
           const int face = tid + k * QNT, l = face / NFC, i = face - l * NFC;
@@ -406,31 +406,20 @@ __device__ __forceinline__ void tile_loop_quad(const Fetch& fetch, int n_tiles, 
               }
             }
             // central-upwind flux at the point
-            R fh[MAXF], g_l, g_r, a;
-            if constexpr (MODE == 0) {
-              a = kt_hydro64(wl, wr, d, gamma, inv_gm1, knp, fh, 1, g_l, g_r);
-            } else {
-              float2 pl[3] = {make_float2(wl[0], wl[1]), make_float2(wl[2], wl[3]), make_float2(wl[4], wl[5])};
-              float2 pr[3] = {make_float2(wr[0], wr[1]), make_float2(wr[2], wr[3]), make_float2(wr[4], wr[5])};
-              float2 fo[3];
-              a = kt_hydro32(pl, pr, d, gamma, inv_gm1, knp, fo, 1, g_l, g_r);
-              fh[0] = fo[0].x, fh[1] = fo[0].y, fh[2] = fo[1].x, fh[3] = fo[1].y, fh[4] = fo[2].x, fh[5] = fo[2].y;
-            }
+            float fh[MAXF], g_l, g_r;
+            float2 pl[3] = {make_float2(wl[0], wl[1]), make_float2(wl[2], wl[3]), make_float2(wl[4], wl[5])};
+            float2 pr[3] = {make_float2(wr[0], wr[1]), make_float2(wr[2], wr[3]), make_float2(wr[4], wr[5])};
+            float2 fo[3];
+            const float a = kt_hydro32(pl, pr, d, gamma, inv_gm1, knp, fo, 1, g_l, g_r);
+            fh[0] = fo[0].x, fh[1] = fo[0].y, fh[2] = fo[1].x, fh[3] = fo[1].y, fh[4] = fo[2].x, fh[5] = fo[2].y;
 #pragma unroll
             for (int f = 6; f < MAXF; f++)
-              if (f - 6 < nsp) {
-                if constexpr (MODE == 0) fh[f] = fma(wl[f], g_l, wr[f] * g_r);
-                else fh[f] = fmaf(wl[f], g_l, wr[f] * g_r);
-              }
-            const R cw = R((o1 == 0 ? 4 : 1) * (o2 == 0 ? 4 : 1));
+              if (f - 6 < nsp) fh[f] = fmaf(wl[f], g_l, wr[f] * g_r);
+            const float cw = (float)((o1 == 0 ? 4 : 1) * (o2 == 0 ? 4 : 1));
 #pragma unroll
             for (int f = 0; f < MAXF; f++)
-              if (f < F) {
-                if constexpr (MODE == 0) fsum[f] = fma(cw, fh[f], fsum[f]);
-                else fsum[f] = fmaf(cw, fh[f], fsum[f]);
-              }
-            if constexpr (MODE == 0) amax = dmaxp(amax, a);
-            else amax = fmaxf(amax, a);
+              if (f < F) fsum[f] = fmaf(cw, fh[f], fsum[f]);
+            amax = fmaxf(amax, a);
           }
 #pragma unroll
           for (int f = 0; f < MAXF; f++)
