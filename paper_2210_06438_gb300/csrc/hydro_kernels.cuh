@@ -1476,7 +1476,7 @@ __host__ __device__ __forceinline__ int sslot_dom(int s) {
 }
 template <int DOM>
 __host__ __device__ __forceinline__ int stage_slot(int s) {
-  return DOM == 1 ? sslot_dom(s) : sslot(s);
+  return DOM != 0 ? sslot_dom(s) : sslot(s);  // forests are ghost-free too
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -1528,7 +1528,7 @@ __device__ __forceinline__ bool chunk_ok(const Tile& tile) {
 // and tid + PNT.  A chunk is (z, y, x0) of its first cell and its staging
 // slot.  Ghosted blocks: 7 per interior row (64 rows, x0 in -3 + 2k), 5 per
 // ghost-slab row (96 rows, x0 in -1 + 2k).  Domain form: 8 per interior row
-// (x0 in -4 + 2k), 4 per ghost-slab row (x0 in 2k).
+// (x0 in -4 + 2k), 4 per ghost-slab row (x0 in 2k); forests the same.
 constexpr int NCHUNK = TE * TE * (LL / 2) + 2 * 6 * TE * (SROW / 2);  // 928
 constexpr int NCHUNK_D = TE * TE * (DROW / 2) + 2 * 6 * TE * (TE / 2);  // 896
 constexpr int PCPT = (NCHUNK + PNT - 1) / PNT;                          // chunks per thread: 2
@@ -1539,9 +1539,10 @@ struct ChunkGeom {
   template <int DOM>
   __device__ __forceinline__ void init(int tid) {
     // chunks per interior row and per slab row, their first x, the slab rows' slot base and width
-    constexpr int CR = DOM == 1 ? DROW / 2 : LL / 2, CS = DOM == 1 ? TE / 2 : SROW / 2;
-    constexpr int X0R = DOM == 1 ? -4 : -3, X0S = DOM == 1 ? 0 : -1;
-    constexpr int RW = DOM == 1 ? DROW : LL, SBASE = DOM == 1 ? TE * TE * DROW : XROWS, SW = DOM == 1 ? TE : SROW;
+    constexpr bool GF = DOM != 0;  // ghost-free storage: domains and forests
+    constexpr int CR = GF ? DROW / 2 : LL / 2, CS = GF ? TE / 2 : SROW / 2;
+    constexpr int X0R = GF ? -4 : -3, X0S = GF ? 0 : -1;
+    constexpr int RW = GF ? DROW : LL, SBASE = GF ? TE * TE * DROW : XROWS, SW = GF ? TE : SROW;
     constexpr int NC = TE * TE * CR + 2 * 6 * TE * CS;
 #pragma unroll
     for (int k = 0; k < PCPT; k++) {
@@ -1586,6 +1587,26 @@ __device__ __forceinline__ void chunk_issue_dom(const Tile& tile, const ChunkGeo
     const int z = (int)(signed char)(cg.zyx[k] & 0xff), y = (int)(signed char)((cg.zyx[k] >> 8) & 0xff),
               x0 = (int)(signed char)((cg.zyx[k] >> 16) & 0xff);
     const double* src = base + dp.off(tile.ox + x0, tile.oy + y, tile.oz + z);
+#pragma unroll
+    for (int f = 0; f < 6; f++)
+      if (f < nf) cp_async16cg(S + f * SSTAR + cg.st[k], src + f * plane);
+  }
+}
+// The same for a forest leaf (a full tile of even N whose leaf and
+// auxiliary blocks start 16-byte aligned): each chunk in the block that
+// ForestLoc locates -- the leaf, a same-level neighbour or the auxiliary
+// block of a face towards another level, all stored [F][N^3].  A chunk
+// never straddles two blocks (N even, x0 even); the cells x = -4 and 11 it
+// also copies go to staging slots that nothing reads.
+__device__ __forceinline__ void chunk_issue_forest(const ForestLoc& fl, const Tile& tile, const ChunkGeom& cg,
+                                                   double* S, int f0, int nf) {
+  const long long plane = (long long)tile.N * tile.N * tile.N;
+#pragma unroll
+  for (int k = 0; k < PCPT; k++) {
+    if (cg.zyx[k] == 0x7f7f7f7f) continue;
+    const int z = (int)(signed char)(cg.zyx[k] & 0xff), y = (int)(signed char)((cg.zyx[k] >> 8) & 0xff),
+              x0 = (int)(signed char)((cg.zyx[k] >> 16) & 0xff);
+    const double* src = fl.ptr(tile.ox + x0, tile.oy + y, tile.oz + z) + (long long)f0 * plane;
 #pragma unroll
     for (int f = 0; f < 6; f++)
       if (f < nf) cp_async16cg(S + f * SSTAR + cg.st[k], src + f * plane);
@@ -1656,8 +1677,16 @@ __device__ __forceinline__ int pipe_offset(const Tile& tile, const DomainPos& dp
 template <int DOM, class Fetch>
 __device__ __forceinline__ void pipe_issue(const Fetch& fetch, const Tile& tile, const SlotXYZ& sx,
                                            const ChunkGeom& cg, double* S, int f0, int nf) {
-  if (chunk_ok<DOM>(tile)) {
+  bool chunks;
+  if constexpr (DOM == 2) {
+    chunks = tile.N - tile.ox >= TE && tile.N - tile.oy >= TE && tile.N - tile.oz >= TE && (tile.N & 1) == 0 &&
+             ((reinterpret_cast<uintptr_t>(fetch.U) | reinterpret_cast<uintptr_t>(fetch.aux)) & 15) == 0;
+  } else {
+    chunks = chunk_ok<DOM>(tile);
+  }
+  if (chunks) {
     if constexpr (DOM == 1) chunk_issue_dom(tile, cg, S, f0, nf);
+    else if constexpr (DOM == 2) chunk_issue_forest(fetch.loc(tile), tile, cg, S, f0, nf);
     else chunk_issue(tile, cg, S, f0, nf);
     cp_async_commit();
     return;
