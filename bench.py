@@ -1204,11 +1204,17 @@ def run_ours(args, rank, world):
             "hbm": {"achieved_gbs": batch.alg_bytes / (ms64 * 1e-3) * 1e-9, "peak_gbs": hbm_peak,
                     "frac": batch.alg_bytes / (ms64 * 1e-3) * 1e-9 / hbm_peak,
                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}}
+    # the dense-block figure beside the algorithmic one: every ghosted block
+    # read whole ((N + 2g)^3 cells) plus dU/dt, the bytes a kernel reading
+    # whole blocks would move
+    dense_bytes = batch.n * ((batch.N + 6) ** 3 + batch.N ** 3) * batch.nf * 8
     mixed_roof = {"bound": "hbm", "achieved": batch.alg_bytes / (msmx * 1e-3) * 1e-9,
                   "peak": hbm_peak, "unit": "GB/s",
                   "traffic": recorded_traffic("mixed", infomx["n_tiles"]),
                   "alg_bytes": batch.alg_bytes,
                   "frac": batch.alg_bytes / (msmx * 1e-3) * 1e-9 / hbm_peak,
+                  "dense_block_bytes": dense_bytes,
+                  "dense_block_frac": dense_bytes / (msmx * 1e-3) * 1e-9 / hbm_peak,
                   "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
 
     # ---- oracle on the host cores (bounded sample of the same workload)
