@@ -100,6 +100,9 @@ typedef enum { HYDRO_FP64 = 0, HYDRO_FP32_FLUX_FP64_ACC = 1 } hydro_precision_t;
  *   gamma      ratio of specific heats, > 1
  *   out_dUdt, out_amax  outputs as described above, in device memory or in
  *              pinned host memory (written in place by the kernel)
+ * Work list: a batch of one N and one field count has its tiles built on the
+ * device from the copied descriptors; other batches build it on the host,
+ * the sub-grids with more fields first.
  * Allocation: the first call on a device (and a call with a larger batch than
  * any before) allocates library workspace; later calls allocate nothing. */
 int hydro_rhs(const hydro_subgrid_t* subgrids, int64_t n_subgrids, int32_t N, int32_t ghost,
