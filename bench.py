@@ -284,6 +284,19 @@ def recorded_traffic(form, n_tiles):
         return None
 
 
+def recorded_counts(form):
+    """The committed ncu record of a form (bytes and instruction counts per
+    tile), or None unless the kernel source's code still matches it."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        src = os.path.join(ROOT, "paper_2210_06438_gb300", "csrc", "hydro_kernels.cuh")
+        if kernel_source_digest(src) != rec["kernel_code_sha256"]:
+            return None
+        return rec["forms"][form]
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -1204,6 +1217,15 @@ def run_ours(args, rank, world):
             "hbm": {"achieved_gbs": batch.alg_bytes / (ms64 * 1e-3) * 1e-9, "peak_gbs": hbm_peak,
                     "frac": batch.alg_bytes / (ms64 * 1e-3) * 1e-9 / hbm_peak,
                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}}
+    # the kernel's own binary64-pipe instructions (ncu record) at the probe's
+    # rate (one fused multiply-add = one pipe instruction, two flops)
+    rc64 = recorded_counts("fp64")
+    if rc64 and "fp64_pipe_thread_instructions_per_tile" in rc64:
+        pipe_ops = rc64["fp64_pipe_thread_instructions_per_tile"] * info64["n_tiles"]
+        floor_ms = pipe_ops / (peak_fp64 * 1e9 / 2) * 1e3
+        roof["fp64_pipe"] = {"thread_instructions": pipe_ops, "floor_ms": floor_ms, "frac": floor_ms / ms64,
+                             "source": "sm__thread_inst_executed_pipe_fp64_pred_on.sum per tile (ncu record) at "
+                                       "the measured probe rate"}
     # the dense-block figure beside the algorithmic one: every ghosted block
     # read whole ((N + 2g)^3 cells) plus dU/dt, the bytes a kernel reading
     # whole blocks would move
@@ -1216,6 +1238,16 @@ def run_ours(args, rank, world):
                   "dense_block_bytes": dense_bytes,
                   "dense_block_frac": dense_bytes / (msmx * 1e-3) * 1e-9 / hbm_peak,
                   "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    # the bound that holds for this kernel: instruction issue (ncu record of
+    # its warp instructions per tile; 4 per clock per SM)
+    rcmx = recorded_counts("mixed")
+    if rcmx and "warp_instructions_per_tile" in rcmx:
+        insts = rcmx["warp_instructions_per_tile"] * infomx["n_tiles"]
+        mhz = clocks.get("sm_mhz") or 2070.0
+        floor_ms = insts / (4.0 * n_sm * mhz * 1e6) * 1e3
+        mixed_roof["issue"] = {"warp_instructions": insts, "floor_ms": floor_ms, "frac": floor_ms / msmx,
+                               "source": "smsp__inst_executed.sum per tile (ncu record), 4 issues per clock "
+                                         "per SM at the sampled SM clock"}
 
     # ---- oracle on the host cores (bounded sample of the same workload)
     cpu = None
