@@ -175,67 +175,74 @@ forest_reflux_kernel(const int* __restrict__ links, const AuxDesc* __restrict__ 
 }
 
 // The 26-point variant reads edge and corner ghosts too: each leaf's ghosted
-// block (G = N + 6) is gathered whole.  One thread per (leaf, cell of the
-// block with each coordinate in [-3, N+2] and at most one at -3 or N+2), all
-// fields.  nb26[27 s + (dx+1) + 3 (dy+1) + 9 (dz+1)] describes the block of
-// the leaf's level at offset (dx, dy, dz): x = 0 a leaf of that level (y),
-// -1 inside the coarser leaf y, +1 refined: kids[8 y + i + 2j + 4k] are its
-// children (those next to the leaf are leaves).
+// block (G = N + 6) is gathered whole.  One CTA per leaf (grid-stride over
+// the leaves); its threads take the cells of the block with each coordinate
+// in [-3, N+2] and at most one at -3 or N+2, all fields, so that the block is
+// written contiguously.  nb26[27 s + (dx+1) + 3 (dy+1) + 9 (dz+1)] describes
+// the block of the leaf's level at offset (dx, dy, dz): x = 0 a leaf of that
+// level (y), -1 inside the coarser leaf y, +1 refined: kids[8 y + i + 2j + 4k]
+// are its children (those next to the leaf are leaves).  The leaf's 27
+// entries and geometry are read once into shared memory.
 __global__ void __launch_bounds__(256)
 forest_gather26_kernel(const double* __restrict__ U, double* __restrict__ ghost, const int2* __restrict__ nb26,
                        const int* __restrict__ kids, const LeafGeo* __restrict__ geo, int nl, int N, int F,
                        int nb0) {
-  const int G = N + 6;
-  const long long g3 = (long long)G * G * G, n3 = (long long)N * N * N, nn = (long long)N * N;
-  const long long total = (long long)nl * g3;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(i / g3);
-    const int r = (int)(i - s * g3);
-    const int cx = r % G - 3, cy = (r / G) % G - 3, cz = r / (G * G) - 3;
-    const int far = (cx == -3 || cx == N + 2) + (cy == -3 || cy == N + 2) + (cz == -3 || cz == N + 2);
-    if (far > 1) continue;
-    double* dst = ghost + (long long)s * F * g3 + r;
-    const int sx = cx < 0 ? -1 : (cx >= N ? 1 : 0), sy = cy < 0 ? -1 : (cy >= N ? 1 : 0),
-              sz = cz < 0 ? -1 : (cz >= N ? 1 : 0);
-    if (sx == 0 && sy == 0 && sz == 0) {
-      const double* src = U + (long long)s * F * n3 + ((long long)cz * N + cy) * N + cx;
-      for (int f = 0; f < F; f++) dst[f * g3] = __ldg(src + f * n3);
-      continue;
-    }
-    const int2 e = nb26[27 * s + (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)];
-    const LeafGeo og = geo[s];
+  __shared__ int2 nbs[27];
+  __shared__ LeafGeo gs;
+  const int G = N + 6, g3 = G * G * G, n3 = N * N * N, nn = N * N;
+  for (int s = blockIdx.x; s < nl; s += gridDim.x) {
+    __syncthreads();  // the previous leaf's readers are done with nbs, gs
+    if (threadIdx.x < 27) nbs[threadIdx.x] = nb26[27 * s + threadIdx.x];
+    if (threadIdx.x == 0) gs = geo[s];
+    __syncthreads();
+    const LeafGeo og = gs;
     const int M = nb0 << og.level;
-    auto wrap = [M](int q) { return q < 0 ? q + M : (q >= M ? q - M : q); };
-    const int px = wrap(og.bx + sx), py = wrap(og.by + sy), pz = wrap(og.bz + sz);
-    const int vx = cx - sx * N, vy = cy - sy * N, vz = cz - sz * N;  // cell in block p
-    const int gx = px * N + vx, gy = py * N + vy, gz = pz * N + vz;  // level cell index
-    if (e.x == 0) {
-      const double* src = U + (long long)e.y * F * n3 + ((long long)vz * N + vy) * N + vx;
-      for (int f = 0; f < F; f++) dst[f * g3] = __ldg(src + f * n3);
-    } else if (e.x < 0) {
-      const LeafGeo cg = geo[e.y];
-      const int lx = (gx >> 1) - cg.bx * N, ly = (gy >> 1) - cg.by * N, lz = (gz >> 1) - cg.bz * N;
-      const double* src = U + (long long)e.y * F * n3 + ((long long)lz * N + ly) * N + lx;
-      for (int f = 0; f < F; f++) dst[f * g3] = __ldg(src + f * n3);
-    } else {
-      const int fx = 2 * gx, fy = 2 * gy, fz = 2 * gz;
-      const int ch = (fx / N - 2 * px) + 2 * (fy / N - 2 * py) + 4 * (fz / N - 2 * pz);
-      const int leaf = __ldg(kids + 8 * e.y + ch);
-      const LeafGeo fg = geo[leaf];
-      const int lx = fx - fg.bx * N, ly = fy - fg.by * N, lz = fz - fg.bz * N;
-      const double* src = U + (long long)leaf * F * n3 + ((long long)lz * N + ly) * N + lx;
-      for (int f = 0; f < F; f++) {
-        const double* q = src + f * n3;
-        double t = __ldg(q);
-        t = t + __ldg(q + 1);
-        t = t + __ldg(q + N);
-        t = t + __ldg(q + N + 1);
-        t = t + __ldg(q + nn);
-        t = t + __ldg(q + nn + 1);
-        t = t + __ldg(q + nn + N);
-        t = t + __ldg(q + nn + N + 1);
-        dst[f * g3] = t * 0.125;
+    const double* own = U + (long long)s * F * n3;
+    double* blk = ghost + (long long)s * F * g3;
+    for (int r = threadIdx.x; r < g3; r += blockDim.x) {
+      const int cx = r % G - 3, cy = (r / G) % G - 3, cz = r / (G * G) - 3;
+      const int far = (cx == -3 || cx == N + 2) + (cy == -3 || cy == N + 2) + (cz == -3 || cz == N + 2);
+      if (far > 1) continue;
+      double* dst = blk + r;
+      const int sx = cx < 0 ? -1 : (cx >= N ? 1 : 0), sy = cy < 0 ? -1 : (cy >= N ? 1 : 0),
+                sz = cz < 0 ? -1 : (cz >= N ? 1 : 0);
+      if (sx == 0 && sy == 0 && sz == 0) {
+        const double* src = own + (cz * N + cy) * N + cx;
+        for (int f = 0; f < F; f++) dst[(long long)f * g3] = __ldg(src + (long long)f * n3);
+        continue;
+      }
+      const int2 e = nbs[(sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)];
+      auto wrap = [M](int q) { return q < 0 ? q + M : (q >= M ? q - M : q); };
+      const int px = wrap(og.bx + sx), py = wrap(og.by + sy), pz = wrap(og.bz + sz);
+      const int vx = cx - sx * N, vy = cy - sy * N, vz = cz - sz * N;  // cell in block p
+      const int gx = px * N + vx, gy = py * N + vy, gz = pz * N + vz;  // level cell index
+      if (e.x == 0) {
+        const double* src = U + (long long)e.y * F * n3 + (vz * N + vy) * N + vx;
+        for (int f = 0; f < F; f++) dst[(long long)f * g3] = __ldg(src + (long long)f * n3);
+      } else if (e.x < 0) {
+        const LeafGeo cg = geo[e.y];
+        const int lx = (gx >> 1) - cg.bx * N, ly = (gy >> 1) - cg.by * N, lz = (gz >> 1) - cg.bz * N;
+        const double* src = U + (long long)e.y * F * n3 + (lz * N + ly) * N + lx;
+        for (int f = 0; f < F; f++) dst[(long long)f * g3] = __ldg(src + (long long)f * n3);
+      } else {
+        const int fx = 2 * gx, fy = 2 * gy, fz = 2 * gz;
+        const int ch = (fx / N - 2 * px) + 2 * (fy / N - 2 * py) + 4 * (fz / N - 2 * pz);
+        const int leaf = __ldg(kids + 8 * e.y + ch);
+        const LeafGeo fg = geo[leaf];
+        const int lx = fx - fg.bx * N, ly = fy - fg.by * N, lz = fz - fg.bz * N;
+        const double* src = U + (long long)leaf * F * n3 + (lz * N + ly) * N + lx;
+        for (int f = 0; f < F; f++) {
+          const double* q = src + (long long)f * n3;
+          double t = __ldg(q);
+          t = t + __ldg(q + 1);
+          t = t + __ldg(q + N);
+          t = t + __ldg(q + N + 1);
+          t = t + __ldg(q + nn);
+          t = t + __ldg(q + nn + 1);
+          t = t + __ldg(q + nn + N);
+          t = t + __ldg(q + nn + N + 1);
+          dst[(long long)f * g3] = t * 0.125;
+        }
       }
     }
   }
@@ -535,8 +542,7 @@ int forest_launch(hydro_forest* fo, const double* U, const double* U0, double al
       }
       fo->bytes += (long long)gb;
     }
-    const long long cells = (long long)fo->nl * G * G * G;
-    const int gg = (int)std::min<long long>((cells + 255) / 256, (long long)D->n_sm * 8);
+    const int gg = (int)std::min<long long>((long long)fo->nl, (long long)D->n_sm * 8);  // CTAs over the leaves
     hydro_dev::forest_gather26_kernel<<<gg, 256, 0, st>>>(U, fo->ghost, fo->nb26, fo->kids, fo->geo, fo->nl, N,
                                                           F, fo->nb0);
     if ((e = cudaGetLastError()) != cudaSuccess) return hydro_host::cuda_fail(e, "forest gather launch");
