@@ -103,6 +103,24 @@ def test_ragged_sizes_and_partial_tiles(N):
     gh.check_fp64(got, ref, gam, ram, blocks, dxs)
 
 
+@pytest.mark.parametrize("prec", [hydro.FP64, hydro.FP32_FLUX_FP64_ACC])
+@pytest.mark.parametrize("N", [33, hydro.HYDRO_MAX_N])
+def test_large_and_largest_subgrids(N, prec):
+    """One sub-grid of many tiles: N = 33 (5 tiles per edge, the last one
+    cell wide) and the largest accepted edge (32768 tiles sharing one
+    signal-speed slot), against the oracle in both precisions."""
+    blocks = [synth.iid_block(synth.rng_for(99, N), N, 8)]
+    dxs = [1.0 / N]
+    got, gam = gh.run_gpu(gh.to_dev(blocks), dxs, prec=prec)
+    mode = 0 if prec == hydro.FP64 else 1
+    ref, ram, fl = gh.oracle_ref(blocks, dxs, mode=mode)
+    assert not fl.any()
+    if mode == 0:
+        gh.check_fp64(got, ref, gam, ram, blocks, dxs)
+    else:
+        gh.check_mixed(got, ref, gam, ram, blocks, dxs)
+
+
 @pytest.mark.parametrize("flags", MIXED_KERNELS)
 @pytest.mark.parametrize("N", [2, 3, 5, 12, 16, 17])
 def test_ragged_sizes_and_partial_tiles_mixed(N, flags):
