@@ -182,18 +182,42 @@ forest_reflux_kernel(const int* __restrict__ links, const AuxDesc* __restrict__ 
 // the block of the leaf's level at offset (dx, dy, dz): x = 0 a leaf of that
 // level (y), -1 inside the coarser leaf y, +1 refined: kids[8 y + i + 2j + 4k]
 // are its children (those next to the leaf are leaves).  The leaf's 27
-// entries and geometry are read once into shared memory.
-__global__ void __launch_bounds__(256)
+// entries, its geometry and those of the leaves its ghosts come from are read
+// once into shared memory; each cell then loads all its fields before it
+// stores them.
+__global__ void __launch_bounds__(256, 4)
 forest_gather26_kernel(const double* __restrict__ U, double* __restrict__ ghost, const int2* __restrict__ nb26,
                        const int* __restrict__ kids, const LeafGeo* __restrict__ geo, int nl, int N, int F,
                        int nb0) {
+  constexpr int MAXF = HYDRO_MAX_FIELDS;
   __shared__ int2 nbs[27];
   __shared__ LeafGeo gs;
+  // per offset j and child c (8 j + c): the leaf a ghost cell is read from and
+  // its geometry; a coarser source in c = 0
+  __shared__ int src_leaf[27 * 8];
+  __shared__ LeafGeo src_geo[27 * 8];
   const int G = N + 6, g3 = G * G * G, n3 = N * N * N, nn = N * N;
   for (int s = blockIdx.x; s < nl; s += gridDim.x) {
-    __syncthreads();  // the previous leaf's readers are done with nbs, gs
+    __syncthreads();  // the previous leaf's readers are done with the tables
     if (threadIdx.x < 27) nbs[threadIdx.x] = nb26[27 * s + threadIdx.x];
     if (threadIdx.x == 0) gs = geo[s];
+    __syncthreads();
+    if (threadIdx.x < 27 * 8) {
+      const int j = threadIdx.x >> 3, c = threadIdx.x & 7;
+      const int jx = j % 3 - 1, jy = (j / 3) % 3 - 1, jz = j / 9 - 1;
+      const int2 e = nbs[j];
+      // the children that ghost cells at this offset fall in: along an axis
+      // with offset +1 the low one, with -1 the high one, with 0 both
+      const bool next = (jx == 0 || (c & 1) == (jx < 0)) && (jy == 0 || ((c >> 1) & 1) == (jy < 0)) &&
+                        (jz == 0 || (c >> 2) == (jz < 0));
+      if (j != 13 && e.x > 0 && next) {
+        const int leaf = __ldg(kids + 8 * e.y + c);
+        src_leaf[threadIdx.x] = leaf;
+        src_geo[threadIdx.x] = geo[leaf];
+      } else if (j != 13 && e.x < 0 && c == 0) {
+        src_geo[threadIdx.x] = geo[e.y];
+      }
+    }
     __syncthreads();
     const LeafGeo og = gs;
     const int M = nb0 << og.level;
@@ -206,42 +230,56 @@ forest_gather26_kernel(const double* __restrict__ U, double* __restrict__ ghost,
       double* dst = blk + r;
       const int sx = cx < 0 ? -1 : (cx >= N ? 1 : 0), sy = cy < 0 ? -1 : (cy >= N ? 1 : 0),
                 sz = cz < 0 ? -1 : (cz >= N ? 1 : 0);
+      const double* src;
+      bool restrict8 = false;
       if (sx == 0 && sy == 0 && sz == 0) {
-        const double* src = own + (cz * N + cy) * N + cx;
-        for (int f = 0; f < F; f++) dst[(long long)f * g3] = __ldg(src + (long long)f * n3);
-        continue;
-      }
-      const int2 e = nbs[(sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)];
-      auto wrap = [M](int q) { return q < 0 ? q + M : (q >= M ? q - M : q); };
-      const int px = wrap(og.bx + sx), py = wrap(og.by + sy), pz = wrap(og.bz + sz);
-      const int vx = cx - sx * N, vy = cy - sy * N, vz = cz - sz * N;  // cell in block p
-      const int gx = px * N + vx, gy = py * N + vy, gz = pz * N + vz;  // level cell index
-      if (e.x == 0) {
-        const double* src = U + (long long)e.y * F * n3 + (vz * N + vy) * N + vx;
-        for (int f = 0; f < F; f++) dst[(long long)f * g3] = __ldg(src + (long long)f * n3);
-      } else if (e.x < 0) {
-        const LeafGeo cg = geo[e.y];
-        const int lx = (gx >> 1) - cg.bx * N, ly = (gy >> 1) - cg.by * N, lz = (gz >> 1) - cg.bz * N;
-        const double* src = U + (long long)e.y * F * n3 + (lz * N + ly) * N + lx;
-        for (int f = 0; f < F; f++) dst[(long long)f * g3] = __ldg(src + (long long)f * n3);
+        src = own + (cz * N + cy) * N + cx;
       } else {
-        const int fx = 2 * gx, fy = 2 * gy, fz = 2 * gz;
-        const int ch = (fx / N - 2 * px) + 2 * (fy / N - 2 * py) + 4 * (fz / N - 2 * pz);
-        const int leaf = __ldg(kids + 8 * e.y + ch);
-        const LeafGeo fg = geo[leaf];
-        const int lx = fx - fg.bx * N, ly = fy - fg.by * N, lz = fz - fg.bz * N;
-        const double* src = U + (long long)leaf * F * n3 + (lz * N + ly) * N + lx;
-        for (int f = 0; f < F; f++) {
-          const double* q = src + (long long)f * n3;
-          double t = __ldg(q);
-          t = t + __ldg(q + 1);
-          t = t + __ldg(q + N);
-          t = t + __ldg(q + N + 1);
-          t = t + __ldg(q + nn);
-          t = t + __ldg(q + nn + 1);
-          t = t + __ldg(q + nn + N);
-          t = t + __ldg(q + nn + N + 1);
-          dst[(long long)f * g3] = t * 0.125;
+        const int j = (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1);
+        const int2 e = nbs[j];
+        auto wrap = [M](int q) { return q < 0 ? q + M : (q >= M ? q - M : q); };
+        const int px = wrap(og.bx + sx), py = wrap(og.by + sy), pz = wrap(og.bz + sz);
+        const int vx = cx - sx * N, vy = cy - sy * N, vz = cz - sz * N;  // cell in block p
+        const int gx = px * N + vx, gy = py * N + vy, gz = pz * N + vz;  // level cell index
+        if (e.x == 0) {
+          src = U + (long long)e.y * F * n3 + (vz * N + vy) * N + vx;
+        } else if (e.x < 0) {
+          const LeafGeo cg = src_geo[8 * j];
+          const int lx = (gx >> 1) - cg.bx * N, ly = (gy >> 1) - cg.by * N, lz = (gz >> 1) - cg.bz * N;
+          src = U + (long long)e.y * F * n3 + (lz * N + ly) * N + lx;
+        } else {
+          const int fx = 2 * gx, fy = 2 * gy, fz = 2 * gz;
+          const int ch = (fx / N - 2 * px) + 2 * (fy / N - 2 * py) + 4 * (fz / N - 2 * pz);
+          const int leaf = src_leaf[8 * j + ch];
+          const LeafGeo fg = src_geo[8 * j + ch];
+          const int lx = fx - fg.bx * N, ly = fy - fg.by * N, lz = fz - fg.bz * N;
+          src = U + (long long)leaf * F * n3 + (lz * N + ly) * N + lx;
+          restrict8 = true;
+        }
+      }
+      if (!restrict8) {
+        double v[MAXF];
+#pragma unroll
+        for (int f = 0; f < MAXF; f++)
+          if (f < F) v[f] = __ldg(src + (long long)f * n3);
+#pragma unroll
+        for (int f = 0; f < MAXF; f++)
+          if (f < F) dst[(long long)f * g3] = v[f];
+      } else {
+#pragma unroll
+        for (int f = 0; f < MAXF; f++) {
+          if (f < F) {
+            const double* q = src + (long long)f * n3;
+            double t = __ldg(q);
+            t = t + __ldg(q + 1);
+            t = t + __ldg(q + N);
+            t = t + __ldg(q + N + 1);
+            t = t + __ldg(q + nn);
+            t = t + __ldg(q + nn + 1);
+            t = t + __ldg(q + nn + N);
+            t = t + __ldg(q + nn + N + 1);
+            dst[(long long)f * g3] = t * 0.125;
+          }
         }
       }
     }
@@ -294,6 +332,7 @@ void* forest_func(int k) {
 struct ForestDev {
   bool ready = false;
   int n_sm = 0, occ[kNumKernels] = {0, 0, 0, 0, 0};
+  int occ_gather = 1;  // resident CTAs of the 26-point gather per SM
 };
 ForestDev g_fdev[64];
 std::mutex g_fmu;
@@ -319,6 +358,10 @@ int forest_setup(int dev, ForestDev** out) {
         return hydro_host::cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
       if (D.occ[m] < 1) D.occ[m] = 1;
     }
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&D.occ_gather, hydro_dev::forest_gather26_kernel, 256,
+                                                           0)) != cudaSuccess)
+      return hydro_host::cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (D.occ_gather < 1) D.occ_gather = 1;
     D.ready = true;
   }
   *out = &D;
@@ -542,7 +585,8 @@ int forest_launch(hydro_forest* fo, const double* U, const double* U0, double al
       }
       fo->bytes += (long long)gb;
     }
-    const int gg = (int)std::min<long long>((long long)fo->nl, (long long)D->n_sm * 8);  // CTAs over the leaves
+    // one wave of resident CTAs over the leaves
+    const int gg = (int)std::min<long long>((long long)fo->nl, (long long)D->n_sm * D->occ_gather);
     hydro_dev::forest_gather26_kernel<<<gg, 256, 0, st>>>(U, fo->ghost, fo->nb26, fo->kids, fo->geo, fo->nl, N,
                                                           F, fo->nb0);
     if ((e = cudaGetLastError()) != cudaSuccess) return hydro_host::cuda_fail(e, "forest gather launch");
