@@ -442,7 +442,7 @@ int hydro_courant(const double* amax, int32_t n_rows, int64_t row_stride, int64_
  *   - n_subgrids > HYDRO_NOALLOC_MAX_SUBGRIDS: HYDRO_ETOOBIG, nothing runs.
  *   - The first call on a device (with that device current) resolves the
  *     array's device address and sets the kernels' attributes for that
- *     device; make that first call before any stream capture.
+ *     device; later calls on that device skip this set-up.
  *   - The descriptor array is copied with cudaMemcpyAsync on `stream`.  From
  *     pageable host memory the copy has taken the data when the call
  *     returns, and the array may be reused at once; from page-locked (pinned)
