@@ -115,6 +115,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.first = 0
 
     def start(self):
         try:
@@ -126,6 +127,13 @@ class ClockSampler:
             self.t.start()
         except Exception:
             self.proc = None
+            return
+        # nvidia-smi takes a moment to start: wait (up to 2 s) for its first
+        # sample so that the timed region that follows is sampled throughout
+        t_end = time.perf_counter() + 2.0
+        while not self.lines and self.proc.poll() is None and time.perf_counter() < t_end:
+            time.sleep(0.01)
+        self.first = len(self.lines)  # samples before this one were taken before the region
 
     def _read(self):
         for line in self.proc.stdout:
@@ -142,7 +150,8 @@ class ClockSampler:
         self.t.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines[self.first:] or self.lines
+        for ln in lines:
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 8:
                 continue
