@@ -191,11 +191,17 @@ def _check(rc, where):
 
 
 def _ptr(x) -> int:
-    """Device pointer of a torch tensor (or an int address)."""
+    """Address of a buffer: a torch tensor of binary64 values stored densely
+    (the C ABI reads and writes plain arrays), or an int address."""
     if x is None:
         return 0
     if isinstance(x, int):
         return x
+    if str(x.dtype) != "torch.float64":
+        raise TypeError("libhydro buffers hold binary64 values, not %s" % x.dtype)
+    if not x.is_contiguous():
+        raise ValueError("libhydro reads and writes dense arrays: pass a contiguous tensor "
+                         "(or the whole buffer, with its stride where the call takes one)")
     return int(x.data_ptr())
 
 

@@ -111,3 +111,25 @@ def test_per_subgrid_and_server_flags_are_checked(lib):
     assert lib.hydro_rhs_per_subgrid_ex(d, 1, 3, 5.0 / 3.0, 64, 64, 0, arr, 1, 1 << 10) == hydro.HYDRO_EINVAL
     with pytest.raises(hydro.HydroError):
         hydro.Server(dry_run_ns=1000, flags=hydro.F_REGISTER_LOADS)
+
+
+def test_buffers_must_be_dense_binary64():
+    """The binding passes a tensor's address only when the C ABI's plain
+    binary64 array reading of it is the tensor's own layout."""
+    import torch
+
+    from paper_2210_06438_gb300 import binding
+
+    a = torch.zeros(4, 6, dtype=torch.float64)
+    assert binding._ptr(a) == a.data_ptr() and binding._ptr(a[1]) == a[1].data_ptr()
+    assert binding._ptr(None) == 0 and binding._ptr(4096) == 4096
+    with pytest.raises(TypeError):
+        binding._ptr(a.float())
+    with pytest.raises(ValueError):
+        binding._ptr(a.t())
+    with pytest.raises(ValueError):
+        binding._ptr(a[:, :3])
+    # the check comes before the library is called
+    desc = hydro.descriptors([(4096, 0.1, 8, 6)])
+    with pytest.raises(TypeError):
+        hydro.rhs(desc, torch.zeros(6 * 512, dtype=torch.float32), a[0])
